@@ -1,0 +1,236 @@
+/*
+ * pdhgc: restarted PDHG for linear programs and the corner-push phase of
+ * Rothberg, "Backing PDHG into a Corner" (arXiv 2511.13894), on one GPU.
+ *
+ * The LP (Section 2) is   min c'x  s.t.  a_i x (=, <=, >=) b_i,  l <= x <= u
+ * with A an m x n sparse matrix.  Its canonical form (all '=', l = 0,
+ * u = +inf) is the primal of Section 2 with dual  max b'y  s.t.  A'y + z = c,
+ * z >= 0.  Inequality rows and bounds are handled implicitly, as Section 2
+ * says practical implementations do: no slack columns are added.
+ *
+ * Conventions of every call:
+ *  - Return value: PDHGC_OK (0) or a negative PDHGC_ERR_* code.  Nothing is
+ *    modified on an error return unless the call says otherwise.
+ *    pdhgc_strerror() gives a message; pdhgc_last_error_detail() gives the
+ *    detail of the last error on the calling thread (e.g. the CUDA error).
+ *  - All device work is enqueued on the CUDA stream given to
+ *    pdhgc_lp_create (NULL = the legacy default stream).  Calls that return
+ *    host results synchronise that stream before returning.
+ *  - A handle is not thread-safe; different handles are independent.
+ *  - Vectors are dense, in the user's row / column order, FP64.  A pointer
+ *    argument documented "host or device" is a device pointer when the
+ *    call's `on_device` flag is 1 and a host pointer when it is 0.
+ *  - Dual signs: y_i >= 0 on '>' rows, y_i <= 0 on '<' rows, free on '='
+ *    rows (Lagrangian c'x - y'(Ax - b)).  z = c - A'y projected onto the
+ *    cone allowed by the finite bounds (z_j >= 0 at a finite lower bound,
+ *    <= 0 at a finite upper bound, 0 for a free column).
+ */
+#ifndef PDHGC_H
+#define PDHGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (return values) ---------------------------------------- */
+#define PDHGC_OK                 0
+#define PDHGC_ERR_INVALID_ARG   -1  /* NULL handle/pointer, m or n < 1, bad flag, bad parameter value */
+#define PDHGC_ERR_INVALID_CSR   -2  /* row_ptr not monotone / not 0-based / nnz mismatch, column out of range */
+#define PDHGC_ERR_NONFINITE     -3  /* NaN or Inf in A, b or c; NaN in a bound; l = +inf or u = -inf */
+#define PDHGC_ERR_BOUNDS        -4  /* l_j > u_j */
+#define PDHGC_ERR_CUDA          -5  /* a CUDA runtime call failed (detail string has the CUDA error) */
+#define PDHGC_ERR_OOM           -6  /* device or pinned-host allocation failed */
+#define PDHGC_ERR_NO_PHASE1     -7  /* corner phase or PHASE1 report requested before pdhgc_solve */
+#define PDHGC_ERR_NO_CORNER     -8  /* CORNER report / solution requested before pdhgc_corner_phase */
+#define PDHGC_ERR_TOO_LARGE     -9  /* nnz >= 2^31 or a dimension >= 2^31 */
+#define PDHGC_ERR_DEVICE        -10 /* a device-side check failed (error word set by a kernel) */
+#define PDHGC_ERR_BUFFER        -11 /* a caller buffer is too small (size written back) */
+
+/* ---- solver outcome (pdhgc_report.status) -------------------------------- */
+#define PDHGC_STATUS_NONE          0
+#define PDHGC_STATUS_OPTIMAL       1  /* the three relative tolerances of Section 2 met */
+#define PDHGC_STATUS_ITER_LIMIT    2
+#define PDHGC_STATUS_TIME_LIMIT    3
+#define PDHGC_STATUS_NUMERICAL     4  /* a non-finite KKT quantity appeared */
+#define PDHGC_STATUS_CORNER_DONE   5  /* Section 3.1 stopping rule met */
+#define PDHGC_STATUS_CORNER_LIMIT  6  /* corner phase hit a limit; the phase-1 x is returned */
+
+/* ---- precision and which-solution selectors ------------------------------ */
+#define PDHGC_FP64       0  /* matrix, iterates and SpMV accumulation in FP64 */
+#define PDHGC_FP32_BULK  1  /* FP32 matrix and iterates in the iteration; FP64-class
+                               (float-float) row sums and running sums; every KKT,
+                               gap, restart, step-size and primal-weight quantity in FP64 */
+
+#define PDHGC_PHASE1  0
+#define PDHGC_CORNER  1
+
+/* Sense codes are ASCII: '=' (61), '<' (60), '>' (62). */
+
+/*
+ * Phase-1 parameters.  The paper fixes eps_rel (1e-6, Section 4.1); every
+ * other value is the cuPDLP-family reading this library implements (the
+ * paper prints no PDHG iteration).  pdhgc_default_params() fills defaults.
+ */
+typedef struct pdhgc_params {
+    double  eps_rel;       /* relative tolerance of the Section 2 test (1e-6); < 0 never stops on it */
+    int64_t max_iters;     /* iteration limit (>= 1), default 1,000,000 */
+    double  time_limit_s;  /* device-clock time limit, checked at each check period (3600) */
+    int32_t check_period;  /* iterations between KKT / restart checks (64, 1..4096) */
+    double  beta_suff;     /* restart on sufficient decay of KKT_omega (0.2) */
+    double  beta_nec;      /* restart on necessary decay without progress (0.8) */
+    double  beta_art;      /* artificial restart when t >= beta_art * k (0.36) */
+    double  theta;         /* primal-weight smoothing in log space (0.5) */
+    double  eta_factor;    /* step eta = eta_factor / sigma_max(A_hat) (0.998) */
+    int32_t ruiz_iters;    /* Ruiz infinity-norm passes (10, 0..100) */
+    int32_t power_iters;   /* power iterations for sigma_max (100, 1..10000) */
+    int32_t precision;     /* PDHGC_FP64 or PDHGC_FP32_BULK */
+    int32_t reserved;
+} pdhgc_params;
+
+/*
+ * Corner-phase parameters (Algorithm 1 and Section 3.1).
+ */
+typedef struct pdhgc_corner_params {
+    double   eps_abs;      /* reduced-cost threshold of Algorithm 1 (1e-6) */
+    double   eps_rel;      /* primal tolerance to regain, Section 3.1 (1e-6) */
+    int64_t  min_iters;    /* at least this many corner iterations (100) */
+    int64_t  max_iters;    /* corner iteration limit (1,000,000) */
+    double   time_limit_s; /* device-clock limit (3600) */
+    uint64_t obj_seed;     /* seed of the Uniform([0,1]^n) objective (SplitMix64 stream) */
+    double   obj_scale;    /* objective = obj_scale * U[0,1) (1.0; Section 5 studies small scales) */
+    int32_t  stop_rule;    /* 0: Section 3.1 primal rule; 1: full relative KKT (a testing aid) */
+    int32_t  reserved;
+} pdhgc_corner_params;
+
+/*
+ * Result of a phase or a report.  Norms are of the user's (unscaled) model.
+ * Metrics follow Section 2.1 and Section 4.2 with tolerance 1e-6, counting
+ * one explicit slack per inequality row:
+ *   off_bound_p    variables (and inequality slacks) more than 1e-6 from both bounds
+ *   zero_rc_d      variables with |z_j| <= 1e-6 plus inequality rows with |y_i| <= 1e-6
+ *   candidates     variables (and slacks) off bound with |reduced cost| <= 1e-6
+ *   corner_measure max(0, candidates - m)
+ *   primal_push_est max(0, p - m);  dual_push_est max(0, m - d)
+ *   should_corner  candidates >= max(2m, 100000)
+ */
+typedef struct pdhgc_report {
+    int32_t status;        /* PDHGC_STATUS_* */
+    int32_t chosen;        /* 0: current iterate returned, 1: average returned */
+    int64_t iters;         /* PDHG iterations of the phase */
+    int64_t restarts;
+    double  rP2, rD2;      /* ||r_P||_2, ||r_D||_2 */
+    double  rPinf, rDinf;  /* infinity norms */
+    double  pobj, dobj;    /* c'x and b'y + sum l_j z_j^+ - sum u_j z_j^- */
+    double  gap;           /* pobj - dobj */
+    double  rel_p, rel_d, rel_gap, rel_kkt; /* Section 2 ratios; rel_kkt = their max */
+    int64_t off_bound_p, zero_rc_d, candidates, corner_measure;
+    int64_t primal_push_est, dual_push_est;
+    int32_t should_corner;
+    int32_t precision;
+    double  seconds;       /* device-clock seconds of the phase (0 for a report) */
+    double  omega, eta, sigma_max; /* primal weight at exit, step size, norm estimate */
+} pdhgc_report;
+
+typedef struct pdhgc_lp pdhgc_lp;   /* opaque; owns all of its device memory */
+
+void pdhgc_default_params(pdhgc_params* p);
+void pdhgc_default_corner_params(pdhgc_corner_params* p);
+
+/*
+ * pdhgc_lp_create — the problem data of Section 2 (A m x n in CSR, b, c,
+ * bounds and row senses).  Validates, copies and lays out the data on the
+ * device: rows and columns are renumbered internally by decreasing nnz so
+ * that rows of similar length share a warp, an explicit CSR of A' is built,
+ * and row tiles for the SpMV kernels are planned.  The caller keeps
+ * ownership of every input; the handle owns the device copies.
+ *   row_ptr  int64[m+1], 0-based, non-decreasing, row_ptr[m] = nnz
+ *   col_idx  int32[nnz] in [0, n); val FP64[nnz], finite
+ *   b FP64[m], c FP64[n] finite
+ *   lb, ub   FP64[n] or NULL (NULL: l = 0, u = +inf); +-inf allowed
+ *   sense    int8[m] of '=', '<', '>' or NULL (all '=')
+ *   inputs_on_device  1: the six array arguments are device pointers
+ *   cuda_stream       cudaStream_t (as void*) used by every later call
+ * Errors: INVALID_ARG, INVALID_CSR, NONFINITE, BOUNDS, TOO_LARGE, CUDA, OOM.
+ * The scaling and step size are computed by pdhgc_solve (they are part of
+ * the timed solve); create only uploads and lays out the data.
+ */
+int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz,
+                    const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                    const double* b, const double* c, const double* lb, const double* ub,
+                    const int8_t* sense, int inputs_on_device, void* cuda_stream);
+
+/*
+ * pdhgc_solve — phase 1: scale (Ruiz + Pock-Chambolle), estimate
+ * sigma_max(A_hat), then run restarted PDHG on the device until the
+ * Section 2 relative test holds with eps_rel (Section 4.1: 1e-6) at a
+ * check, or a limit.  The whole loop (iterations, checks, restarts,
+ * termination) runs as one CUDA graph with a device-side while condition;
+ * no host round trip per iteration.  `out` may be NULL.  Re-solving
+ * discards any previous phase-1 and corner result of the handle.
+ */
+int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out);
+
+/*
+ * pdhgc_corner_phase — Algorithm 1 applied to the phase-1 result:
+ * ub_j <- x_j where z_j > eps_abs, lb_j <- x_j where z_j < -eps_abs,
+ * inequality rows with |y_i| > eps_abs become '=' (Section 3), objective
+ * obj_scale * Uniform([0,1]^n) from SplitMix64(obj_seed), PDHG restarted
+ * from (x, 0) with the phase-1 step size, stopped by the Section 3.1 rule
+ * (k >= min_iters and ||r_P||_2 <= eps_rel (1 + ||b||_2), at a check).
+ * Returns (x_hat, y, z) with the phase-1 y and z.  The report's KKT numbers
+ * and metrics are those of (x_hat, y, z) on the ORIGINAL model.
+ * Errors: NO_PHASE1 before pdhgc_solve.
+ */
+int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_report* out);
+
+/*
+ * pdhgc_kkt_report — residuals, objectives, Section 2 ratios and the
+ * Section 2.1 / 4.2 metrics of the PHASE1 or CORNER solution on the
+ * original model, computed on the device.
+ */
+int pdhgc_kkt_report(pdhgc_lp* lp, int which, pdhgc_report* out);
+
+/*
+ * pdhgc_get_solution — x (n), y (m), z (n) of the PHASE1 or CORNER
+ * solution in the user's order and scale.  Any of the three may be NULL.
+ */
+int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z, int on_device);
+
+/*
+ * pdhgc_get_iterates — the solver's state in scaled space, user order:
+ * current x_hat (n), y_hat (m) and the running averages of the iterates
+ * since the last restart (zeros when no iteration ran since it).  Any
+ * pointer may be NULL.  iters_out (may be NULL) receives {k, t, restarts}.
+ * For parity tests against a reference implementation.
+ */
+int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double* y_avg,
+                       int64_t* iters_out, int on_device);
+
+/*
+ * pdhgc_get_scaling — D_r (m), D_c (n) in user order and the scalars
+ * {sigma_max, eta, omega, tau, sigma} (5 doubles).  Any pointer may be NULL.
+ */
+int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalars, int on_device);
+
+/*
+ * pdhgc_uniform — out[j] = obj_scale * U_j for j < n, where U_j is the top 53
+ * bits of the (j+1)-th SplitMix64 output from state `seed`, times 2^-53
+ * (the corner objective of Algorithm 1).  `out` is a device pointer; the
+ * work is enqueued on `cuda_stream` and the call synchronises it.
+ */
+int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void* cuda_stream);
+
+/* Size in bytes of the opaque device kernel count record (for tests). */
+int64_t pdhgc_kernel_launches(const pdhgc_lp* lp);
+
+void pdhgc_lp_destroy(pdhgc_lp* lp);
+const char* pdhgc_strerror(int code);
+const char* pdhgc_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDHGC_H */

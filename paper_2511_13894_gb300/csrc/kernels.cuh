@@ -1,0 +1,525 @@
+// Device code of the PDHG + corner-push path (sm_103a).
+//
+// Every matrix pass is one "tile SpMV": a CTA takes one row tile of a CSR
+// (host_prep.h), stages the tile's values and column indices in shared
+// memory with coalesced loads, and reduces each row with `lanes` lanes
+// (one lane per row for short rows, so a row's sum costs exactly one FMA
+// per nonzero) or with the whole CTA for a long row.  The per-row result
+// goes straight into a fused epilogue (projection, extrapolation, running
+// sums, residuals) and per-tile partial sums for the KKT reductions, which
+// a single CTA later folds in a fixed order: every reduction is
+// deterministic run to run.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "host_prep.h"
+
+namespace pdhgc {
+
+// ---------------------------------------------------------------------------
+// Device scalar state of one phase.  Written only by the single-thread
+// control kernels (init / pre-check / decide) between matrix passes.
+// ---------------------------------------------------------------------------
+struct Scalars {
+  double eta, omega, tau, sigma, sigma_max;
+  double kkt_r, kkt_prev, inv_t;
+  double eps_rel, beta_suff, beta_nec, beta_art, theta, time_limit_s;
+  double nb, nc;           // ||b||_2 of the user's b; ||c||_2 of the phase's (unscaled) objective
+  double nb_hat, nc_hat;   // ||b_hat||, ||c_hat|| (initial primal weight)
+  long long k, t, restarts, chunks, max_chunks, max_iters, min_iters;
+  unsigned long long t0_ns, t1_ns;
+  int check_period, phase, stop_rule, done, status, chosen, restart_to;
+  int at_check, at_limit, pi_zero, error;
+  // last evaluation of the current (0) and average (1) point
+  double kkt[2], rel_p[2], rel_d[2], rel_gap[2], rel_kkt[2], rP2[2];
+};
+
+struct DevModel {
+  const double* chat;
+  const double* lhat;
+  const double* uhat;
+  const double* bhat;
+  const double* Dr;
+  const double* Dc;
+  const int8_t* ge;
+};
+
+struct DevIter {
+  double* x;
+  double* y;
+  double* xbar;
+  double* sum_x;
+  double* sum_y;
+  double* x_r;
+  double* y_r;
+};
+
+constexpr int kWarps = kBlock / 32;
+
+// ---------------------------------------------------------------------------
+// Accumulators
+// ---------------------------------------------------------------------------
+template <int NV>
+struct SumD {
+  double v[NV];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(const SumD& o) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += o.v[i];
+  }
+  __device__ __forceinline__ SumD shfl_xor(unsigned mask, int off) const {
+    SumD r;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) r.v[i] = __shfl_xor_sync(mask, v[i], off);
+    return r;
+  }
+};
+
+struct MaxD {
+  double v[1];
+  __device__ __forceinline__ void zero() { v[0] = 0.0; }
+  __device__ __forceinline__ void add(const MaxD& o) { v[0] = fmax(v[0], o.v[0]); }
+  __device__ __forceinline__ MaxD shfl_xor(unsigned mask, int off) const {
+    MaxD r;
+    r.v[0] = __shfl_xor_sync(mask, v[0], off);
+    return r;
+  }
+};
+
+// z = projection of lam onto the cone the finite bounds allow (Section 2)
+__device__ __forceinline__ double proj_dual(double lam, double l, double u) {
+  const bool lf = l != -INFINITY, uf = u != INFINITY;
+  if (lf && uf) return lam;
+  if (lf) return fmax(lam, 0.0);
+  if (uf) return fmin(lam, 0.0);
+  return 0.0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// The tile SpMV kernel
+// ---------------------------------------------------------------------------
+template <class Op>
+__global__ void __launch_bounds__(kBlock) tile_spmv(const Tile* __restrict__ tiles, int ntiles,
+                                                    const int* __restrict__ row_ptr,
+                                                    const int* __restrict__ col,
+                                                    const double* __restrict__ val, Op op,
+                                                    double* __restrict__ partials) {
+  constexpr int NQ = Op::NQ;
+  constexpr int NQS = NQ > 0 ? NQ : 1;
+  __shared__ double s_val[kTileNnz];
+  __shared__ int s_col[kTileNnz];
+  __shared__ typename Op::Acc s_acc[kWarps];
+  __shared__ double s_red[NQS][kWarps];
+  if (op.skip()) return;
+  const Tile t = tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int lane32 = tid & 31, warp = tid >> 5;
+  double part[NQS];
+#pragma unroll
+  for (int q = 0; q < NQS; ++q) part[q] = 0.0;
+
+  if (t.lanes == 0) {
+    const int r = t.row0;
+    const int e0 = row_ptr[r], e1 = row_ptr[r + 1];
+    const double rc = op.row_ctx(r);
+    typename Op::Acc acc;
+    acc.zero();
+    for (int e = e0 + tid; e < e1; e += kBlock) op.combine(acc, rc, val[e], col[e]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
+    if (lane32 == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      typename Op::Acc tot = s_acc[0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) tot.add(s_acc[w]);
+      op.epilogue(r, tot, part);
+    }
+  } else {
+    const int e0 = row_ptr[t.row0];
+    const int cnt = row_ptr[t.row0 + t.nrows] - e0;
+    for (int k = tid; k < cnt; k += kBlock) {
+      s_val[k] = val[e0 + k];
+      s_col[k] = col[e0 + k];
+    }
+    __syncthreads();
+    const int g = t.lanes;
+    const int grp = tid / g;
+    const int lane = tid & (g - 1);
+    if (grp < t.nrows) {
+      const int r = t.row0 + grp;
+      const int a = row_ptr[r] - e0, b = row_ptr[r + 1] - e0;
+      const double rc = op.row_ctx(r);
+      typename Op::Acc acc;
+      acc.zero();
+      for (int k = a + lane; k < b; k += g) op.combine(acc, rc, s_val[k], s_col[k]);
+      if (g > 1) {
+        const unsigned base = lane32 & ~(g - 1);
+        const unsigned mask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << base);
+        for (int off = g >> 1; off > 0; off >>= 1) acc.add(acc.shfl_xor(mask, off));
+      }
+      if (lane == 0) op.epilogue(r, acc, part);
+    }
+  }
+
+  if constexpr (NQ > 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double v = part[q];
+      const bool is_max = (Op::kMaxMask >> q) & 1u;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = is_max ? fmax(v, o) : v + o;
+      }
+      if (lane32 == 0) s_red[q][warp] = v;
+    }
+    __syncthreads();
+    if (tid < NQ) {
+      const bool is_max = (Op::kMaxMask >> tid) & 1u;
+      double v = s_red[tid][0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) v = is_max ? fmax(v, s_red[tid][w]) : v + s_red[tid][w];
+      partials[(size_t)tid * ntiles + blockIdx.x] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue operators
+// ---------------------------------------------------------------------------
+
+// x' = proj_[l,u](x - tau (c - A'y)),  x_bar = 2x' - x,  sum_x += x'
+struct PrimalOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const Scalars* S;
+  int it;
+  const double* __restrict__ y;
+  DevModel md;
+  DevIter w;
+  __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double*) const {
+    const double tau = S->tau;
+    const double g = md.chat[j] - a.v[0];
+    const double xo = w.x[j];
+    const double xn = fmin(fmax(xo - tau * g, md.lhat[j]), md.uhat[j]);
+    w.xbar[j] = 2.0 * xn - xo;
+    w.sum_x[j] += xn;
+    w.x[j] = xn;
+  }
+};
+
+// y' = y + sigma (b - A x_bar), y' >= 0 on '>' rows,  sum_y += y'
+struct DualOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const Scalars* S;
+  int it;
+  const double* __restrict__ xbar;
+  DevModel md;
+  DevIter w;
+  __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(xbar + c), a.v[0]); }
+  __device__ void epilogue(int i, const Acc& a, double*) const {
+    const double sigma = S->sigma;
+    double yn = w.y[i] + sigma * (md.bhat[i] - a.v[0]);
+    if (md.ge[i]) yn = fmax(yn, 0.0);
+    w.sum_y[i] += yn;
+    w.y[i] = yn;
+  }
+};
+
+// KKT pieces from the rows: for w in {current, average}
+//   r_hat = b_hat - A_hat x_w (max(.,0) on '>' rows), r_hat^2, (r_hat/D_r)^2,
+//   max |r_hat/D_r|, b_hat y_w, (y_w - y_r)^2
+struct EvalRowsOp {
+  using Acc = SumD<2>;
+  static constexpr int NQ = 10;
+  static constexpr unsigned kMaxMask = (1u << 2) | (1u << 7);
+  const Scalars* S;
+  const double* __restrict__ x;
+  const double* __restrict__ sum_x;
+  const double* __restrict__ y;
+  const double* __restrict__ sum_y;
+  const double* __restrict__ y_r;
+  DevModel md;
+  __device__ bool skip() const { return S->done; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const {
+    a.v[0] = fma(v, __ldg(x + c), a.v[0]);
+    a.v[1] = fma(v, __ldg(sum_x + c), a.v[1]);
+  }
+  __device__ void epilogue(int i, const Acc& a, double* part) const {
+    const double inv_t = S->inv_t;
+    const double b = md.bhat[i], dr = md.Dr[i];
+    const bool ge = md.ge[i];
+#pragma unroll
+    for (int wv = 0; wv < 2; ++wv) {
+      const double ax = wv == 0 ? a.v[0] : a.v[1] * inv_t;
+      double r = b - ax;
+      if (ge) r = fmax(r, 0.0);
+      const double ru = r / dr;
+      const double yw = wv == 0 ? y[i] : sum_y[i] * inv_t;
+      const double d = yw - y_r[i];
+      part[5 * wv + 0] += r * r;
+      part[5 * wv + 1] += ru * ru;
+      part[5 * wv + 2] = fmax(part[5 * wv + 2], fabs(ru));
+      part[5 * wv + 3] += b * yw;
+      part[5 * wv + 4] += d * d;
+    }
+  }
+};
+
+// KKT pieces from the columns: lam = c_hat - A_hat' y_w, z = proj(lam),
+//   r_D = lam - z, r_D^2, (r_D/D_c)^2, max |r_D/D_c|, c_hat x_w,
+//   l z^+ - u z^- (finite bounds), (x_w - x_r)^2
+struct EvalColsOp {
+  using Acc = SumD<2>;
+  static constexpr int NQ = 12;
+  static constexpr unsigned kMaxMask = (1u << 2) | (1u << 8);
+  const Scalars* S;
+  const double* __restrict__ y;
+  const double* __restrict__ sum_y;
+  const double* __restrict__ x;
+  const double* __restrict__ sum_x;
+  const double* __restrict__ x_r;
+  DevModel md;
+  __device__ bool skip() const { return S->done; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const {
+    a.v[0] = fma(v, __ldg(y + c), a.v[0]);
+    a.v[1] = fma(v, __ldg(sum_y + c), a.v[1]);
+  }
+  __device__ void epilogue(int j, const Acc& a, double* part) const {
+    const double inv_t = S->inv_t;
+    const double c = md.chat[j], l = md.lhat[j], u = md.uhat[j], dc = md.Dc[j];
+#pragma unroll
+    for (int wv = 0; wv < 2; ++wv) {
+      const double aty = wv == 0 ? a.v[0] : a.v[1] * inv_t;
+      const double lam = c - aty;
+      const double z = proj_dual(lam, l, u);
+      const double rd = lam - z;
+      const double rdu = rd / dc;
+      const double xw = wv == 0 ? x[j] : sum_x[j] * inv_t;
+      const double bnd = (l != -INFINITY ? l * fmax(z, 0.0) : 0.0) - (u != INFINITY ? u * fmax(-z, 0.0) : 0.0);
+      const double d = xw - x_r[j];
+      part[6 * wv + 0] += rd * rd;
+      part[6 * wv + 1] += rdu * rdu;
+      part[6 * wv + 2] = fmax(part[6 * wv + 2], fabs(rdu));
+      part[6 * wv + 3] += c * xw;
+      part[6 * wv + 4] += bnd;
+      part[6 * wv + 5] += d * d;
+    }
+  }
+};
+
+// Ruiz / Pock-Chambolle factor passes on the entries (D_r |a|) D_c of the
+// current scaled matrix, in the order the products are formed on the host
+// reference.  ScaleMaxOp: 1/sqrt(row or column maximum); ScaleSumOp:
+// 1/sqrt(row or column sum); 1 for an empty row or column.  kTransposed: the
+// CSR is A' (its row is column j of A, its col is row i of A).
+template <bool kTransposed>
+struct ScaleMaxOp {
+  using Acc = MaxD;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const double* __restrict__ d_own;    // D_r for A rows, D_c for A' rows
+  const double* __restrict__ d_other;  // D_c for A rows, D_r for A' rows
+  double* __restrict__ fac;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int r) const { return d_own[r]; }
+  __device__ void combine(Acc& a, double rc, double v, int c) const {
+    const double e = kTransposed ? (d_other[c] * fabs(v)) * rc : (rc * fabs(v)) * d_other[c];
+    a.v[0] = fmax(a.v[0], e);
+  }
+  __device__ void epilogue(int r, const Acc& a, double*) const {
+    fac[r] = a.v[0] > 0.0 ? 1.0 / sqrt(a.v[0]) : 1.0;
+  }
+};
+
+template <bool kTransposed>
+struct ScaleSumOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const double* __restrict__ d_own;
+  const double* __restrict__ d_other;
+  double* __restrict__ fac;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int r) const { return d_own[r]; }
+  __device__ void combine(Acc& a, double rc, double v, int c) const {
+    const double e = kTransposed ? (d_other[c] * fabs(v)) * rc : (rc * fabs(v)) * d_other[c];
+    a.v[0] += e;
+  }
+  __device__ void epilogue(int r, const Acc& a, double*) const {
+    fac[r] = a.v[0] > 0.0 ? 1.0 / sqrt(a.v[0]) : 1.0;
+  }
+};
+
+// out = A_hat v (or A_hat' v); optional partial sum of out^2
+template <bool kNorm>
+struct SpmvOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = kNorm ? 1 : 0;
+  static constexpr unsigned kMaxMask = 0;
+  const Scalars* S;
+  const double* __restrict__ v;
+  double* __restrict__ out;
+  __device__ bool skip() const { return S->pi_zero != 0; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double val, int c) const { a.v[0] = fma(val, __ldg(v + c), a.v[0]); }
+  __device__ void epilogue(int r, const Acc& a, double* part) const {
+    out[r] = a.v[0];
+    if constexpr (kNorm) part[0] += a.v[0] * a.v[0];
+  }
+};
+
+// Report on the ORIGINAL model for a given scaled point (x_hat, y_hat):
+// residual pieces plus the Section 2.1 / 4.2 slack metrics per row.
+struct ReportRowsOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 7;
+  static constexpr unsigned kMaxMask = 1u << 2;
+  const double* __restrict__ x;
+  const double* __restrict__ y;
+  DevModel md;
+  double tol;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(x + c), a.v[0]); }
+  __device__ void epilogue(int i, const Acc& a, double* part) const {
+    const double b = md.bhat[i], dr = md.Dr[i];
+    const bool ge = md.ge[i];
+    double r = b - a.v[0];
+    if (ge) r = fmax(r, 0.0);
+    const double ru = r / dr;
+    part[0] += r * r;
+    part[1] += ru * ru;
+    part[2] = fmax(part[2], fabs(ru));
+    part[3] += b * y[i];
+    if (ge) {
+      const double slack = (a.v[0] - b) / dr;
+      const bool off = slack > tol;
+      const bool zero = fabs(dr * y[i]) <= tol;
+      part[4] += off ? 1.0 : 0.0;
+      part[5] += zero ? 1.0 : 0.0;
+      part[6] += (off && zero) ? 1.0 : 0.0;
+    }
+  }
+};
+
+struct ReportColsOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 8;
+  static constexpr unsigned kMaxMask = 1u << 2;
+  const double* __restrict__ y;
+  const double* __restrict__ x;
+  const double* __restrict__ l_user;
+  const double* __restrict__ u_user;
+  DevModel md;
+  double tol;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double* part) const {
+    const double c = md.chat[j], l = md.lhat[j], u = md.uhat[j], dc = md.Dc[j];
+    const double lam = c - a.v[0];
+    const double z = proj_dual(lam, l, u);
+    const double rd = lam - z;
+    const double rdu = rd / dc;
+    part[0] += rd * rd;
+    part[1] += rdu * rdu;
+    part[2] = fmax(part[2], fabs(rdu));
+    part[3] += c * x[j];
+    part[4] += (l != -INFINITY ? l * fmax(z, 0.0) : 0.0) - (u != INFINITY ? u * fmax(-z, 0.0) : 0.0);
+    const double xu = dc * x[j];
+    const double zu = z / dc;
+    const bool off = fmin(xu - l_user[j], u_user[j] - xu) > tol;
+    const bool zero = fabs(zu) <= tol;
+    part[5] += off ? 1.0 : 0.0;
+    part[6] += zero ? 1.0 : 0.0;
+    part[7] += (off && zero) ? 1.0 : 0.0;
+  }
+};
+
+// SplitMix64 (Steele, Lea and Flood 2014): output number (j+1) of the stream
+// started at `seed`, i.e. the finaliser applied to seed + (j+1) * gamma.
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long j) {
+  unsigned long long z = seed + (j + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Algorithm 1 on the columns: z = proj(c_hat - A_hat' y1) / D_c (unscaled),
+// ub <- x where z > eps_abs, lb <- x where z < -eps_abs (scaled space),
+// c' = obj_scale * U(seed, user column) scaled by D_c; partial sums of
+// c_hat'^2 and c'^2 for the new primal weight and ||c'||.
+struct CornerColsOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 2;
+  static constexpr unsigned kMaxMask = 0;
+  const double* __restrict__ y1;
+  const double* __restrict__ x1;
+  const int* __restrict__ col_perm;
+  DevModel md;  // original model
+  double* __restrict__ lc;
+  double* __restrict__ uc;
+  double* __restrict__ cc;
+  double eps_abs, obj_scale;
+  unsigned long long seed;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y1 + c), a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double* part) const {
+    const double dc = md.Dc[j];
+    const double lam = md.chat[j] - a.v[0];
+    const double z = proj_dual(lam, md.lhat[j], md.uhat[j]) / dc;
+    lc[j] = z < -eps_abs ? x1[j] : md.lhat[j];
+    uc[j] = z > eps_abs ? x1[j] : md.uhat[j];
+    const double cu = obj_scale * splitmix_uniform(seed, (unsigned long long)col_perm[j]);
+    const double ch = dc * cu;
+    cc[j] = ch;
+    part[0] += ch * ch;
+    part[1] += cu * cu;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+
+// deterministic sum (or max) of partials[q * ntiles + 0 .. ntiles-1] by one CTA
+__device__ double block_fold(const double* __restrict__ p, int ntiles, bool is_max, double* s_tmp) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < ntiles; k += blockDim.x) v = is_max ? fmax(v, p[k]) : v + p[k];
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = is_max ? fmax(v, o) : v + o;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s_tmp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double tot = s_tmp[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = is_max ? fmax(tot, s_tmp[w]) : tot + s_tmp[w];
+  return tot;  // same value in every thread
+}
+
+}  // namespace pdhgc

@@ -1,0 +1,1134 @@
+// C-ABI of the PDHG + corner-push library (include/pdhgc.h): handle,
+// device memory, setup kernels, the graph-driven restarted PDHG loop,
+// Algorithm 1, reports and accessors.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhgc.h"
+#include "host_prep.h"
+#include "kernels.cuh"
+
+using namespace pdhgc;
+
+namespace {
+
+thread_local std::string g_detail;
+
+int set_err(int code, const std::string& d) {
+  g_detail = d;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return set_err(e_ == cudaErrorMemoryAllocation ? PDHGC_ERR_OOM : PDHGC_ERR_CUDA,    \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                     \
+  } while (0)
+
+#define CKL()                                                                             \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(PDHGC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- report as computed on the device ------------------------------------
+struct DevReport {
+  double rP2, rD2, rPinf, rDinf, pobj, dobj, gap, rel_p, rel_d, rel_gap, rel_kkt;
+  double p, d, cand;
+};
+
+// ---- small kernels ---------------------------------------------------------
+
+__global__ void k_fill(double* v, int n, double a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = a;
+}
+
+__global__ void k_mul_inplace(double* v, const double* f, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = v[i] * f[i];
+}
+
+// A_hat values: (D_r a) D_c for A, the same product for A'
+__global__ void k_scale_values(const int* __restrict__ row_ptr, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ out, int rows,
+                               const double* __restrict__ Dr, const double* __restrict__ Dc,
+                               int transposed) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  for (int e = row_ptr[warp] + lane; e < row_ptr[warp + 1]; e += 32) {
+    const int c = col[e];
+    out[e] = transposed ? (Dr[c] * val[e]) * Dc[warp] : (Dr[warp] * val[e]) * Dc[c];
+  }
+}
+
+// b_hat = D_r b_int; c_hat = D_c c; l_hat = l / D_c; u_hat = u / D_c
+__global__ void k_scale_vectors(int m, int n, const double* Dr, const double* Dc, const double* b_int,
+                                const double* c, const double* l, const double* u, double* bhat,
+                                double* chat, double* lhat, double* uhat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) bhat[i] = Dr[i] * b_int[i];
+  if (i < n) {
+    chat[i] = Dc[i] * c[i];
+    lhat[i] = l[i] / Dc[i];
+    uhat[i] = u[i] / Dc[i];
+  }
+}
+
+// one CTA: out[0] = sum v^2 (fixed order)
+__global__ void k_norm2(const double* __restrict__ v, int n, double* out) {
+  __shared__ double s_tmp[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += v[i] * v[i];
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if ((threadIdx.x & 31) == 0) s_tmp[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = s_tmp[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t += s_tmp[w];
+    out[0] = t;
+  }
+}
+
+// power iteration: nw = ||w|| from partials; flag A_hat = 0
+__global__ void k_pi_norm(Scalars* S, const double* partials, int ntiles, double* nw_out) {
+  __shared__ double s_tmp[32];
+  if (S->pi_zero) return;
+  const double s = block_fold(partials, ntiles, false, s_tmp);
+  if (threadIdx.x == 0) {
+    const double nw = sqrt(s);
+    nw_out[0] = nw;
+    if (nw == 0.0) S->pi_zero = 1;
+  }
+}
+
+__global__ void k_pi_scale(const Scalars* S, const double* w, const double* nw, double* v, int n) {
+  if (S->pi_zero) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = w[i] / nw[0];
+}
+
+// sigma_max, eta, initial primal weight
+__global__ void k_pi_final(Scalars* S, const double* partials, int ntiles, double eta_factor,
+                           const double* nb2, const double* nc2) {
+  __shared__ double s_tmp[32];
+  double s = 0.0;
+  if (!S->pi_zero) s = block_fold(partials, ntiles, false, s_tmp);
+  if (threadIdx.x == 0) {
+    const double smax = S->pi_zero ? 0.0 : sqrt(s);
+    S->sigma_max = smax;
+    S->eta = smax > 0.0 ? eta_factor / smax : 1.0;
+    S->nb_hat = sqrt(nb2[0]);
+    S->nc_hat = sqrt(nc2[0]);
+  }
+}
+
+// start of a phase: x (from x_start, or proj(0)), y = 0, sums = 0, restart point
+__global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double x0 = x_start ? x_start[i] : fmin(fmax(0.0, md.lhat[i]), md.uhat[i]);
+    w.x[i] = x0;
+    w.xbar[i] = x0;
+    w.x_r[i] = x0;
+    w.sum_x[i] = 0.0;
+  }
+  if (i < m) {
+    w.y[i] = 0.0;
+    w.y_r[i] = 0.0;
+    w.sum_y[i] = 0.0;
+  }
+}
+
+struct PhaseInit {
+  double eps_rel, beta_suff, beta_nec, beta_art, theta, time_limit_s, nb, nc;
+  long long max_iters, min_iters;
+  int check_period, phase, stop_rule;
+  int use_cc2;  // corner: primal weight from ||c_hat'|| (cc2[0]) and ||c'|| (cc2[1])
+};
+
+__global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
+  if (threadIdx.x != 0) return;
+  S->eps_rel = pi.eps_rel;
+  S->beta_suff = pi.beta_suff;
+  S->beta_nec = pi.beta_nec;
+  S->beta_art = pi.beta_art;
+  S->theta = pi.theta;
+  S->time_limit_s = pi.time_limit_s;
+  S->nb = pi.nb;
+  S->nc = pi.use_cc2 ? sqrt(cc2[1]) : pi.nc;
+  const double nch = pi.use_cc2 ? sqrt(cc2[0]) : S->nc_hat;
+  S->max_iters = pi.max_iters;
+  S->min_iters = pi.min_iters;
+  S->check_period = pi.check_period;
+  S->phase = pi.phase;
+  S->stop_rule = pi.stop_rule;
+  S->omega = (nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0;
+  S->tau = S->eta / S->omega;
+  S->sigma = S->eta * S->omega;
+  S->k = 0;
+  S->t = 0;
+  S->restarts = 0;
+  S->chunks = 0;
+  S->max_chunks = pi.max_iters / pi.check_period + 2;
+  S->done = 0;
+  S->status = PDHGC_STATUS_NONE;
+  S->chosen = 0;
+  S->restart_to = 0;
+  S->inv_t = 0.0;
+  S->at_check = 0;
+  S->at_limit = 0;
+  S->error = 0;
+  S->kkt_prev = INFINITY;
+  S->t0_ns = global_ns();
+}
+
+// after a chunk of iterations: iteration counters and 1/t for the averages
+__global__ void k_pre_check(Scalars* S) {
+  if (threadIdx.x != 0 || S->done) return;
+  long long run = S->max_iters - S->k;
+  if (run > S->check_period) run = S->check_period;
+  if (run < 0) run = 0;
+  S->k += run;
+  S->t += run;
+  S->inv_t = S->t > 0 ? 1.0 / (double)S->t : 0.0;
+  S->at_check = (S->k % S->check_period) == 0;
+  S->at_limit = S->k >= S->max_iters;
+  S->chunks += 1;
+  if (S->chunks > S->max_chunks) S->at_limit = 1;
+}
+
+// Fold the KKT partials, then: termination (Section 2 test, or the Section
+// 3.1 rule in the corner phase), limits, and the adaptive restart with the
+// primal-weight update.  mode 0: initial restart point only.
+__global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, const double* __restrict__ pT,
+                         int ntT, int mode, cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ double s_tmp[32];
+  __shared__ double q[22];
+  if (S->done) {
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  for (int qi = 0; qi < 10; ++qi) {
+    const double v = block_fold(pA + (size_t)qi * ntA, ntA, qi == 2 || qi == 7, s_tmp);
+    if (threadIdx.x == 0) q[qi] = v;
+    __syncthreads();
+  }
+  for (int qi = 0; qi < 12; ++qi) {
+    const double v = block_fold(pT + (size_t)qi * ntT, ntT, qi == 2 || qi == 8, s_tmp);
+    if (threadIdx.x == 0) q[10 + qi] = v;
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+
+  double nrp2[2], nrd2[2], gap[2], dx2[2], dy2[2];
+  const double om = S->omega;
+  for (int w = 0; w < 2; ++w) {
+    nrp2[w] = q[5 * w + 0];
+    const double rP2 = sqrt(q[5 * w + 1]);
+    const double by = q[5 * w + 3];
+    dy2[w] = q[5 * w + 4];
+    nrd2[w] = q[10 + 6 * w + 0];
+    const double rD2 = sqrt(q[10 + 6 * w + 1]);
+    const double cx = q[10 + 6 * w + 3];
+    const double bnd = q[10 + 6 * w + 4];
+    dx2[w] = q[10 + 6 * w + 5];
+    const double pobj = cx, dobj = by + bnd;
+    gap[w] = pobj - dobj;
+    S->kkt[w] = sqrt(om * nrp2[w] + nrd2[w] / om + gap[w] * gap[w]);
+    S->rP2[w] = rP2;
+    S->rel_p[w] = rP2 / (1.0 + S->nb);
+    S->rel_d[w] = rD2 / (1.0 + S->nc);
+    S->rel_gap[w] = fabs(gap[w]) / (1.0 + fabs(pobj) + fabs(dobj));
+    S->rel_kkt[w] = fmax(S->rel_p[w], fmax(S->rel_d[w], S->rel_gap[w]));
+  }
+  if (mode == 0) {
+    S->kkt_r = S->kkt[0];
+    S->kkt_prev = INFINITY;
+    return;
+  }
+  S->restart_to = 0;
+  const int pick = S->rel_kkt[1] <= S->rel_kkt[0] ? 1 : 0;
+  const double elapsed = (double)(global_ns() - S->t0_ns) * 1e-9;
+  const bool finite = isfinite(S->kkt[0]) && isfinite(S->kkt[1]);
+  if (S->phase == 0) {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_NUMERICAL; S->chosen = 0;
+    } else if (S->at_check && fmin(S->rel_kkt[0], S->rel_kkt[1]) <= S->eps_rel) {
+      S->done = 1; S->status = PDHGC_STATUS_OPTIMAL; S->chosen = pick;
+    } else if (S->at_limit) {
+      S->done = 1; S->status = PDHGC_STATUS_ITER_LIMIT; S->chosen = pick;
+    } else if (elapsed > S->time_limit_s) {
+      S->done = 1; S->status = PDHGC_STATUS_TIME_LIMIT; S->chosen = pick;
+    }
+  } else {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 0;
+    } else if (S->at_check && S->k >= S->min_iters) {
+      const double tol = S->eps_rel * (1.0 + S->nb);
+      if (S->stop_rule == 1) {
+        if (fmin(S->rel_kkt[0], S->rel_kkt[1]) <= S->eps_rel) {
+          S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = pick;
+        }
+      } else if (S->rP2[0] <= tol) {
+        S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 0;
+      } else if (S->rP2[1] <= tol) {
+        S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 1;
+      }
+    }
+    if (!S->done && (S->at_limit || elapsed > S->time_limit_s)) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 0;
+    }
+  }
+  if (!S->done) {
+    const int c = S->kkt[1] <= S->kkt[0] ? 1 : 0;
+    const double kc = S->kkt[c];
+    const bool restart = kc <= S->beta_suff * S->kkt_r ||
+                         (kc <= S->beta_nec * S->kkt_r && kc > S->kkt_prev) ||
+                         (double)S->t >= S->beta_art * (double)S->k;
+    if (!restart) {
+      S->kkt_prev = kc;
+    } else {
+      const double dx = sqrt(dx2[c]), dy = sqrt(dy2[c]);
+      double omega = S->omega;
+      if (dx > 1e-10 && dy > 1e-10)
+        omega = exp(S->theta * log(dy / dx) + (1.0 - S->theta) * log(omega));
+      S->omega = omega;
+      S->kkt_r = sqrt(omega * nrp2[c] + nrd2[c] / omega + gap[c] * gap[c]);
+      S->kkt_prev = INFINITY;
+      S->t = 0;
+      S->restarts += 1;
+      S->restart_to = c ? 2 : 1;
+      S->tau = S->eta / omega;
+      S->sigma = S->eta * omega;
+    }
+  }
+  S->t1_ns = global_ns();
+  if (use_handle) cudaGraphSetConditional(h, S->done ? 0u : 1u);
+}
+
+// restart: jump to the candidate, new restart point, sums cleared
+__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w) {
+  const int rt = S->restart_to;
+  if (rt == 0 || S->done) return;
+  const double inv_t = S->inv_t;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double xn = rt == 2 ? w.sum_x[i] * inv_t : w.x[i];
+    w.x[i] = xn;
+    w.x_r[i] = xn;
+    w.sum_x[i] = 0.0;
+  }
+  if (i < m) {
+    const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
+    w.y[i] = yn;
+    w.y_r[i] = yn;
+    w.sum_y[i] = 0.0;
+  }
+}
+
+// end of a phase: the returned point (current or average; the phase-1 x on a
+// corner limit)
+__global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo, double* yo,
+                           const double* x_fallback) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool avg = S->chosen == 1 && S->t > 0;
+  const double inv_t = S->inv_t;
+  const bool fallback = x_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
+  if (i < n) xo[i] = fallback ? x_fallback[i] : (avg ? w.sum_x[i] * inv_t : w.x[i]);
+  if (yo && i < m) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
+}
+
+__global__ void k_corner_rows(int m, const int8_t* ge, const double* Dr, const double* y1, double eps_abs,
+                              int8_t* ge_c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) ge_c[i] = (ge[i] && !(fabs(Dr[i] * y1[i]) > eps_abs)) ? 1 : 0;
+}
+
+__global__ void k_report_final(const double* __restrict__ pR, int ntA, const double* __restrict__ pC, int ntT,
+                               double nb, double nc, DevReport* out) {
+  __shared__ double s_tmp[32];
+  __shared__ double q[15];
+  for (int qi = 0; qi < 7; ++qi) {
+    const double v = block_fold(pR + (size_t)qi * ntA, ntA, qi == 2, s_tmp);
+    if (threadIdx.x == 0) q[qi] = v;
+    __syncthreads();
+  }
+  for (int qi = 0; qi < 8; ++qi) {
+    const double v = block_fold(pC + (size_t)qi * ntT, ntT, qi == 2, s_tmp);
+    if (threadIdx.x == 0) q[7 + qi] = v;
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  DevReport r;
+  r.rP2 = sqrt(q[1]);
+  r.rPinf = q[2];
+  r.rD2 = sqrt(q[8]);
+  r.rDinf = q[9];
+  r.pobj = q[10];
+  r.dobj = q[3] + q[11];
+  r.gap = r.pobj - r.dobj;
+  r.rel_p = r.rP2 / (1.0 + nb);
+  r.rel_d = r.rD2 / (1.0 + nc);
+  r.rel_gap = fabs(r.gap) / (1.0 + fabs(r.pobj) + fabs(r.dobj));
+  r.rel_kkt = fmax(r.rel_p, fmax(r.rel_d, r.rel_gap));
+  r.p = q[4] + q[12];
+  r.d = q[5] + q[13];
+  r.cand = q[6] + q[14];
+  *out = r;
+}
+
+// reduced costs of the original model, z = proj(c_hat - A_hat' y) / D_c
+struct ZOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const double* __restrict__ y;
+  DevModel md;
+  double* __restrict__ z;
+  __device__ bool skip() const { return false; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double*) const {
+    z[j] = proj_dual(md.chat[j] - a.v[0], md.lhat[j], md.uhat[j]) / md.Dc[j];
+  }
+};
+
+// out_user[perm[i]] = a[i] * f1[i] * f2[i] (f1, f2 optional)
+__global__ void k_unpermute(int len, const int* perm, const double* a, const double* f1, const double* f2,
+                            double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  double v = a[i];
+  if (f1) v = f1[i] * v;
+  if (f2) v = f2[i] * v;
+  out[perm[i]] = v;
+}
+
+__global__ void k_uniform(unsigned long long seed, long long n, double scale, double* out) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = scale * splitmix_uniform(seed, (unsigned long long)j);
+}
+
+// folds two partial rows (q = 0, 1) of `p` into out[0], out[1]
+__global__ void k_fold2(const double* __restrict__ p, int nt, double* out) {
+  __shared__ double s_tmp[32];
+  const double a = block_fold(p, nt, false, s_tmp);
+  __syncthreads();
+  const double b = block_fold(p + nt, nt, false, s_tmp);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+__global__ void k_fill_scaled(double* v, int n, double a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = v[i] * a;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The handle
+// ---------------------------------------------------------------------------
+struct pdhgc_lp {
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<void*> allocs;
+  int64_t launches = 0;
+
+  // matrix (internal numbering)
+  int *A_rp = nullptr, *A_col = nullptr, *T_rp = nullptr, *T_col = nullptr;
+  double *A_val = nullptr, *T_val = nullptr, *A_hat = nullptr, *T_hat = nullptr;
+  Tile *A_tiles = nullptr, *T_tiles = nullptr;
+  int ntA = 0, ntT = 0;
+  // vectors (internal order)
+  double *b_int = nullptr, *sign = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
+  int8_t* ge = nullptr;
+  double *Dr = nullptr, *Dc = nullptr, *bhat = nullptr, *chat = nullptr, *lhat = nullptr, *uhat = nullptr;
+  double *rfac = nullptr, *cfac = nullptr;
+  int *row_perm = nullptr, *col_perm = nullptr;
+  // iterates
+  DevIter it{};
+  double *x1 = nullptr, *y1 = nullptr, *xc = nullptr;
+  double *chat_c = nullptr, *lhat_c = nullptr, *uhat_c = nullptr;
+  int8_t* ge_c = nullptr;
+  double *pi_v = nullptr, *pi_w = nullptr, *pi_u = nullptr, *tmp_n = nullptr, *tmp_m = nullptr;
+  double *pA = nullptr, *pT = nullptr, *scratch = nullptr;
+  Scalars* S = nullptr;
+  DevReport* rep = nullptr;
+  double b_norm = 0.0, c_norm = 0.0;
+  bool have_phase1 = false, have_corner = false;
+  pdhgc_report rep1{}, repc{};
+  pdhgc_params params{};
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    void* q = nullptr;
+    const size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+      return set_err(PDHGC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PDHGC_OK;
+  }
+  ~pdhgc_lp() {
+    for (void* q : allocs) cudaFree(q);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+namespace {
+
+inline int grid_for(long long n, int block = 256) { return (int)((n + block - 1) / block); }
+
+template <class Op>
+int launch_tiles(pdhgc_lp* lp, bool transposed, const double* val, const Op& op, double* partials,
+                 cudaStream_t st) {
+  const int nt = transposed ? lp->ntT : lp->ntA;
+  if (nt == 0) return PDHGC_OK;
+  tile_spmv<Op><<<nt, kBlock, 0, st>>>(transposed ? lp->T_tiles : lp->A_tiles, nt,
+                                       transposed ? lp->T_rp : lp->A_rp, transposed ? lp->T_col : lp->A_col,
+                                       val, op, partials);
+  lp->launches++;
+  CKL();
+  return PDHGC_OK;
+}
+
+DevModel model_orig(const pdhgc_lp* lp) {
+  return DevModel{lp->chat, lp->lhat, lp->uhat, lp->bhat, lp->Dr, lp->Dc, lp->ge};
+}
+DevModel model_corner(const pdhgc_lp* lp) {
+  return DevModel{lp->chat_c, lp->lhat_c, lp->uhat_c, lp->bhat, lp->Dr, lp->Dc, lp->ge_c};
+}
+
+#define RET(x)                 \
+  do {                         \
+    int r_ = (x);              \
+    if (r_ != PDHGC_OK) return r_; \
+  } while (0)
+
+// a0: Ruiz + Pock-Chambolle scaling, scaled copies, power iteration
+int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
+  cudaStream_t st = lp->stream;
+  const int m = lp->m, n = lp->n;
+  k_fill<<<grid_for(m), 256, 0, st>>>(lp->Dr, m, 1.0);
+  k_fill<<<grid_for(n), 256, 0, st>>>(lp->Dc, n, 1.0);
+  lp->launches += 2;
+  CKL();
+  for (int pass = 0; pass < p.ruiz_iters; ++pass) {
+    RET(launch_tiles(lp, false, lp->A_val, ScaleMaxOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
+    RET(launch_tiles(lp, true, lp->T_val, ScaleMaxOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
+    k_mul_inplace<<<grid_for(m), 256, 0, st>>>(lp->Dr, lp->rfac, m);
+    k_mul_inplace<<<grid_for(n), 256, 0, st>>>(lp->Dc, lp->cfac, n);
+    lp->launches += 2;
+    CKL();
+  }
+  RET(launch_tiles(lp, false, lp->A_val, ScaleSumOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
+  RET(launch_tiles(lp, true, lp->T_val, ScaleSumOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
+  k_mul_inplace<<<grid_for(m), 256, 0, st>>>(lp->Dr, lp->rfac, m);
+  k_mul_inplace<<<grid_for(n), 256, 0, st>>>(lp->Dc, lp->cfac, n);
+  k_scale_values<<<grid_for((long long)m * 32), 256, 0, st>>>(lp->A_rp, lp->A_col, lp->A_val, lp->A_hat, m,
+                                                              lp->Dr, lp->Dc, 0);
+  k_scale_values<<<grid_for((long long)n * 32), 256, 0, st>>>(lp->T_rp, lp->T_col, lp->T_val, lp->T_hat, n,
+                                                              lp->Dr, lp->Dc, 1);
+  k_scale_vectors<<<grid_for(m > n ? m : n), 256, 0, st>>>(m, n, lp->Dr, lp->Dc, lp->b_int, lp->c, lp->l,
+                                                            lp->u, lp->bhat, lp->chat, lp->lhat, lp->uhat);
+  k_norm2<<<1, 1024, 0, st>>>(lp->bhat, m, lp->scratch + 0);
+  k_norm2<<<1, 1024, 0, st>>>(lp->chat, n, lp->scratch + 1);
+  lp->launches += 7;
+  CKL();
+  // power iteration on A_hat' A_hat from v = 1/sqrt(n)
+  CK(cudaMemsetAsync(&lp->S->pi_zero, 0, sizeof(int), st));
+  k_fill<<<grid_for(n), 256, 0, st>>>(lp->pi_v, n, 1.0 / std::sqrt((double)n));
+  lp->launches++;
+  for (int k = 0; k < p.power_iters; ++k) {
+    RET(launch_tiles(lp, false, lp->A_hat, SpmvOp<false>{lp->S, lp->pi_v, lp->pi_u}, nullptr, st));
+    RET(launch_tiles(lp, true, lp->T_hat, SpmvOp<true>{lp->S, lp->pi_u, lp->pi_w}, lp->pT, st));
+    k_pi_norm<<<1, 1024, 0, st>>>(lp->S, lp->pT, lp->ntT, lp->scratch + 2);
+    k_pi_scale<<<grid_for(n), 256, 0, st>>>(lp->S, lp->pi_w, lp->scratch + 2, lp->pi_v, n);
+    lp->launches += 2;
+    CKL();
+  }
+  RET(launch_tiles(lp, false, lp->A_hat, SpmvOp<true>{lp->S, lp->pi_v, lp->pi_u}, lp->pA, st));
+  k_pi_final<<<1, 1024, 0, st>>>(lp->S, lp->pA, lp->ntA, p.eta_factor, lp->scratch + 0, lp->scratch + 1);
+  lp->launches++;
+  CKL();
+  return PDHGC_OK;
+}
+
+// the KKT evaluation of the current and average points (two matrix passes)
+int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st) {
+  const DevIter& w = lp->it;
+  RET(launch_tiles(lp, false, lp->A_hat, EvalRowsOp{lp->S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, lp->pA, st));
+  RET(launch_tiles(lp, true, lp->T_hat, EvalColsOp{lp->S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, lp->pT, st));
+  return PDHGC_OK;
+}
+
+// Runs one phase: init, the device-driven loop graph, finalize.
+int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const double* x_start, const double* cc2,
+              double* xo, double* yo, const double* x_fallback) {
+  cudaStream_t st = lp->stream;
+  const int n = lp->n, m = lp->m;
+  const int gnm = grid_for(n > m ? n : m);
+  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start);
+  k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
+  lp->launches += 2;
+  CKL();
+  RET(launch_eval(lp, md, st));
+  k_decide<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+  lp->launches++;
+  CKL();
+
+  // the loop: while (!done) { P iterations; pre-check; eval; decide; restart }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  std::unique_ptr<CUgraph_st, void (*)(cudaGraph_t)> g_guard(graph, [](cudaGraph_t g) { cudaGraphDestroy(g); });
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = lp->cap_stream;
+  CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = lp->launches;
+  int rc = PDHGC_OK;
+  for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
+    rc = launch_tiles(lp, true, lp->T_hat, PrimalOp{lp->S, i, lp->it.y, md, lp->it}, nullptr, cs);
+    if (rc == PDHGC_OK)
+      rc = launch_tiles(lp, false, lp->A_hat, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs);
+  }
+  if (rc == PDHGC_OK) {
+    k_pre_check<<<1, 32, 0, cs>>>(lp->S);
+    lp->launches++;
+    rc = launch_eval(lp, md, cs);
+  }
+  if (rc == PDHGC_OK) {
+    k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
+    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it);
+    lp->launches += 2;
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+  const int64_t per_body = lp->launches - before;
+  lp->launches = before;  // counted per executed body below
+  if (rc != PDHGC_OK) return rc;
+  if (ce != cudaSuccess) return set_err(PDHGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+  CK(cudaGraphInstantiate(&exec, graph, 0));
+  std::unique_ptr<CUgraphExec_st, void (*)(cudaGraphExec_t)> e_guard(exec,
+                                                                    [](cudaGraphExec_t e) { cudaGraphExecDestroy(e); });
+  CK(cudaGraphLaunch(exec, st));
+  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback);
+  lp->launches++;
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  long long chunks = 0;
+  CK(cudaMemcpy(&chunks, &lp->S->chunks, sizeof(chunks), cudaMemcpyDeviceToHost));
+  lp->launches += chunks * per_body;
+  return PDHGC_OK;
+}
+
+int run_report(pdhgc_lp* lp, const double* x, const double* y, pdhgc_report* out) {
+  cudaStream_t st = lp->stream;
+  DevModel md = model_orig(lp);
+  RET(launch_tiles(lp, false, lp->A_hat, ReportRowsOp{x, y, md, 1e-6}, lp->pA, st));
+  RET(launch_tiles(lp, true, lp->T_hat, ReportColsOp{y, x, lp->l, lp->u, md, 1e-6}, lp->pT, st));
+  k_report_final<<<1, 256, 0, st>>>(lp->pA, lp->ntA, lp->pT, lp->ntT, lp->b_norm, lp->c_norm, lp->rep);
+  lp->launches++;
+  CKL();
+  DevReport r;
+  CK(cudaMemcpyAsync(&r, lp->rep, sizeof(r), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  out->rP2 = r.rP2;
+  out->rD2 = r.rD2;
+  out->rPinf = r.rPinf;
+  out->rDinf = r.rDinf;
+  out->pobj = r.pobj;
+  out->dobj = r.dobj;
+  out->gap = r.gap;
+  out->rel_p = r.rel_p;
+  out->rel_d = r.rel_d;
+  out->rel_gap = r.rel_gap;
+  out->rel_kkt = r.rel_kkt;
+  const int64_t m = lp->m;
+  out->off_bound_p = (int64_t)llround(r.p);
+  out->zero_rc_d = (int64_t)llround(r.d);
+  out->candidates = (int64_t)llround(r.cand);
+  out->corner_measure = out->candidates > m ? out->candidates - m : 0;
+  out->primal_push_est = out->off_bound_p > m ? out->off_bound_p - m : 0;
+  out->dual_push_est = m > out->zero_rc_d ? m - out->zero_rc_d : 0;
+  const int64_t thr = 2 * m > 100000 ? 2 * m : 100000;
+  out->should_corner = out->candidates >= thr ? 1 : 0;
+  return PDHGC_OK;
+}
+
+int fill_phase_report(pdhgc_lp* lp, pdhgc_report* r) {
+  Scalars S;
+  CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));
+  r->status = S.status;
+  r->chosen = S.chosen;
+  r->iters = S.k;
+  r->restarts = S.restarts;
+  r->seconds = (double)(S.t1_ns - S.t0_ns) * 1e-9;
+  r->omega = S.omega;
+  r->eta = S.eta;
+  r->sigma_max = S.sigma_max;
+  r->precision = lp->params.precision;
+  return PDHGC_OK;
+}
+
+int check_params(const pdhgc_params* p) {
+  if (!p) return PDHGC_ERR_INVALID_ARG;
+  if (p->max_iters < 1 || p->check_period < 1 || p->check_period > 4096 || p->ruiz_iters < 0 ||
+      p->ruiz_iters > 100 || p->power_iters < 1 || p->power_iters > 10000 || !(p->eta_factor > 0.0) ||
+      !(p->eta_factor < 1.0) || !(p->time_limit_s > 0.0) || !(p->theta >= 0.0 && p->theta <= 1.0))
+    return set_err(PDHGC_ERR_INVALID_ARG, "parameter out of range");
+  if (p->precision != PDHGC_FP64)
+    return set_err(PDHGC_ERR_INVALID_ARG, "precision not supported by this build");
+  return PDHGC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void pdhgc_default_params(pdhgc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps_rel = 1e-6;
+  p->max_iters = 1000000;
+  p->time_limit_s = 3600.0;
+  p->check_period = 64;
+  p->beta_suff = 0.2;
+  p->beta_nec = 0.8;
+  p->beta_art = 0.36;
+  p->theta = 0.5;
+  p->eta_factor = 0.998;
+  p->ruiz_iters = 10;
+  p->power_iters = 100;
+  p->precision = PDHGC_FP64;
+}
+
+void pdhgc_default_corner_params(pdhgc_corner_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps_abs = 1e-6;
+  p->eps_rel = 1e-6;
+  p->min_iters = 100;
+  p->max_iters = 1000000;
+  p->time_limit_s = 3600.0;
+  p->obj_seed = 0;
+  p->obj_scale = 1.0;
+  p->stop_rule = 0;
+}
+
+int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                    const int32_t* col_idx, const double* val, const double* b, const double* c,
+                    const double* lb, const double* ub, const int8_t* sense, int inputs_on_device,
+                    void* cuda_stream) {
+  if (!out) return set_err(PDHGC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (inputs_on_device != 0 && inputs_on_device != 1)
+    return set_err(PDHGC_ERR_INVALID_ARG, "inputs_on_device must be 0 or 1");
+  if (m < 1 || n < 1 || nnz < 0) return set_err(PDHGC_ERR_INVALID_ARG, "m and n must be >= 1, nnz >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // host copies for validation and layout
+  std::vector<int64_t> h_rp;
+  std::vector<int32_t> h_col;
+  std::vector<double> h_val, h_b, h_c, h_l, h_u;
+  std::vector<int8_t> h_s;
+  if (inputs_on_device) {
+    if (!row_ptr || !b || !c || (nnz > 0 && (!col_idx || !val)))
+      return set_err(PDHGC_ERR_INVALID_ARG, "NULL array argument");
+    h_rp.resize((size_t)m + 1);
+    h_col.resize((size_t)nnz);
+    h_val.resize((size_t)nnz);
+    h_b.resize(m);
+    h_c.resize(n);
+    CK(cudaMemcpyAsync(h_rp.data(), row_ptr, h_rp.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (nnz > 0) {
+      CK(cudaMemcpyAsync(h_col.data(), col_idx, (size_t)nnz * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(h_val.data(), val, (size_t)nnz * 8, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(h_b.data(), b, (size_t)m * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_c.data(), c, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    if (lb) {
+      h_l.resize(n);
+      CK(cudaMemcpyAsync(h_l.data(), lb, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (ub) {
+      h_u.resize(n);
+      CK(cudaMemcpyAsync(h_u.data(), ub, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (sense) {
+      h_s.resize(m);
+      CK(cudaMemcpyAsync(h_s.data(), sense, (size_t)m, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    row_ptr = h_rp.data();
+    col_idx = h_col.data();
+    val = h_val.data();
+    b = h_b.data();
+    c = h_c.data();
+    lb = lb ? h_l.data() : nullptr;
+    ub = ub ? h_u.data() : nullptr;
+    sense = sense ? h_s.data() : nullptr;
+  }
+  Prepared P;
+  std::string detail;
+  int rc = prepare_lp(P, m, n, nnz, row_ptr, col_idx, val, b, c, lb, ub, sense, detail);
+  if (rc != PDHGC_OK) return set_err(rc, detail);
+
+  std::unique_ptr<pdhgc_lp> lp(new pdhgc_lp());
+  lp->m = m;
+  lp->n = n;
+  lp->nnz = nnz;
+  lp->stream = st;
+  lp->b_norm = P.b_norm;
+  lp->c_norm = P.c_norm;
+  CK(cudaStreamCreateWithFlags(&lp->cap_stream, cudaStreamNonBlocking));
+  const size_t nz = (size_t)nnz;
+  lp->ntA = (int)P.A.tiles.size();
+  lp->ntT = (int)P.AT.tiles.size();
+  const int ntmax = lp->ntA > lp->ntT ? lp->ntA : lp->ntT;
+  RET(lp->alloc(&lp->A_rp, m + 1));
+  RET(lp->alloc(&lp->A_col, nz));
+  RET(lp->alloc(&lp->A_val, nz));
+  RET(lp->alloc(&lp->A_hat, nz));
+  RET(lp->alloc(&lp->T_rp, n + 1));
+  RET(lp->alloc(&lp->T_col, nz));
+  RET(lp->alloc(&lp->T_val, nz));
+  RET(lp->alloc(&lp->T_hat, nz));
+  RET(lp->alloc(&lp->A_tiles, lp->ntA));
+  RET(lp->alloc(&lp->T_tiles, lp->ntT));
+  RET(lp->alloc(&lp->b_int, m));
+  RET(lp->alloc(&lp->sign, m));
+  RET(lp->alloc(&lp->ge, m));
+  RET(lp->alloc(&lp->ge_c, m));
+  RET(lp->alloc(&lp->c, n));
+  RET(lp->alloc(&lp->l, n));
+  RET(lp->alloc(&lp->u, n));
+  RET(lp->alloc(&lp->Dr, m));
+  RET(lp->alloc(&lp->Dc, n));
+  RET(lp->alloc(&lp->bhat, m));
+  RET(lp->alloc(&lp->chat, n));
+  RET(lp->alloc(&lp->lhat, n));
+  RET(lp->alloc(&lp->uhat, n));
+  RET(lp->alloc(&lp->rfac, m));
+  RET(lp->alloc(&lp->cfac, n));
+  RET(lp->alloc(&lp->row_perm, m));
+  RET(lp->alloc(&lp->col_perm, n));
+  RET(lp->alloc(&lp->it.x, n));
+  RET(lp->alloc(&lp->it.xbar, n));
+  RET(lp->alloc(&lp->it.sum_x, n));
+  RET(lp->alloc(&lp->it.x_r, n));
+  RET(lp->alloc(&lp->it.y, m));
+  RET(lp->alloc(&lp->it.sum_y, m));
+  RET(lp->alloc(&lp->it.y_r, m));
+  RET(lp->alloc(&lp->x1, n));
+  RET(lp->alloc(&lp->y1, m));
+  RET(lp->alloc(&lp->xc, n));
+  RET(lp->alloc(&lp->chat_c, n));
+  RET(lp->alloc(&lp->lhat_c, n));
+  RET(lp->alloc(&lp->uhat_c, n));
+  RET(lp->alloc(&lp->pi_v, n));
+  RET(lp->alloc(&lp->pi_w, n));
+  RET(lp->alloc(&lp->pi_u, m));
+  RET(lp->alloc(&lp->tmp_n, n));
+  RET(lp->alloc(&lp->tmp_m, m));
+  RET(lp->alloc(&lp->pA, (size_t)16 * (lp->ntA > 0 ? lp->ntA : 1)));
+  RET(lp->alloc(&lp->pT, (size_t)16 * (lp->ntT > 0 ? lp->ntT : 1)));
+  RET(lp->alloc(&lp->scratch, 64));
+  RET(lp->alloc(&lp->S, 1));
+  RET(lp->alloc(&lp->rep, 1));
+  (void)ntmax;
+  CK(cudaMemcpyAsync(lp->A_rp, P.A.row_ptr.data(), (m + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->T_rp, P.AT.row_ptr.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (nz) {
+    CK(cudaMemcpyAsync(lp->A_col, P.A.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->A_val, P.A.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->T_col, P.AT.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->T_val, P.AT.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(lp->A_tiles, P.A.tiles.data(), lp->ntA * sizeof(Tile), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->T_tiles, P.AT.tiles.data(), lp->ntT * sizeof(Tile), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->b_int, P.b_int.data(), (size_t)m * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->sign, P.sign.data(), (size_t)m * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->ge, P.ge.data(), (size_t)m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->c, P.c.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->l, P.l.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->u, P.u.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->row_perm, P.row_perm.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->col_perm, P.col_perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(lp->S, 0, sizeof(Scalars), st));
+  CK(cudaStreamSynchronize(st));  // the host vectors of P go out of scope
+  pdhgc_default_params(&lp->params);
+  *out = lp.release();
+  return PDHGC_OK;
+}
+
+int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out) {
+  if (!lp) return set_err(PDHGC_ERR_INVALID_ARG, "lp is NULL");
+  pdhgc_params p;
+  if (params) p = *params; else pdhgc_default_params(&p);
+  RET(check_params(&p));
+  lp->params = p;
+  lp->have_phase1 = false;
+  lp->have_corner = false;
+  RET(setup_scaling(lp, p));
+  PhaseInit pi{};
+  pi.eps_rel = p.eps_rel;
+  pi.beta_suff = p.beta_suff;
+  pi.beta_nec = p.beta_nec;
+  pi.beta_art = p.beta_art;
+  pi.theta = p.theta;
+  pi.time_limit_s = p.time_limit_s;
+  pi.nb = lp->b_norm;
+  pi.nc = lp->c_norm;
+  pi.max_iters = p.max_iters;
+  pi.min_iters = 0;
+  pi.check_period = p.check_period;
+  pi.phase = 0;
+  pi.stop_rule = 0;
+  pi.use_cc2 = 0;
+  RET(run_phase(lp, model_orig(lp), pi, nullptr, nullptr, lp->x1, lp->y1, nullptr));
+  pdhgc_report r{};
+  RET(fill_phase_report(lp, &r));
+  RET(run_report(lp, lp->x1, lp->y1, &r));
+  lp->rep1 = r;
+  lp->have_phase1 = true;
+  if (out) *out = r;
+  return PDHGC_OK;
+}
+
+int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_report* out) {
+  if (!lp) return set_err(PDHGC_ERR_INVALID_ARG, "lp is NULL");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
+  pdhgc_corner_params cp;
+  if (params) cp = *params; else pdhgc_default_corner_params(&cp);
+  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
+    return set_err(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  lp->have_corner = false;
+  cudaStream_t st = lp->stream;
+  const DevModel md = model_orig(lp);
+  // Algorithm 1: new bounds and objective (columns), new senses (rows)
+  RET(launch_tiles(lp, true, lp->T_hat,
+                   CornerColsOp{lp->y1, lp->x1, lp->col_perm, md, lp->lhat_c, lp->uhat_c, lp->chat_c, cp.eps_abs,
+                                cp.obj_scale, (unsigned long long)cp.obj_seed},
+                   lp->pT, st));
+  k_corner_rows<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->ge, lp->Dr, lp->y1, cp.eps_abs, lp->ge_c);
+  lp->launches++;
+  CKL();
+  k_fold2<<<1, 256, 0, st>>>(lp->pT, lp->ntT, lp->scratch + 8);
+  lp->launches++;
+  CKL();
+  const pdhgc_params& p = lp->params;
+  PhaseInit pi{};
+  pi.eps_rel = cp.eps_rel;
+  pi.beta_suff = p.beta_suff;
+  pi.beta_nec = p.beta_nec;
+  pi.beta_art = p.beta_art;
+  pi.theta = p.theta;
+  pi.time_limit_s = cp.time_limit_s;
+  pi.nb = lp->b_norm;
+  pi.nc = 0.0;
+  pi.max_iters = cp.max_iters;
+  pi.min_iters = cp.min_iters;
+  pi.check_period = p.check_period;
+  pi.phase = 1;
+  pi.stop_rule = cp.stop_rule;
+  pi.use_cc2 = 1;
+  RET(run_phase(lp, model_corner(lp), pi, lp->x1, lp->scratch + 8, lp->xc, nullptr, lp->x1));
+  pdhgc_report r{};
+  RET(fill_phase_report(lp, &r));
+  RET(run_report(lp, lp->xc, lp->y1, &r));
+  lp->repc = r;
+  lp->have_corner = true;
+  if (out) *out = r;
+  return PDHGC_OK;
+}
+
+int pdhgc_kkt_report(pdhgc_lp* lp, int which, pdhgc_report* out) {
+  if (!lp || !out || (which != PDHGC_PHASE1 && which != PDHGC_CORNER))
+    return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
+  if (which == PDHGC_CORNER && !lp->have_corner) return set_err(PDHGC_ERR_NO_CORNER, "no corner result");
+  pdhgc_report r = which == PDHGC_PHASE1 ? lp->rep1 : lp->repc;
+  RET(run_report(lp, which == PDHGC_PHASE1 ? lp->x1 : lp->xc, lp->y1, &r));
+  *out = r;
+  return PDHGC_OK;
+}
+
+static int copy_out(pdhgc_lp* lp, double* dst, const double* dev_user, size_t count, int on_device) {
+  CK(cudaMemcpyAsync(dst, dev_user, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     lp->stream));
+  return PDHGC_OK;
+}
+
+int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z, int on_device) {
+  if (!lp || (which != PDHGC_PHASE1 && which != PDHGC_CORNER) || (on_device != 0 && on_device != 1))
+    return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
+  if (which == PDHGC_CORNER && !lp->have_corner) return set_err(PDHGC_ERR_NO_CORNER, "no corner result");
+  cudaStream_t st = lp->stream;
+  const int m = lp->m, n = lp->n;
+  if (x) {
+    k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, which == PDHGC_PHASE1 ? lp->x1 : lp->xc, lp->Dc,
+                                            nullptr, lp->tmp_n);
+    lp->launches++;
+    CKL();
+    RET(copy_out(lp, x, lp->tmp_n, n, on_device));
+  }
+  if (y) {
+    k_unpermute<<<grid_for(m), 256, 0, st>>>(m, lp->row_perm, lp->y1, lp->Dr, lp->sign, lp->tmp_m);
+    lp->launches++;
+    CKL();
+    RET(copy_out(lp, y, lp->tmp_m, m, on_device));
+  }
+  if (z) {
+    // the unpermute below reads pi_w; the stream orders it after the ZOp pass
+    RET(launch_tiles(lp, true, lp->T_hat, ZOp{lp->y1, model_orig(lp), lp->pi_w}, nullptr, st));
+    k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, lp->pi_w, nullptr, nullptr, lp->tmp_n);
+    lp->launches++;
+    CKL();
+    RET(copy_out(lp, z, lp->tmp_n, n, on_device));
+  }
+  CK(cudaStreamSynchronize(st));
+  return PDHGC_OK;
+}
+
+int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double* y_avg, int64_t* iters_out,
+                       int on_device) {
+  if (!lp || (on_device != 0 && on_device != 1)) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = lp->stream;
+  const int m = lp->m, n = lp->n;
+  Scalars S;
+  CK(cudaMemcpyAsync(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double inv_t = S.t > 0 ? 1.0 / (double)S.t : 0.0;
+  struct V {
+    double* dst;
+    const double* src;
+    const int* perm;
+    int len;
+    double scale;
+  } vs[4] = {{x, lp->it.x, lp->col_perm, n, 1.0},
+             {y, lp->it.y, lp->row_perm, m, 1.0},
+             {x_avg, lp->it.sum_x, lp->col_perm, n, inv_t},
+             {y_avg, lp->it.sum_y, lp->row_perm, m, inv_t}};
+  for (const V& v : vs) {
+    if (!v.dst) continue;
+    double* tmp = v.len == n ? lp->tmp_n : lp->tmp_m;
+    if (v.len == n && v.len == m && v.perm == lp->row_perm) tmp = lp->tmp_m;
+    k_unpermute<<<grid_for(v.len), 256, 0, st>>>(v.len, v.perm, v.src, nullptr, nullptr, tmp);
+    lp->launches++;
+    CKL();
+    if (v.scale != 1.0) {
+      k_fill_scaled<<<grid_for(v.len), 256, 0, st>>>(tmp, v.len, v.scale);
+      lp->launches++;
+      CKL();
+    }
+    RET(copy_out(lp, v.dst, tmp, v.len, on_device));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (iters_out) {
+    iters_out[0] = S.k;
+    iters_out[1] = S.t;
+    iters_out[2] = S.restarts;
+  }
+  return PDHGC_OK;
+}
+
+int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalars, int on_device) {
+  if (!lp || (on_device != 0 && on_device != 1)) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = lp->stream;
+  if (d_row) {
+    k_unpermute<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->row_perm, lp->Dr, nullptr, nullptr, lp->tmp_m);
+    lp->launches++;
+    CKL();
+    RET(copy_out(lp, d_row, lp->tmp_m, lp->m, on_device));
+  }
+  if (d_col) {
+    k_unpermute<<<grid_for(lp->n), 256, 0, st>>>(lp->n, lp->col_perm, lp->Dc, nullptr, nullptr, lp->tmp_n);
+    lp->launches++;
+    CKL();
+    RET(copy_out(lp, d_col, lp->tmp_n, lp->n, on_device));
+  }
+  CK(cudaStreamSynchronize(st));
+  if (scalars) {
+    Scalars S;
+    CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));
+    const double v[5] = {S.sigma_max, S.eta, S.omega, S.tau, S.sigma};
+    if (on_device) {
+      CK(cudaMemcpy(scalars, v, sizeof(v), cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(scalars, v, sizeof(v));
+    }
+  }
+  return PDHGC_OK;
+}
+
+int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && !out)) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  if (n == 0) return PDHGC_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  k_uniform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((unsigned long long)seed, (long long)n, obj_scale, out);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  return PDHGC_OK;
+}
+
+int64_t pdhgc_kernel_launches(const pdhgc_lp* lp) { return lp ? lp->launches : 0; }
+
+void pdhgc_lp_destroy(pdhgc_lp* lp) {
+  if (!lp) return;
+  cudaStreamSynchronize(lp->stream);
+  delete lp;
+}
+
+const char* pdhgc_strerror(int code) {
+  switch (code) {
+    case PDHGC_OK: return "ok";
+    case PDHGC_ERR_INVALID_ARG: return "invalid argument";
+    case PDHGC_ERR_INVALID_CSR: return "invalid CSR structure";
+    case PDHGC_ERR_NONFINITE: return "non-finite input";
+    case PDHGC_ERR_BOUNDS: return "lower bound above upper bound";
+    case PDHGC_ERR_CUDA: return "CUDA error";
+    case PDHGC_ERR_OOM: return "out of memory";
+    case PDHGC_ERR_NO_PHASE1: return "no phase-1 solution";
+    case PDHGC_ERR_NO_CORNER: return "no corner solution";
+    case PDHGC_ERR_TOO_LARGE: return "problem too large";
+    case PDHGC_ERR_DEVICE: return "device-side check failed";
+    case PDHGC_ERR_BUFFER: return "buffer too small";
+    default: return "unknown error";
+  }
+}
+
+const char* pdhgc_last_error_detail(void) { return g_detail.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+"""Python binding of libpdhgc (include/pdhgc.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module
+converts arrays to pointers, fills the C parameter structs and turns
+reports into dicts.  PyTorch supplies device memory and the CUDA stream.
+There is no CPU fallback: importing this module raises if the compiled
+library is missing, and every call raises PdhgcError on a non-zero return.
+
+Function names follow the C entry points without the `pdhgc_` prefix
+(`lp_create`, `solve`, `corner_phase`, `kkt_report`, `get_solution`, ...);
+the raw ctypes functions are available as `lib.pdhgc_*`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdhgc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it first (python -m paper_2511_13894_gb300.build); "
+        "there is no CPU fallback")
+
+lib = C.CDLL(LIB_PATH)
+
+# ---- constants (include/pdhgc.h) -------------------------------------------
+OK = 0
+ERR_NAMES = {-1: "INVALID_ARG", -2: "INVALID_CSR", -3: "NONFINITE", -4: "BOUNDS", -5: "CUDA", -6: "OOM",
+             -7: "NO_PHASE1", -8: "NO_CORNER", -9: "TOO_LARGE", -10: "DEVICE", -11: "BUFFER"}
+STATUS_NAMES = {0: "NONE", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "TIME_LIMIT", 4: "NUMERICAL",
+                5: "CORNER_DONE", 6: "CORNER_LIMIT"}
+FP64, FP32_BULK = 0, 1
+PHASE1, CORNER = 0, 1
+
+
+class PdhgcError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        detail = lib.pdhgc_last_error_detail().decode(errors="replace")
+        super().__init__(f"{where}: {ERR_NAMES.get(code, code)} "
+                         f"({lib.pdhgc_strerror(code).decode()}): {detail}")
+
+
+class Params(C.Structure):
+    _fields_ = [("eps_rel", C.c_double), ("max_iters", C.c_int64), ("time_limit_s", C.c_double),
+                ("check_period", C.c_int32), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
+                ("beta_art", C.c_double), ("theta", C.c_double), ("eta_factor", C.c_double),
+                ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class CornerParams(C.Structure):
+    _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double), ("min_iters", C.c_int64),
+                ("max_iters", C.c_int64), ("time_limit_s", C.c_double), ("obj_seed", C.c_uint64),
+                ("obj_scale", C.c_double), ("stop_rule", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("chosen", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64),
+                ("rP2", C.c_double), ("rD2", C.c_double), ("rPinf", C.c_double), ("rDinf", C.c_double),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("gap", C.c_double),
+                ("rel_p", C.c_double), ("rel_d", C.c_double), ("rel_gap", C.c_double), ("rel_kkt", C.c_double),
+                ("off_bound_p", C.c_int64), ("zero_rc_d", C.c_int64), ("candidates", C.c_int64),
+                ("corner_measure", C.c_int64), ("primal_push_est", C.c_int64), ("dual_push_est", C.c_int64),
+                ("should_corner", C.c_int32), ("precision", C.c_int32), ("seconds", C.c_double),
+                ("omega", C.c_double), ("eta", C.c_double), ("sigma_max", C.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+_vp = C.c_void_p
+_sig = {
+    "pdhgc_default_params": (None, [C.POINTER(Params)]),
+    "pdhgc_default_corner_params": (None, [C.POINTER(CornerParams)]),
+    "pdhgc_lp_create": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, C.c_int, _vp]),
+    "pdhgc_solve": (C.c_int, [_vp, C.POINTER(Params), C.POINTER(Report)]),
+    "pdhgc_corner_phase": (C.c_int, [_vp, C.POINTER(CornerParams), C.POINTER(Report)]),
+    "pdhgc_kkt_report": (C.c_int, [_vp, C.c_int, C.POINTER(Report)]),
+    "pdhgc_get_solution": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int]),
+    "pdhgc_get_iterates": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
+    "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
+    "pdhgc_kernel_launches": (C.c_int64, [_vp]),
+    "pdhgc_lp_destroy": (None, [_vp]),
+    "pdhgc_strerror": (C.c_char_p, [C.c_int]),
+    "pdhgc_last_error_detail": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise PdhgcError(rc, where)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib.pdhgc_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def default_corner_params(**kw) -> CornerParams:
+    p = CornerParams()
+    lib.pdhgc_default_corner_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown corner parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr_host(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    return arr, arr.ctypes.data
+
+
+def _is_cuda_tensor(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _current_stream():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+class LP:
+    """One LP on the GPU (owns the library handle)."""
+
+    def __init__(self, handle, m, n, stream):
+        self._h = handle
+        self.m = m
+        self.n = n
+        self.stream = stream
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.pdhgc_lp_destroy(h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    # -- phases --------------------------------------------------------------
+    def solve(self, params: Params | None = None, **kw) -> dict:
+        p = params if params is not None else default_params(**kw)
+        r = Report()
+        _check(lib.pdhgc_solve(self._h, C.byref(p), C.byref(r)), "pdhgc_solve")
+        return r.as_dict()
+
+    def corner_phase(self, params: CornerParams | None = None, **kw) -> dict:
+        p = params if params is not None else default_corner_params(**kw)
+        r = Report()
+        _check(lib.pdhgc_corner_phase(self._h, C.byref(p), C.byref(r)), "pdhgc_corner_phase")
+        return r.as_dict()
+
+    def kkt_report(self, which: int = PHASE1) -> dict:
+        r = Report()
+        _check(lib.pdhgc_kkt_report(self._h, which, C.byref(r)), "pdhgc_kkt_report")
+        return r.as_dict()
+
+    # -- accessors -------------------------------------------------------------
+    def _outs(self, sizes, device):
+        if device:
+            torch = _torch()
+            bufs = [torch.empty(s, dtype=torch.float64, device="cuda") if s else None for s in sizes]
+            ptrs = [b.data_ptr() if b is not None else None for b in bufs]
+        else:
+            bufs = [np.empty(s, dtype=np.float64) if s else None for s in sizes]
+            ptrs = [b.ctypes.data if b is not None else None for b in bufs]
+        return bufs, ptrs
+
+    def get_solution(self, which: int = PHASE1, device: bool = False):
+        (x, y, z), (px, py, pz) = self._outs([self.n, self.m, self.n], device)
+        _check(lib.pdhgc_get_solution(self._h, which, px, py, pz, int(device)), "pdhgc_get_solution")
+        return x, y, z
+
+    def get_iterates(self, device: bool = False):
+        (x, y, xa, ya), ptrs = self._outs([self.n, self.m, self.n, self.m], device)
+        it = (C.c_int64 * 3)()
+        _check(lib.pdhgc_get_iterates(self._h, *ptrs, C.cast(it, _vp), int(device)), "pdhgc_get_iterates")
+        return dict(x=x, y=y, x_avg=xa, y_avg=ya, k=it[0], t=it[1], restarts=it[2])
+
+    def get_scaling(self):
+        dr = np.empty(self.m)
+        dc = np.empty(self.n)
+        sc = np.empty(5)
+        _check(lib.pdhgc_get_scaling(self._h, dr.ctypes.data, dc.ctypes.data, sc.ctypes.data, 0),
+               "pdhgc_get_scaling")
+        return dict(Dr=dr, Dc=dc, sigma_max=sc[0], eta=sc[1], omega=sc[2], tau=sc[3], sigma=sc[4])
+
+    def kernel_launches(self) -> int:
+        return int(lib.pdhgc_kernel_launches(self._h))
+
+
+def lp_create(m, n, row_ptr, col_idx, val, b, c, lb=None, ub=None, sense=None, stream=None) -> LP:
+    """pdhgc_lp_create.  Arrays may be numpy (host) or torch CUDA tensors
+    (device; then all of them must be, with dtypes int64 / int32 / float64 /
+    int8 as the header states).  `stream` is a raw cudaStream_t (int); by
+    default torch's current stream."""
+    arrays = [row_ptr, col_idx, val, b, c, lb, ub, sense]
+    on_device = any(_is_cuda_tensor(a) for a in arrays if a is not None)
+    keep = []
+    if on_device:
+        torch = _torch()
+        dts = [torch.int64, torch.int32, torch.float64, torch.float64, torch.float64, torch.float64,
+               torch.float64, torch.int8]
+        ptrs = []
+        for a, dt in zip(arrays, dts):
+            if a is None:
+                ptrs.append(None)
+                continue
+            if not _is_cuda_tensor(a) or a.dtype != dt or not a.is_contiguous():
+                raise TypeError("device inputs must all be contiguous CUDA tensors of the documented dtypes")
+            ptrs.append(a.data_ptr())
+    else:
+        dts = [np.int64, np.int32, np.float64, np.float64, np.float64, np.float64, np.float64, np.int8]
+        ptrs = []
+        for a, dt in zip(arrays, dts):
+            arr, p = _ptr_host(a, dt)
+            keep.append(arr)
+            ptrs.append(p)
+    nnz = int(row_ptr[-1]) if not on_device else int(row_ptr[-1].item())
+    if stream is None:
+        stream = _current_stream() if (on_device or _cuda_available()) else None
+    h = _vp()
+    rc = lib.pdhgc_lp_create(C.byref(h), int(m), int(n), nnz, *ptrs, int(on_device), stream)
+    _check(rc, "pdhgc_lp_create")
+    return LP(h, int(m), int(n), stream)
+
+
+def lp_from_dict(lp: dict, stream=None, device=False) -> LP:
+    """lp_create from a generator dict (keys m, n, row_ptr, col_idx, val, b,
+    c, lb, ub, sense); device=True first copies the arrays to the GPU."""
+    keys = ["row_ptr", "col_idx", "val", "b", "c", "lb", "ub", "sense"]
+    arrs = [lp.get(k) for k in keys]
+    if device:
+        torch = _torch()
+        dts = [torch.int64, torch.int32, torch.float64, torch.float64, torch.float64, torch.float64,
+               torch.float64, torch.int8]
+        arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+                for a, dt in zip(arrs, dts)]
+    return lp_create(lp["m"], lp["n"], *arrs, stream=stream)
+
+
+def uniform(seed: int, n: int, obj_scale: float = 1.0):
+    """pdhgc_uniform into a new CUDA tensor."""
+    torch = _torch()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(lib.pdhgc_uniform(C.c_uint64(seed), n, obj_scale, out.data_ptr(), _current_stream()),
+           "pdhgc_uniform")
+    return out
+
+
+def _cuda_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

@@ -1,0 +1,171 @@
+"""CUDA path vs the CPU oracle, through the C-ABI (needs a GB300).
+
+Tolerances: iterates after 100 iterations agree to 1e-10 relative (max-norm
+error over max(1, max-norm of the oracle's vector)): both sides run the
+same FP64 algorithm and differ only in rounding order (FMA contraction,
+row-sum order, 1/t versus division), which stays near 1e-14 after 100
+contractive PDHG steps.  Integer results (iteration counts, restarts,
+status, metric counts) must be equal.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2511_13894_gb300.pdhgc")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ITER_TOL = 1e-10
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if b.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def _lp_cases():
+    return {
+        "face_200x500_s0": lambda: lpgen.small_face_lp(0),
+        "face_200x500_s7": lambda: lpgen.small_face_lp(7),
+        "bounded_ineq": lambda: lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(3), 3),
+        "power_law_skewed": lambda: lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000),
+        "transport_30x70": lambda: lpgen.transportation_lp(30, 70, seed=2),
+        "tiny_5x11": lambda: lpgen.tiny_face_lp(5, 11, 7, seed=101),
+    }
+
+
+@pytest.mark.parametrize("name", list(_lp_cases()))
+def test_iterates_after_100_match_oracle(name):
+    lp = _lp_cases()[name]()
+    ref = oracle.run_iterations(lp, 100)
+    s = ref["state"]
+    g = P.lp_from_dict(lp)
+    rep = g.solve(max_iters=100, eps_rel=-1.0)
+    assert rep["status_name"] == "ITER_LIMIT" and rep["iters"] == 100
+    it = g.get_iterates()
+    assert it["k"] == 100 and it["t"] == s.t and it["restarts"] == s.restarts
+    xa, ya = s.average()
+    assert rel_err(it["x"], s.x) <= ITER_TOL
+    assert rel_err(it["y"], s.y) <= ITER_TOL
+    assert rel_err(it["x_avg"], xa) <= ITER_TOL
+    assert rel_err(it["y_avg"], ya) <= ITER_TOL
+    sc = g.get_scaling()
+    model = ref["model"]
+    assert rel_err(sc["Dr"], model.Dr) <= 1e-13
+    assert rel_err(sc["Dc"], model.Dc) <= 1e-13
+    assert abs(sc["sigma_max"] - ref["sigma_max"]) <= 1e-12 * ref["sigma_max"]
+    assert abs(sc["omega"] - s.omega) <= 1e-10 * s.omega
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed", "transport_30x70"])
+def test_full_solve_matches_oracle(name):
+    lp = _lp_cases()[name]()
+    ref = oracle.solve(lp)
+    g = P.lp_from_dict(lp)
+    rep = g.solve()
+    assert rep["status_name"] == "OPTIMAL" and ref["status"] == oracle.OPTIMAL
+    assert rep["iters"] == ref["iters"] and rep["restarts"] == ref["restarts"]
+    assert rep["rel_kkt"] <= 1e-6
+    x, y, z = g.get_solution()
+    xo, yo, zo = oracle.unscale(ref["model"], ref["x_hat"], ref["y_hat"])
+    assert rel_err(x, xo) <= 1e-8 and rel_err(y, yo) <= 1e-8 and rel_err(z, zo) <= 1e-8
+    orep = oracle.kkt_report(ref["model"], ref["x_hat"], ref["y_hat"])
+    for k in ("rP2", "rD2", "pobj", "dobj"):
+        assert abs(rep[k] - orep[k]) <= 1e-7 * (1.0 + abs(orep[k])), k
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure"):
+        assert rep[k] == orep[k], k
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq"])
+def test_corner_phase_matches_oracle(name):
+    lp = _lp_cases()[name]()
+    ref1 = oracle.solve(lp)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=11))
+    g = P.lp_from_dict(lp)
+    g.solve()
+    rep = g.corner_phase(obj_seed=11)
+    assert rep["status_name"] == "CORNER_DONE" and refc["status"] == oracle.CORNER_DONE
+    assert rep["iters"] == refc["iters"] and rep["restarts"] == refc["restarts"]
+    x, y, z = g.get_solution(P.CORNER)
+    xo, yo, zo = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+    assert rel_err(x, xo) <= 1e-7
+    orep = oracle.kkt_report(ref1["model"], refc["x_hat"], refc["y_hat"])
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure", "primal_push_est"):
+        assert rep[k] == orep[k], k
+
+
+def test_uniform_objective_is_bitwise_equal():
+    for seed, n in [(0, 1), (1234567, 1000), (2**63 + 5, 4099)]:
+        got = P.uniform(seed, n).cpu().numpy()
+        ref = oracle.splitmix64_uniform(seed, n)
+        assert np.array_equal(got, ref)
+
+
+def test_edge_shapes():
+    # 1 x 1; an empty column; an empty row with b = 0; nnz = 0
+    one = dict(m=1, n=1, row_ptr=np.array([0, 1]), col_idx=np.array([0], dtype=np.int32), val=np.array([2.0]),
+               b=np.array([3.0]), c=np.array([1.0]), lb=np.zeros(1), ub=np.full(1, np.inf),
+               sense=np.array([oracle.EQ], dtype=np.int8))
+    empty_col = dict(m=2, n=3, row_ptr=np.array([0, 2, 4]), col_idx=np.array([0, 2, 0, 2], dtype=np.int32),
+                     val=np.array([1.0, 1.0, 1.0, -1.0]), b=np.array([2.0, 0.0]), c=np.array([1.0, 5.0, 1.0]),
+                     lb=np.zeros(3), ub=np.array([np.inf, 4.0, np.inf]),
+                     sense=np.array([oracle.EQ, oracle.EQ], dtype=np.int8))
+    empty_row = dict(m=3, n=2, row_ptr=np.array([0, 2, 2, 3]), col_idx=np.array([0, 1, 1], dtype=np.int32),
+                     val=np.array([1.0, 1.0, 1.0]), b=np.array([1.0, 0.0, 0.25]), c=np.array([1.0, 2.0]),
+                     lb=np.zeros(2), ub=np.full(2, np.inf),
+                     sense=np.array([oracle.EQ, oracle.EQ, oracle.GE], dtype=np.int8))
+    no_nnz = dict(m=1, n=2, row_ptr=np.array([0, 0]), col_idx=np.zeros(0, dtype=np.int32), val=np.zeros(0),
+                  b=np.array([0.0]), c=np.array([1.0, -1.0]), lb=np.array([0.0, -1.0]), ub=np.array([5.0, 2.0]),
+                  sense=np.array([oracle.EQ], dtype=np.int8))
+    for lp in (one, empty_col, empty_row, no_nnz):
+        ref = oracle.run_iterations(lp, 100)
+        g = P.lp_from_dict(lp)
+        g.solve(max_iters=100, eps_rel=-1.0)
+        it = g.get_iterates()
+        s = ref["state"]
+        assert rel_err(it["x"], s.x) <= ITER_TOL and rel_err(it["y"], s.y) <= ITER_TOL
+        full = oracle.solve(lp)
+        rep = P.lp_from_dict(lp).solve()
+        assert rep["status"] == full["status"] and rep["iters"] == full["iters"]
+
+
+def test_device_inputs_and_errors():
+    lp = lpgen.small_face_lp(2)
+    g = P.lp_from_dict(lp, device=True)
+    rep = g.solve(max_iters=100, eps_rel=-1.0)
+    h = P.lp_from_dict(lp)
+    rep2 = h.solve(max_iters=100, eps_rel=-1.0)
+    assert np.array_equal(g.get_iterates()["x"], h.get_iterates()["x"])  # deterministic
+    x_dev, _, _ = g.get_solution(device=True)
+    assert x_dev.is_cuda
+    with pytest.raises(P.PdhgcError):
+        g.corner_phase(stop_rule=7)
+    with pytest.raises(P.PdhgcError):
+        P.lp_from_dict(lp).corner_phase()  # no phase 1
+    bad = dict(lp)
+    bad["lb"] = lp["lb"].copy()
+    bad["lb"][3] = 5.0
+    bad["ub"] = lp["ub"].copy()
+    bad["ub"][3] = 1.0
+    with pytest.raises(P.PdhgcError) as ei:
+        P.lp_from_dict(bad)
+    assert ei.value.code == -4
+    assert rep["iters"] == rep2["iters"] == 100
+
+
+def test_iteration_and_time_limits_stop_the_device_loop():
+    lp = lpgen.small_face_lp(4)
+    g = P.lp_from_dict(lp)
+    rep = g.solve(max_iters=130, eps_rel=1e-14)
+    assert rep["status_name"] == "ITER_LIMIT" and rep["iters"] == 130
+    rep = g.solve(max_iters=10**9, eps_rel=1e-300, time_limit_s=0.05)
+    assert rep["status_name"] == "TIME_LIMIT"
+    assert rep["seconds"] < 5.0
