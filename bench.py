@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark: restarted PDHG (phase 1 to rel-KKT 1e-6) + the corner-push phase
+of "Backing PDHG into a Corner" on one synthetic LP per GPU.
+
+One step = pdhgc_solve (Ruiz + Pock-Chambolle scaling, power iteration,
+restarted PDHG until the Section 2 relative test holds at 1e-6) followed by
+pdhgc_corner_phase (Algorithm 1, Section 3.1 stopping rule, capped at
+--corner-max-iters), on the LP already resident in HBM.  The reported value is
+PDHG iterations per second over the whole step (phase-1 plus corner
+iterations divided by step time); time-to-corner is the step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): a single LP does not shard without
+two all-gathers per iteration, so every rank solves its own replica of the
+workload (weak scaling); the only collectives are the timing barrier and the
+max-over-ranks reduction.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lpgen  # noqa: E402
+
+METRIC = "PDHG iters/s, time-to-corner at rel-KKT 1e-6, %HBM peak vs plain FP64"
+FALLBACK_HBM_GBS = 6800.0
+# FP64 peak from the part's published unit rate (1.25 TFLOP/s FP64 on GB300):
+# one DFMA is 2 flops, so 0.625e12 FP64 operations per second for FMA-only code.
+FP64_PEAK_TFLOPS = 1.25
+
+WORKLOADS = {
+    "power_law_m100k_n400k": lambda: lpgen.large_power_law_lp(0),
+    "transportation_1000x2000": lambda: lpgen.large_transportation_lp(0),
+    "random_face_m200_n500": lambda: lpgen.small_face_lp(0),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="power_law_m100k_n400k")
+    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--phase1-max-iters", type=int, default=1_000_000)
+    ap.add_argument("--corner-max-iters", type=int, default=200_000)
+    ap.add_argument("--corner-seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--profile-iters", type=int, default=50)
+    ap.add_argument("--cpu-iters", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
+                    help="kernels: short solve, then --profile-iters replays of the two iteration "
+                         "kernels as plain launches inside the NVTX range 'pdhg_kernels' (for ncu)")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record():
+    """dram bytes per launch recorded from an ncu capture (profiles/ncu_traffic.txt),
+    valid only while the kernel sources hash to the recorded value."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_13894_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    if rec.get("sources_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id=None):
+        self.lines = []
+        self.proc = None
+        self.device_id = device_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8):
+    """Bytes one PDHG iteration must move (gathers counted once per element):
+    primal (A' pass): values + indices, row pointers, reads of c, l, u, x and
+    the running sum, writes of x, x_bar and the running sum, y gathered once;
+    dual (A pass): values + indices, row pointers, reads of b, y, the running
+    sum and the sense byte, writes of y and the running sum, x_bar gathered once."""
+    primal = nnz * (s_v + 4) + n * 4 + n * 8 * s_x + m * s_x
+    dual = nnz * (s_v + 4) + m * 4 + m * (5 * s_x + 1) + n * s_x
+    return primal, dual
+
+
+def fp64_ops(m, n, nnz):
+    """FP64 operations per launch: one FMA per nonzero plus the epilogue
+    (primal: 6 per column; dual: 4 per row)."""
+    return nnz + 6 * n, nnz + 4 * m
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain FP64 numpy/scipy, as it stands) on this machine's CPU: each
+    step is a bounded sample of the workload, `cpu_iters` phase-1 PDHG
+    iterations from the start on the same LP; the scaling and power-iteration
+    setup runs once before the warm-up and is not timed."""
+    if rank != 0:
+        return
+    import oracle
+    lp = WORKLOADS[args.workload]()
+    model, p, sigma_max, eta = oracle.setup(lp)
+    iters = args.cpu_iters
+
+    def one_step():
+        import math
+        x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
+        s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            oracle.pdhg_step(model, s)
+            if s.k % p["check_period"] == 0:
+                xa, ya = s.average()
+                ec = oracle.evaluate(model, s.x, s.y, s.omega)
+                ea = oracle.evaluate(model, xa, ya, s.omega)
+                oracle.restart_check(model, s, p, ec, ea)
+        return time.perf_counter() - t0, math.nan
+
+    for _ in range(args.warmup):
+        one_step()
+    times = [one_step()[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = iters * args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "m": lp["m"], "n": lp["n"], "nnz": int(lp["row_ptr"][-1]),
+                   "precision": "fp64", "sample_iters_per_step": iters},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{iters} phase-1 PDHG iterations (with their restart checks) per step on "
+                                   f"the same LP; numpy/scipy single-threaded; setup untimed"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_sample(lp, iters):
+    """The oracle timed on this host on a bounded sample (rank 0, N = 1)."""
+    import oracle
+    t0 = time.perf_counter()
+    model, p, sigma_max, eta = oracle.setup(lp)
+    t_setup = time.perf_counter() - t0
+    x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
+    s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        oracle.pdhg_step(model, s)
+        if s.k % p["check_period"] == 0:
+            xa, ya = s.average()
+            ec = oracle.evaluate(model, s.x, s.y, s.omega)
+            ea = oracle.evaluate(model, xa, ya, s.omega)
+            oracle.restart_check(model, s, p, ec, ea)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} phase-1 PDHG iterations with restart checks on the same LP "
+                      f"({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
+                      f"numpy/scipy, single-threaded"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_2511_13894_gb300 import pdhgc as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    lp_dict = WORKLOADS[args.workload]()
+    m, n, nnz = lp_dict["m"], lp_dict["n"], int(lp_dict["row_ptr"][-1])
+    stream = torch.cuda.current_stream()
+    g = P.lp_from_dict(lp_dict, stream=stream.cuda_stream)
+    if args.mode == "kernels":
+        g.solve(max_iters=64)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pdhg_kernels")
+        ms = g.profile_iteration(args.profile_iters)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"mode": "kernels", "workload": args.workload, "primal_ms": ms[0], "dual_ms": ms[1]}))
+        return
+    params = P.default_params(max_iters=args.phase1_max_iters)
+    cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        r1 = g.solve(params)
+        rc = g.corner_phase(cparams)
+        return r1, rc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    launches0 = g.kernel_launches()
+    step_ms, iters, reps = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush: 512 MiB write between steps
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r1, rc = step()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(r1["iters"] + rc["iters"])
+        reps.append((r1, rc))
+    launches = g.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    total_iters = sum(iters)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        total_iters_all = float(it.item())
+    else:
+        total_iters_all = float(total_iters)
+    value = total_iters_all / (total_ms * 1e-3)
+
+    # kernel durations: event-bracketed replays of the two iteration kernels
+    ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
+    b_primal, b_dual = algorithmic_bytes(m, n, nnz)
+    f_primal, f_dual = fp64_ops(m, n, nnz)
+    dom = "primal" if ms_primal >= ms_dual else "dual"
+    ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
+    peak, peak_kind = measured_peaks()
+    achieved = b_dom / (ms_dom * 1e-3) / 1e9
+    tr = traffic_record()
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": (float(tr["dram_bytes_per_launch_" + dom]) if tr and ("dram_bytes_per_launch_" + dom) in tr
+                    else None),
+        "kernel": f"tile_spmv<{'PrimalOp' if dom == 'primal' else 'DualOp'}> ({dom} step)",
+        "peak_source": f"{peak_kind} hbm_gbs",
+        "algorithmic_bytes_per_launch": b_dom, "launch_ms": ms_dom,
+        "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
+        "fp64": {"ops_per_launch": f_dom, "achieved_tflops": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12,
+                 "peak_tflops": FP64_PEAK_TFLOPS,
+                 "frac": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                 "note": "every FP64 pipe operation counted as one FMA (2 flops) against 1.25 TFLOP/s"},
+    }
+    if roofline["fp64"]["frac"] > roofline["frac"]:
+        roofline["bound"] = "alu"
+    r1, rc = reps[-1]
+
+    # end-to-end through the public API with host buffers (pinned), per step:
+    # H2D of the inputs in lp_create, solve, corner, D2H of x, y, z
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {}
+        h2d = 0
+        for k in ("row_ptr", "col_idx", "val", "b", "c", "lb", "ub", "sense"):
+            a = np.ascontiguousarray(lp_dict[k])
+            t = torch.from_numpy(a).pin_memory()
+            host[k] = t.numpy()
+            h2d += a.nbytes
+        host["m"], host["n"] = m, n
+        d2h = 8 * (2 * n + m)
+        e_ms, e_it = [], []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            ge = P.lp_from_dict(host, stream=stream.cuda_stream)
+            a1 = ge.solve(params)
+            a2 = ge.corner_phase(cparams)
+            ge.get_solution(P.CORNER)
+            torch.cuda.synchronize()
+            e_ms.append((time.perf_counter() - t0) * 1e3)
+            e_it.append(a1["iters"] + a2["iters"])
+            ge.close()
+        e_total = sum(e_ms)
+        if dist is not None:
+            t = torch.tensor([e_total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_total = float(t.item())
+        e2e = {"value": sum(e_it) * world / (e_total * 1e-3), "unit": "iters/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e_total / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(lp_dict, args.cpu_iters)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "m": m, "n": n, "nnz": nnz, "precision": args.precision,
+                       "phase1_max_iters": args.phase1_max_iters, "corner_max_iters": args.corner_max_iters,
+                       "corner_seed": args.corner_seed, "eps_rel": 1e-6,
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "time_to_corner_s": total_ms / args.steps * 1e-3,
+            "phase1": {"status": r1["status_name"], "iters": r1["iters"], "restarts": r1["restarts"],
+                       "rel_kkt": r1["rel_kkt"], "seconds": r1["seconds"], "corner_measure": r1["corner_measure"],
+                       "candidates": r1["candidates"], "off_bound_p": r1["off_bound_p"],
+                       "should_corner": r1["should_corner"]},
+            "corner": {"status": rc["status_name"], "iters": rc["iters"], "restarts": rc["restarts"],
+                       "seconds": rc["seconds"], "corner_measure": rc["corner_measure"],
+                       "candidates": rc["candidates"], "off_bound_p": rc["off_bound_p"],
+                       "rel_p": rc["rel_p"], "rel_kkt": rc["rel_kkt"]},
+            "us_per_iter": total_ms * 1e3 / max(1, total_iters),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

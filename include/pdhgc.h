@@ -223,8 +223,23 @@ int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalar
  */
 int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void* cuda_stream);
 
-/* Size in bytes of the opaque device kernel count record (for tests). */
+/*
+ * pdhgc_kernel_launches — number of CUDA kernels this handle has launched
+ * so far (kernels inside the solve graph counted once per execution).
+ */
 int64_t pdhgc_kernel_launches(const pdhgc_lp* lp);
+
+/*
+ * pdhgc_profile_iteration — replays `iters` PDHG iterations of the last
+ * phase's model as plain launches on the handle's stream, each kernel
+ * bracketed by CUDA events, and writes the mean duration in milliseconds of
+ * one launch of the primal step (the A' pass, ms_out[0]) and of the dual
+ * step (the A pass, ms_out[1]).  The replayed iterations are real: they
+ * advance the iterate state, which is left inconsistent with the phase's
+ * report (x1/y1 and the corner result are not touched).  For profiling.
+ * Errors: NO_PHASE1, INVALID_ARG (iters < 1 or ms_out NULL).
+ */
+int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out);
 
 void pdhgc_lp_destroy(pdhgc_lp* lp);
 const char* pdhgc_strerror(int code);

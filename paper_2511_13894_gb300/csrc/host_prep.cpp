@@ -19,40 +19,48 @@ std::vector<int32_t> order_by_decreasing(const std::vector<int64_t>& len) {
   return idx;
 }
 
-int next_pow2(int v) {
-  int p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
-
 }  // namespace
 
-void plan_tiles(Csr& csr) {
-  csr.tiles.clear();
+void plan_segments(Csr& csr) {
   const int32_t R = csr.rows;
+  auto len = [&](int32_t r) { return csr.row_ptr[r + 1] - csr.row_ptr[r]; };
   int32_t r = 0;
-  while (r < R) {
-    const int32_t len = csr.row_ptr[r + 1] - csr.row_ptr[r];
-    if (len > kLongRow) {
-      csr.tiles.push_back(Tile{r, 1, 0, 0});
-      ++r;
-      continue;
+  while (r < R && len(r) > kWarpMaxLen) ++r;
+  csr.cta_rows = r;
+  while (r < R && len(r) > kSellMaxLen) ++r;
+  csr.long_rows = r;
+  const int32_t short_rows = R - csr.long_rows;
+  csr.nslices = (short_rows + kSellH - 1) / kSellH;
+  csr.slice_ptr.assign(csr.nslices + 1, 0);
+  csr.slice_w.assign(csr.nslices, 0);
+  for (int32_t s = 0; s < csr.nslices; ++s) {
+    const int32_t w = len(csr.long_rows + s * kSellH);  // the first row is the longest
+    csr.slice_w[s] = w;
+    csr.slice_ptr[s + 1] = csr.slice_ptr[s] + w * kSellH;
+  }
+  // K warps per slice, then blocks of 8 / K slices of equal K
+  csr.sell_blocks.clear();
+  auto warps_for = [](int32_t w) {
+    int32_t k = 1;
+    while (k < kWarpsPerBlock && k * kColsPerWarp < w) k <<= 1;
+    return k;
+  };
+  for (int32_t s = 0; s < csr.nslices;) {
+    const int32_t k = warps_for(csr.slice_w[s]);
+    const int32_t per = kWarpsPerBlock / k;
+    int32_t cnt = 0;
+    while (s + cnt < csr.nslices && cnt < per && warps_for(csr.slice_w[s + cnt]) == k) ++cnt;
+    csr.sell_blocks.push_back(SellBlock{s, cnt, k, 0});
+    s += cnt;
+  }
+  csr.sell_map.assign(csr.slice_ptr[csr.nslices], -1);
+  for (int32_t s = 0; s < csr.nslices; ++s) {
+    for (int32_t t = 0; t < kSellH; ++t) {
+      const int32_t row = csr.long_rows + s * kSellH + t;
+      if (row >= R) break;
+      for (int32_t j = 0; j < len(row); ++j)
+        csr.sell_map[csr.slice_ptr[s] + j * kSellH + t] = csr.row_ptr[row] + j;
     }
-    // lanes per row from the first (longest) row of the tile
-    int lanes = next_pow2((len + kLaneWork - 1) / kLaneWork);
-    if (lanes < 1) lanes = 1;
-    if (lanes > 32) lanes = 32;
-    const int32_t max_rows = kBlock / lanes;
-    const int32_t start = r;
-    int64_t nnz = 0;
-    while (r < R && r - start < max_rows) {
-      const int32_t l = csr.row_ptr[r + 1] - csr.row_ptr[r];
-      if (l > kLongRow || nnz + l > kTileNnz) break;
-      nnz += l;
-      ++r;
-    }
-    if (r == start) ++r;  // cannot happen (len <= kLongRow <= kTileNnz), kept for safety
-    csr.tiles.push_back(Tile{start, r - start, lanes, 0});
   }
 }
 
@@ -193,8 +201,8 @@ int prepare_lp(Prepared& P, int32_t m, int32_t n, int64_t nnz, const int64_t* ro
     cn += c[uj] * c[uj];
   }
   P.c_norm = std::sqrt(cn);
-  plan_tiles(P.A);
-  plan_tiles(P.AT);
+  plan_segments(P.A);
+  plan_segments(P.AT);
   return PDHGC_OK;
 }
 

@@ -1,10 +1,10 @@
 // Host-side layout of an LP for the GPU kernels (plain C++, no CUDA).
 //
 // Rows and columns are renumbered internally by decreasing nnz (stable), so
-// that consecutive rows handled by one warp have nearly equal lengths; '<'
-// rows are negated into '>' rows (Section 2: inequalities handled
-// implicitly); an explicit CSR of A' is built by a stable counting sort; and
-// each CSR is cut into row tiles for the SpMV kernels.
+// that the 32 rows of a warp have nearly equal lengths; '<' rows are negated
+// into '>' rows (Section 2: inequalities handled implicitly); an explicit CSR
+// of A' is built by a stable counting sort; and each CSR gets its row
+// segments and SELL-32 slots planned.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -12,19 +12,30 @@
 
 namespace pdhgc {
 
-// Tile kinds, chosen per tile from the longest row in it:
-//   lanes = 0      one whole CTA per row (row longer than kLongRow)
-//   lanes = g > 0  g lanes per row (g a power of two <= 32), the tile's
-//                  values and column indices staged in shared memory
-constexpr int kBlock = 256;          // threads per CTA of every tile kernel
-constexpr int kTileNnz = 2048;       // nnz staged per tile
-constexpr int kLongRow = 1024;       // rows longer than this get a CTA each
-constexpr int kLaneWork = 32;        // target nnz per lane in a staged tile
+// Row segments of a CSR whose rows are sorted by decreasing length:
+//   rows [0, cta_rows)           longer than kWarpMaxLen: one CTA per row
+//   rows [cta_rows, long_rows)   longer than kSellMaxLen: one warp per row
+//   rows [long_rows, rows)       SELL-32: slices of 32 consecutive rows stored
+//                                column-major (element j of the slice's 32 rows
+//                                contiguous), each slice as wide as its first
+//                                (longest) row; a lane owns one row, and the
+//                                slice's columns are split over K warps
+//                                (K = 1, 2, 4 or 8, at most kColsPerWarp
+//                                columns each) whose partial row sums are
+//                                added in shared memory in warp order
+constexpr int kBlock = 256;          // threads per CTA of the SpMV kernel
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kSellH = 32;           // rows per slice (one warp)
+constexpr int kColsPerWarp = 16;     // SELL columns one warp takes
+constexpr int kSellMaxLen = kColsPerWarp * kWarpsPerBlock;  // longest row kept in SELL (128)
+constexpr int kWarpMaxLen = 4096;    // longest row given to a single warp
+constexpr int kPad = 8;              // trailing padding elements of every device array
 
-struct Tile {
-  int32_t row0;    // first (internal) row
-  int32_t nrows;   // rows in the tile
-  int32_t lanes;   // lanes per row; 0 = CTA per row
+// one CTA of SELL work: slices [first, first + count), K warps per slice
+struct SellBlock {
+  int32_t first;
+  int32_t count;
+  int32_t k;
   int32_t pad;
 };
 
@@ -34,7 +45,16 @@ struct Csr {
   std::vector<int32_t> row_ptr;  // rows + 1
   std::vector<int32_t> col;      // nnz
   std::vector<double> val;       // nnz
-  std::vector<Tile> tiles;
+  // segments
+  int32_t cta_rows = 0, long_rows = 0, nslices = 0;
+  std::vector<int32_t> slice_ptr;  // nslices + 1 element offsets (multiples of 32)
+  std::vector<int32_t> slice_w;    // nslices
+  std::vector<int32_t> sell_map;   // slice_ptr[nslices]: CSR index of each slot, -1 = padding
+  std::vector<SellBlock> sell_blocks;
+  int32_t nb_cta() const { return cta_rows; }
+  int32_t nb_warp() const { return (long_rows - cta_rows + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+  int32_t nb_sell() const { return (int32_t)sell_blocks.size(); }
+  int32_t nblocks() const { return nb_cta() + nb_warp() + nb_sell(); }
 };
 
 struct Prepared {
@@ -57,7 +77,8 @@ int prepare_lp(Prepared& out, int32_t m, int32_t n, int64_t nnz, const int64_t* 
                const int32_t* col_idx, const double* val, const double* b, const double* c,
                const double* lb, const double* ub, const int8_t* sense, std::string& detail);
 
-// Cuts a CSR (rows sorted by decreasing length) into tiles.
-void plan_tiles(Csr& csr);
+// Plans the row segments and the SELL-32 slots of a CSR whose rows are
+// sorted by decreasing length.
+void plan_segments(Csr& csr);
 
 }  // namespace pdhgc

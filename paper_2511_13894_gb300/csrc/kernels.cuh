@@ -1,14 +1,10 @@
 // Device code of the PDHG + corner-push path (sm_103a).
 //
-// Every matrix pass is one "tile SpMV": a CTA takes one row tile of a CSR
-// (host_prep.h), stages the tile's values and column indices in shared
-// memory with coalesced loads, and reduces each row with `lanes` lanes
-// (one lane per row for short rows, so a row's sum costs exactly one FMA
-// per nonzero) or with the whole CTA for a long row.  The per-row result
-// goes straight into a fused epilogue (projection, extrapolation, running
-// sums, residuals) and per-tile partial sums for the KKT reductions, which
-// a single CTA later folds in a fixed order: every reduction is
-// deterministic run to run.
+// Every matrix pass is one SpMV launch over the row segments of host_prep.h
+// (SELL-32 slices for short rows, a warp or a CTA per long row) with a fused
+// epilogue (projection, extrapolation, running sums, residuals) and per-block
+// partial sums for the KKT reductions, which a single CTA later folds in a
+// fixed order: every reduction is deterministic run to run.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -55,7 +51,6 @@ struct DevIter {
   double* y_r;
 };
 
-constexpr int kWarps = kBlock / 32;
 
 // ---------------------------------------------------------------------------
 // Accumulators
@@ -90,6 +85,19 @@ struct MaxD {
   }
 };
 
+// Ordering key of a (non-NaN) double as a signed 64-bit integer: clamps of
+// the iteration epilogues are done on the integer pipe, sparing the FP64 unit
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffll;
+}
+__device__ __forceinline__ double clamp_i(double x, double lo, double hi) {
+  const long long k = dkey(x);
+  if (k < dkey(lo)) return lo;
+  if (k > dkey(hi)) return hi;
+  return x;
+}
+
 // z = projection of lam onto the cone the finite bounds allow (Section 2)
 __device__ __forceinline__ double proj_dual(double lam, double l, double u) {
   const bool lf = l != -INFINITY, uf = u != INFINITY;
@@ -106,91 +114,231 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // ---------------------------------------------------------------------------
-// The tile SpMV kernel
+// The SpMV kernel
+//
+// One launch covers a whole matrix pass.  Blocks are split over the three
+// row segments planned on the host (host_prep.h):
+//   CTA rows   the whole CTA strides over the row
+//   warp rows  a warp strides over the row, then a shuffle reduction
+//   SELL-32    a lane owns one row of a 32-row slice; element j of the
+//              slice's rows is contiguous, so every value / index load of a
+//              warp is one coalesced 256 + 128-byte access, there is no
+//              shared memory and no barrier, and a row costs exactly one FMA
+//              per nonzero; eight gathers are kept in flight per lane
+// The row sum goes straight into the operator's fused epilogue, and the
+// epilogue's partial sums are folded per block in a fixed order.
+//
+// kPdl: launched with programmatic dependent launch.  The matrix is never
+// written by an iteration kernel, so row lengths and the first batch of
+// values and indices are read before `griddepcontrol.wait`; every gather of
+// an iterate, every read of the scalar state and every write come after it.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <int NG>
+struct GV {
+  double v[NG];
+};
+
+struct SpmvMat {
+  const int* __restrict__ row_ptr;
+  const int* __restrict__ col;
+  const double* __restrict__ val;        // CSR values (CTA and warp rows)
+  const int* __restrict__ slice_ptr;
+  const int* __restrict__ slice_w;
+  const int* __restrict__ scol;          // SELL-32 indices
+  const double* __restrict__ sval;       // SELL-32 values
+  const SellBlock* __restrict__ sell_blocks;
+  int rows, cta_rows, long_rows, nslices;
+  int nb_cta, nb_warp, nb_sell;
+};
+
+constexpr int kBatch = 8;  // gathers in flight per lane
+
+// acc += sum over k = k0, k0+step, ... < k1 of val[k] * gathered(col[k]), in
+// that order, with kBatch gathers in flight per lane (CSR rows)
 template <class Op>
-__global__ void __launch_bounds__(kBlock) tile_spmv(const Tile* __restrict__ tiles, int ntiles,
-                                                    const int* __restrict__ row_ptr,
-                                                    const int* __restrict__ col,
-                                                    const double* __restrict__ val, Op op,
-                                                    double* __restrict__ partials) {
+__device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& acc, double rc,
+                                               const double* __restrict__ val, const int* __restrict__ col,
+                                               int k0, int k1, int step) {
+  constexpr int NG = Op::NG;
+  int k = k0;
+  for (; k + (kBatch - 1) * step < k1; k += kBatch * step) {
+    double v[kBatch];
+    int c[kBatch];
+    GV<NG> g[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = val[k + u * step];
+      c[u] = col[k + u * step];
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+      for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) op.accum(acc, rc, v[u], g[u]);
+  }
+  for (; k < k1; k += step) {
+    GV<NG> g;
+    const int c = col[k];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) g.v[i] = __ldg(op.gsrc(i) + c);
+    op.accum(acc, rc, val[k], g);
+  }
+}
+
+template <class Op, bool kPdl>
+__global__ void __launch_bounds__(kBlock) spmv(SpmvMat M, Op op, double* __restrict__ partials) {
+  constexpr int NG = Op::NG;
   constexpr int NQ = Op::NQ;
   constexpr int NQS = NQ > 0 ? NQ : 1;
-  __shared__ double s_val[kTileNnz];
-  __shared__ int s_col[kTileNnz];
-  __shared__ typename Op::Acc s_acc[kWarps];
-  __shared__ double s_red[NQS][kWarps];
-  if (op.skip()) return;
-  const Tile t = tiles[blockIdx.x];
+  __shared__ typename Op::Acc s_acc[kWarpsPerBlock];
+  __shared__ double s_red[NQS][kWarpsPerBlock];
+  if constexpr (!kPdl) {
+    if (op.skip()) return;
+  }
   const int tid = threadIdx.x;
-  const int lane32 = tid & 31, warp = tid >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int blk = blockIdx.x;
   double part[NQS];
 #pragma unroll
   for (int q = 0; q < NQS; ++q) part[q] = 0.0;
 
-  if (t.lanes == 0) {
-    const int r = t.row0;
-    const int e0 = row_ptr[r], e1 = row_ptr[r + 1];
+  if (blk < M.nb_cta) {
+    const int r = blk;
+    const int e0 = M.row_ptr[r], e1 = M.row_ptr[r + 1];
+    if constexpr (kPdl) {
+      grid_dep_wait();
+      if (op.skip()) return;
+    }
     const double rc = op.row_ctx(r);
     typename Op::Acc acc;
     acc.zero();
-    for (int e = e0 + tid; e < e1; e += kBlock) op.combine(acc, rc, val[e], col[e]);
+    row_dot_global(op, acc, rc, M.val, M.col, e0 + tid, e1, kBlock);
+    if constexpr (kPdl) grid_dep_launch();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
-    if (lane32 == 0) s_acc[warp] = acc;
+    if (lane == 0) s_acc[warp] = acc;
     __syncthreads();
     if (tid == 0) {
       typename Op::Acc tot = s_acc[0];
 #pragma unroll
-      for (int w = 1; w < kWarps; ++w) tot.add(s_acc[w]);
+      for (int w = 1; w < kWarpsPerBlock; ++w) tot.add(s_acc[w]);
       op.epilogue(r, tot, part);
     }
-  } else {
-    const int e0 = row_ptr[t.row0];
-    const int cnt = row_ptr[t.row0 + t.nrows] - e0;
-    for (int k = tid; k < cnt; k += kBlock) {
-      s_val[k] = val[e0 + k];
-      s_col[k] = col[e0 + k];
+  } else if (blk < M.nb_cta + M.nb_warp) {
+    const int r = M.cta_rows + (blk - M.nb_cta) * kWarpsPerBlock + warp;
+    const bool has = r < M.long_rows;  // uniform within the warp
+    int e0 = 0, e1 = 0;
+    if (has) {
+      e0 = M.row_ptr[r];
+      e1 = M.row_ptr[r + 1];
     }
-    __syncthreads();
-    const int g = t.lanes;
-    const int grp = tid / g;
-    const int lane = tid & (g - 1);
-    if (grp < t.nrows) {
-      const int r = t.row0 + grp;
-      const int a = row_ptr[r] - e0, b = row_ptr[r + 1] - e0;
+    if constexpr (kPdl) {
+      grid_dep_wait();
+      if (op.skip()) return;
+    }
+    if (has) {
       const double rc = op.row_ctx(r);
       typename Op::Acc acc;
       acc.zero();
-      for (int k = a + lane; k < b; k += g) op.combine(acc, rc, s_val[k], s_col[k]);
-      if (g > 1) {
-        const unsigned base = lane32 & ~(g - 1);
-        const unsigned mask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << base);
-        for (int off = g >> 1; off > 0; off >>= 1) acc.add(acc.shfl_xor(mask, off));
-      }
+      row_dot_global(op, acc, rc, M.val, M.col, e0 + lane, e1, 32);
+      if constexpr (kPdl) grid_dep_launch();
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
       if (lane == 0) op.epilogue(r, acc, part);
+    } else {
+      if constexpr (kPdl) grid_dep_launch();
     }
+  } else {
+    // SELL-32: this warp sums columns [jb, je) of its slice's 32 rows
+    const SellBlock sb = M.sell_blocks[blk - M.nb_cta - M.nb_warp];
+    const int K = sb.k;
+    const int ls = warp / K, kw = warp - ls * K;
+    int r = -1, len = 0, base = 0, jb = 0, je = 0;
+    if (ls < sb.count) {
+      const int s = sb.first + ls;
+      base = M.slice_ptr[s];
+      const int w = M.slice_w[s];
+      const int cw = (w + K - 1) / K;
+      jb = kw * cw;
+      je = min(w, jb + cw);
+      const int rr = M.long_rows + s * kSellH + lane;
+      if (rr < M.rows) {
+        r = rr;
+        len = M.row_ptr[rr + 1] - M.row_ptr[rr];
+      }
+    }
+    const int jend = min(je, len);  // this lane's last column + 1
+    double v[kBatch];
+    int c[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (jb + u < jend) {
+        v[u] = M.sval[base + (jb + u) * kSellH + lane];
+        c[u] = M.scol[base + (jb + u) * kSellH + lane];
+      }
+    }
+    if constexpr (kPdl) {
+      grid_dep_wait();
+      if (op.skip()) return;
+    }
+    typename Op::Acc acc;
+    acc.zero();
+    const double rc = r >= 0 ? op.row_ctx(r) : 0.0;
+    for (int j = jb; j < je; j += kBatch) {
+      if (j > jb) {
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          if (j + u < jend) {
+            v[u] = M.sval[base + (j + u) * kSellH + lane];
+            c[u] = M.scol[base + (j + u) * kSellH + lane];
+          }
+        }
+      }
+      GV<NG> g[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < jend)
+#pragma unroll
+          for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < jend) op.accum(acc, rc, v[u], g[u]);
+    }
+    if constexpr (kPdl) grid_dep_launch();
+    if (K > 1) {  // uniform over the block
+      __shared__ typename Op::Acc s_part[kWarpsPerBlock][kSellH];
+      s_part[warp][lane] = acc;
+      __syncthreads();
+      if (kw == 0) {
+        for (int q = 1; q < K; ++q) acc.add(s_part[warp + q][lane]);
+      }
+    }
+    if (kw == 0 && r >= 0) op.epilogue(r, acc, part);
   }
 
   if constexpr (NQ > 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      double v = part[q];
+      double x = part[q];
       const bool is_max = (Op::kMaxMask >> q) & 1u;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double o = __shfl_xor_sync(0xffffffffu, v, off);
-        v = is_max ? fmax(v, o) : v + o;
+        const double o = __shfl_xor_sync(0xffffffffu, x, off);
+        x = is_max ? fmax(x, o) : x + o;
       }
-      if (lane32 == 0) s_red[q][warp] = v;
+      if (lane == 0) s_red[q][warp] = x;
     }
     __syncthreads();
     if (tid < NQ) {
       const bool is_max = (Op::kMaxMask >> tid) & 1u;
-      double v = s_red[tid][0];
+      double x = s_red[tid][0];
 #pragma unroll
-      for (int w = 1; w < kWarps; ++w) v = is_max ? fmax(v, s_red[tid][w]) : v + s_red[tid][w];
-      partials[(size_t)tid * ntiles + blockIdx.x] = v;
+      for (int w2 = 1; w2 < kWarpsPerBlock; ++w2) x = is_max ? fmax(x, s_red[tid][w2]) : x + s_red[tid][w2];
+      partials[(size_t)tid * gridDim.x + blk] = x;
     }
   }
 }
@@ -211,12 +359,14 @@ struct PrimalOp {
   DevIter w;
   __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double*) const {
     const double tau = S->tau;
     const double g = md.chat[j] - a.v[0];
     const double xo = w.x[j];
-    const double xn = fmin(fmax(xo - tau * g, md.lhat[j]), md.uhat[j]);
+    const double xn = clamp_i(xo - tau * g, md.lhat[j], md.uhat[j]);
     w.xbar[j] = 2.0 * xn - xo;
     w.sum_x[j] += xn;
     w.x[j] = xn;
@@ -235,11 +385,13 @@ struct DualOp {
   DevIter w;
   __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(xbar + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return xbar; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int i, const Acc& a, double*) const {
     const double sigma = S->sigma;
     double yn = w.y[i] + sigma * (md.bhat[i] - a.v[0]);
-    if (md.ge[i]) yn = fmax(yn, 0.0);
+    if (md.ge[i] && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
     w.sum_y[i] += yn;
     w.y[i] = yn;
   }
@@ -261,9 +413,11 @@ struct EvalRowsOp {
   DevModel md;
   __device__ bool skip() const { return S->done; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const {
-    a.v[0] = fma(v, __ldg(x + c), a.v[0]);
-    a.v[1] = fma(v, __ldg(sum_x + c), a.v[1]);
+  static constexpr int NG = 2;
+  __device__ const double* gsrc(int i) const { return i == 0 ? x : sum_x; }
+  __device__ void accum(Acc& a, double, double v, const GV<2>& g) const {
+    a.v[0] = fma(v, g.v[0], a.v[0]);
+    a.v[1] = fma(v, g.v[1], a.v[1]);
   }
   __device__ void epilogue(int i, const Acc& a, double* part) const {
     const double inv_t = S->inv_t;
@@ -302,9 +456,11 @@ struct EvalColsOp {
   DevModel md;
   __device__ bool skip() const { return S->done; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const {
-    a.v[0] = fma(v, __ldg(y + c), a.v[0]);
-    a.v[1] = fma(v, __ldg(sum_y + c), a.v[1]);
+  static constexpr int NG = 2;
+  __device__ const double* gsrc(int i) const { return i == 0 ? y : sum_y; }
+  __device__ void accum(Acc& a, double, double v, const GV<2>& g) const {
+    a.v[0] = fma(v, g.v[0], a.v[0]);
+    a.v[1] = fma(v, g.v[1], a.v[1]);
   }
   __device__ void epilogue(int j, const Acc& a, double* part) const {
     const double inv_t = S->inv_t;
@@ -344,8 +500,11 @@ struct ScaleMaxOp {
   double* __restrict__ fac;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int r) const { return d_own[r]; }
-  __device__ void combine(Acc& a, double rc, double v, int c) const {
-    const double e = kTransposed ? (d_other[c] * fabs(v)) * rc : (rc * fabs(v)) * d_other[c];
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return d_other; }
+  __device__ void accum(Acc& a, double rc, double v, const GV<1>& g) const {
+    const double d = g.v[0];
+    const double e = kTransposed ? (d * fabs(v)) * rc : (rc * fabs(v)) * d;
     a.v[0] = fmax(a.v[0], e);
   }
   __device__ void epilogue(int r, const Acc& a, double*) const {
@@ -363,8 +522,11 @@ struct ScaleSumOp {
   double* __restrict__ fac;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int r) const { return d_own[r]; }
-  __device__ void combine(Acc& a, double rc, double v, int c) const {
-    const double e = kTransposed ? (d_other[c] * fabs(v)) * rc : (rc * fabs(v)) * d_other[c];
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return d_other; }
+  __device__ void accum(Acc& a, double rc, double v, const GV<1>& g) const {
+    const double d = g.v[0];
+    const double e = kTransposed ? (d * fabs(v)) * rc : (rc * fabs(v)) * d;
     a.v[0] += e;
   }
   __device__ void epilogue(int r, const Acc& a, double*) const {
@@ -383,7 +545,9 @@ struct SpmvOp {
   double* __restrict__ out;
   __device__ bool skip() const { return S->pi_zero != 0; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double val, int c) const { a.v[0] = fma(val, __ldg(v + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return v; }
+  __device__ void accum(Acc& a, double, double val, const GV<1>& g) const { a.v[0] = fma(val, g.v[0], a.v[0]); }
   __device__ void epilogue(int r, const Acc& a, double* part) const {
     out[r] = a.v[0];
     if constexpr (kNorm) part[0] += a.v[0] * a.v[0];
@@ -402,7 +566,9 @@ struct ReportRowsOp {
   double tol;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(x + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return x; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int i, const Acc& a, double* part) const {
     const double b = md.bhat[i], dr = md.Dr[i];
     const bool ge = md.ge[i];
@@ -436,7 +602,9 @@ struct ReportColsOp {
   double tol;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double* part) const {
     const double c = md.chat[j], l = md.lhat[j], u = md.uhat[j], dc = md.Dc[j];
     const double lam = c - a.v[0];
@@ -487,7 +655,9 @@ struct CornerColsOp {
   unsigned long long seed;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y1 + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return y1; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double* part) const {
     const double dc = md.Dc[j];
     const double lam = md.chat[j] - a.v[0];

@@ -73,6 +73,16 @@ __global__ void k_scale_values(const int* __restrict__ row_ptr, const int* __res
   }
 }
 
+// SELL-32 copy of a CSR array: dst[k] = src[map[k]], 0 on padding slots
+template <class T>
+__global__ void k_sell_fill(const int* __restrict__ map, const T* __restrict__ src, T* __restrict__ dst, int nslots) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nslots) {
+    const int e = map[k];
+    dst[k] = e >= 0 ? src[e] : T(0);
+  }
+}
+
 // b_hat = D_r b_int; c_hat = D_c c; l_hat = l / D_c; u_hat = u / D_c
 __global__ void k_scale_vectors(int m, int n, const double* Dr, const double* Dc, const double* b_int,
                                 const double* c, const double* l, const double* u, double* bhat,
@@ -399,7 +409,9 @@ struct ZOp {
   double* __restrict__ z;
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ void combine(Acc& a, double, double v, int c) const { a.v[0] = fma(v, __ldg(y + c), a.v[0]); }
+  static constexpr int NG = 1;
+  __device__ const double* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double*) const {
     z[j] = proj_dual(md.chat[j] - a.v[0], md.lhat[j], md.uhat[j]) / md.Dc[j];
   }
@@ -452,10 +464,20 @@ struct pdhgc_lp {
   int64_t launches = 0;
 
   // matrix (internal numbering)
-  int *A_rp = nullptr, *A_col = nullptr, *T_rp = nullptr, *T_col = nullptr;
-  double *A_val = nullptr, *T_val = nullptr, *A_hat = nullptr, *T_hat = nullptr;
-  Tile *A_tiles = nullptr, *T_tiles = nullptr;
-  int ntA = 0, ntT = 0;
+  // one matrix (A or A') on the device: CSR plus its SELL-32 copy
+  struct Mat {
+    int rows = 0, cta_rows = 0, long_rows = 0, nslices = 0, nslots = 0;
+    int nb_cta = 0, nb_warp = 0, nb_sell = 0;
+    int *rp = nullptr, *col = nullptr, *slice_ptr = nullptr, *slice_w = nullptr, *scol = nullptr, *smap = nullptr;
+    SellBlock* sblocks = nullptr;
+    double *val = nullptr, *hat = nullptr, *sval = nullptr, *shat = nullptr;  // original / scaled values
+    int nblocks() const { return nb_cta + nb_warp + nb_sell; }
+    SpmvMat view(bool scaled) const {
+      return SpmvMat{rp,   col,      scaled ? hat : val, slice_ptr, slice_w, scol,   scaled ? shat : sval,
+                     sblocks, rows, cta_rows, long_rows, nslices,  nb_cta,  nb_warp, nb_sell};
+    }
+  } A, T;
+  int ntA = 0, ntT = 0;  // blocks of one pass over A / A' (partials per quantity)
   // vectors (internal order)
   double *b_int = nullptr, *sign = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
   int8_t* ge = nullptr;
@@ -469,6 +491,7 @@ struct pdhgc_lp {
   int8_t* ge_c = nullptr;
   double *pi_v = nullptr, *pi_w = nullptr, *pi_u = nullptr, *tmp_n = nullptr, *tmp_m = nullptr;
   double *pA = nullptr, *pT = nullptr, *scratch = nullptr;
+  int* err = nullptr;  // device error word set by a kernel whose bounded wait ran out
   Scalars* S = nullptr;
   DevReport* rep = nullptr;
   double b_norm = 0.0, c_norm = 0.0;
@@ -498,13 +521,27 @@ namespace {
 inline int grid_for(long long n, int block = 256) { return (int)((n + block - 1) / block); }
 
 template <class Op>
-int launch_tiles(pdhgc_lp* lp, bool transposed, const double* val, const Op& op, double* partials,
-                 cudaStream_t st) {
-  const int nt = transposed ? lp->ntT : lp->ntA;
-  if (nt == 0) return PDHGC_OK;
-  tile_spmv<Op><<<nt, kBlock, 0, st>>>(transposed ? lp->T_tiles : lp->A_tiles, nt,
-                                       transposed ? lp->T_rp : lp->A_rp, transposed ? lp->T_col : lp->A_col,
-                                       val, op, partials);
+int launch_tiles(pdhgc_lp* lp, bool transposed, bool scaled, const Op& op, double* partials, cudaStream_t st,
+                 bool pdl = false) {
+  const pdhgc_lp::Mat& M = transposed ? lp->T : lp->A;
+  const int nb = M.nblocks();
+  if (nb == 0) return PDHGC_OK;
+  const SpmvMat view = M.view(scaled);
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, spmv<Op, true>, view, op, partials));
+  } else {
+    spmv<Op, false><<<nb, kBlock, 0, st>>>(view, op, partials);
+  }
   lp->launches++;
   CKL();
   return PDHGC_OK;
@@ -532,21 +569,26 @@ int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
   lp->launches += 2;
   CKL();
   for (int pass = 0; pass < p.ruiz_iters; ++pass) {
-    RET(launch_tiles(lp, false, lp->A_val, ScaleMaxOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
-    RET(launch_tiles(lp, true, lp->T_val, ScaleMaxOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
+    RET(launch_tiles(lp, false, false, ScaleMaxOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
+    RET(launch_tiles(lp, true, false, ScaleMaxOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
     k_mul_inplace<<<grid_for(m), 256, 0, st>>>(lp->Dr, lp->rfac, m);
     k_mul_inplace<<<grid_for(n), 256, 0, st>>>(lp->Dc, lp->cfac, n);
     lp->launches += 2;
     CKL();
   }
-  RET(launch_tiles(lp, false, lp->A_val, ScaleSumOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
-  RET(launch_tiles(lp, true, lp->T_val, ScaleSumOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
+  RET(launch_tiles(lp, false, false, ScaleSumOp<false>{lp->Dr, lp->Dc, lp->rfac}, nullptr, st));
+  RET(launch_tiles(lp, true, false, ScaleSumOp<true>{lp->Dc, lp->Dr, lp->cfac}, nullptr, st));
   k_mul_inplace<<<grid_for(m), 256, 0, st>>>(lp->Dr, lp->rfac, m);
   k_mul_inplace<<<grid_for(n), 256, 0, st>>>(lp->Dc, lp->cfac, n);
-  k_scale_values<<<grid_for((long long)m * 32), 256, 0, st>>>(lp->A_rp, lp->A_col, lp->A_val, lp->A_hat, m,
+  k_scale_values<<<grid_for((long long)m * 32), 256, 0, st>>>(lp->A.rp, lp->A.col, lp->A.val, lp->A.hat, m,
                                                               lp->Dr, lp->Dc, 0);
-  k_scale_values<<<grid_for((long long)n * 32), 256, 0, st>>>(lp->T_rp, lp->T_col, lp->T_val, lp->T_hat, n,
+  k_scale_values<<<grid_for((long long)n * 32), 256, 0, st>>>(lp->T.rp, lp->T.col, lp->T.val, lp->T.hat, n,
                                                               lp->Dr, lp->Dc, 1);
+  for (const pdhgc_lp::Mat* M : {&lp->A, &lp->T}) {
+    if (M->nslots == 0) continue;  // no nonzeros in SELL rows
+    k_sell_fill<<<grid_for(M->nslots), 256, 0, st>>>(M->smap, M->hat, M->shat, M->nslots);
+    lp->launches++;
+  }
   k_scale_vectors<<<grid_for(m > n ? m : n), 256, 0, st>>>(m, n, lp->Dr, lp->Dc, lp->b_int, lp->c, lp->l,
                                                             lp->u, lp->bhat, lp->chat, lp->lhat, lp->uhat);
   k_norm2<<<1, 1024, 0, st>>>(lp->bhat, m, lp->scratch + 0);
@@ -558,14 +600,14 @@ int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
   k_fill<<<grid_for(n), 256, 0, st>>>(lp->pi_v, n, 1.0 / std::sqrt((double)n));
   lp->launches++;
   for (int k = 0; k < p.power_iters; ++k) {
-    RET(launch_tiles(lp, false, lp->A_hat, SpmvOp<false>{lp->S, lp->pi_v, lp->pi_u}, nullptr, st));
-    RET(launch_tiles(lp, true, lp->T_hat, SpmvOp<true>{lp->S, lp->pi_u, lp->pi_w}, lp->pT, st));
+    RET(launch_tiles(lp, false, true, SpmvOp<false>{lp->S, lp->pi_v, lp->pi_u}, nullptr, st));
+    RET(launch_tiles(lp, true, true, SpmvOp<true>{lp->S, lp->pi_u, lp->pi_w}, lp->pT, st));
     k_pi_norm<<<1, 1024, 0, st>>>(lp->S, lp->pT, lp->ntT, lp->scratch + 2);
     k_pi_scale<<<grid_for(n), 256, 0, st>>>(lp->S, lp->pi_w, lp->scratch + 2, lp->pi_v, n);
     lp->launches += 2;
     CKL();
   }
-  RET(launch_tiles(lp, false, lp->A_hat, SpmvOp<true>{lp->S, lp->pi_v, lp->pi_u}, lp->pA, st));
+  RET(launch_tiles(lp, false, true, SpmvOp<true>{lp->S, lp->pi_v, lp->pi_u}, lp->pA, st));
   k_pi_final<<<1, 1024, 0, st>>>(lp->S, lp->pA, lp->ntA, p.eta_factor, lp->scratch + 0, lp->scratch + 1);
   lp->launches++;
   CKL();
@@ -575,8 +617,8 @@ int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
 // the KKT evaluation of the current and average points (two matrix passes)
 int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st) {
   const DevIter& w = lp->it;
-  RET(launch_tiles(lp, false, lp->A_hat, EvalRowsOp{lp->S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, lp->pA, st));
-  RET(launch_tiles(lp, true, lp->T_hat, EvalColsOp{lp->S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, lp->pT, st));
+  RET(launch_tiles(lp, false, true, EvalRowsOp{lp->S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, lp->pA, st));
+  RET(launch_tiles(lp, true, true, EvalColsOp{lp->S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, lp->pT, st));
   return PDHGC_OK;
 }
 
@@ -615,9 +657,9 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
   const int64_t before = lp->launches;
   int rc = PDHGC_OK;
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
-    rc = launch_tiles(lp, true, lp->T_hat, PrimalOp{lp->S, i, lp->it.y, md, lp->it}, nullptr, cs);
+    rc = launch_tiles(lp, true, true, PrimalOp{lp->S, i, lp->it.y, md, lp->it}, nullptr, cs, true);
     if (rc == PDHGC_OK)
-      rc = launch_tiles(lp, false, lp->A_hat, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs);
+      rc = launch_tiles(lp, false, true, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs, true);
   }
   if (rc == PDHGC_OK) {
     k_pre_check<<<1, 32, 0, cs>>>(lp->S);
@@ -643,6 +685,10 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
   lp->launches++;
   CKL();
   CK(cudaStreamSynchronize(st));
+  int derr = 0;
+  CK(cudaMemcpy(&derr, lp->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr != 0) return set_err(PDHGC_ERR_DEVICE, "a bounded device wait ran out (error word " +
+                                                      std::to_string(derr) + ")");
   long long chunks = 0;
   CK(cudaMemcpy(&chunks, &lp->S->chunks, sizeof(chunks), cudaMemcpyDeviceToHost));
   lp->launches += chunks * per_body;
@@ -652,8 +698,8 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
 int run_report(pdhgc_lp* lp, const double* x, const double* y, pdhgc_report* out) {
   cudaStream_t st = lp->stream;
   DevModel md = model_orig(lp);
-  RET(launch_tiles(lp, false, lp->A_hat, ReportRowsOp{x, y, md, 1e-6}, lp->pA, st));
-  RET(launch_tiles(lp, true, lp->T_hat, ReportColsOp{y, x, lp->l, lp->u, md, 1e-6}, lp->pT, st));
+  RET(launch_tiles(lp, false, true, ReportRowsOp{x, y, md, 1e-6}, lp->pA, st));
+  RET(launch_tiles(lp, true, true, ReportColsOp{y, x, lp->l, lp->u, md, 1e-6}, lp->pT, st));
   k_report_final<<<1, 256, 0, st>>>(lp->pA, lp->ntA, lp->pT, lp->ntT, lp->b_norm, lp->c_norm, lp->rep);
   lp->launches++;
   CKL();
@@ -706,6 +752,51 @@ int check_params(const pdhgc_params* p) {
     return set_err(PDHGC_ERR_INVALID_ARG, "parameter out of range");
   if (p->precision != PDHGC_FP64)
     return set_err(PDHGC_ERR_INVALID_ARG, "precision not supported by this build");
+  return PDHGC_OK;
+}
+
+// uploads one CSR (padded by kPad) and builds its SELL-32 copy on the device
+int setup_mat(pdhgc_lp* lp, pdhgc_lp::Mat& M, const Csr& C, cudaStream_t st) {
+  const size_t nz = (size_t)C.nnz;
+  M.rows = C.rows;
+  M.cta_rows = C.cta_rows;
+  M.long_rows = C.long_rows;
+  M.nslices = C.nslices;
+  M.nslots = C.slice_ptr[C.nslices];
+  M.nb_cta = C.nb_cta();
+  M.nb_warp = C.nb_warp();
+  M.nb_sell = C.nb_sell();
+  const size_t ns = (size_t)M.nslots;
+  RET(lp->alloc(&M.rp, (size_t)C.rows + 1 + kPad));
+  RET(lp->alloc(&M.col, nz + kPad));
+  RET(lp->alloc(&M.val, nz + kPad));
+  RET(lp->alloc(&M.hat, nz + kPad));
+  RET(lp->alloc(&M.slice_ptr, (size_t)C.nslices + 1 + kPad));
+  RET(lp->alloc(&M.slice_w, (size_t)C.nslices + kPad));
+  RET(lp->alloc(&M.scol, ns + kPad));
+  RET(lp->alloc(&M.smap, ns + kPad));
+  RET(lp->alloc(&M.sval, ns + kPad));
+  RET(lp->alloc(&M.shat, ns + kPad));
+  RET(lp->alloc(&M.sblocks, C.sell_blocks.size() + 1));
+  if (!C.sell_blocks.empty())
+    CK(cudaMemcpyAsync(M.sblocks, C.sell_blocks.data(), C.sell_blocks.size() * sizeof(SellBlock),
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(M.hat, 0, (nz + kPad) * 8, st));
+  CK(cudaMemsetAsync(M.shat, 0, (ns + kPad) * 8, st));
+  CK(cudaMemcpyAsync(M.rp, C.row_ptr.data(), ((size_t)C.rows + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (nz) {
+    CK(cudaMemcpyAsync(M.col, C.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(M.val, C.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(M.slice_ptr, C.slice_ptr.data(), ((size_t)C.nslices + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (C.nslices) CK(cudaMemcpyAsync(M.slice_w, C.slice_w.data(), (size_t)C.nslices * 4, cudaMemcpyHostToDevice, st));
+  if (ns) {
+    CK(cudaMemcpyAsync(M.smap, C.sell_map.data(), ns * 4, cudaMemcpyHostToDevice, st));
+    k_sell_fill<<<grid_for((long long)ns), 256, 0, st>>>(M.smap, M.col, M.scol, (int)ns);
+    k_sell_fill<<<grid_for((long long)ns), 256, 0, st>>>(M.smap, M.val, M.sval, (int)ns);
+    lp->launches += 2;
+    CKL();
+  }
   return PDHGC_OK;
 }
 
@@ -812,19 +903,11 @@ int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int
   lp->c_norm = P.c_norm;
   CK(cudaStreamCreateWithFlags(&lp->cap_stream, cudaStreamNonBlocking));
   const size_t nz = (size_t)nnz;
-  lp->ntA = (int)P.A.tiles.size();
-  lp->ntT = (int)P.AT.tiles.size();
-  const int ntmax = lp->ntA > lp->ntT ? lp->ntA : lp->ntT;
-  RET(lp->alloc(&lp->A_rp, m + 1));
-  RET(lp->alloc(&lp->A_col, nz));
-  RET(lp->alloc(&lp->A_val, nz));
-  RET(lp->alloc(&lp->A_hat, nz));
-  RET(lp->alloc(&lp->T_rp, n + 1));
-  RET(lp->alloc(&lp->T_col, nz));
-  RET(lp->alloc(&lp->T_val, nz));
-  RET(lp->alloc(&lp->T_hat, nz));
-  RET(lp->alloc(&lp->A_tiles, lp->ntA));
-  RET(lp->alloc(&lp->T_tiles, lp->ntT));
+  RET(setup_mat(lp.get(), lp->A, P.A, st));
+  RET(setup_mat(lp.get(), lp->T, P.AT, st));
+  lp->ntA = lp->A.nblocks();
+  lp->ntT = lp->T.nblocks();
+  RET(lp->alloc(&lp->err, 1));
   RET(lp->alloc(&lp->b_int, m));
   RET(lp->alloc(&lp->sign, m));
   RET(lp->alloc(&lp->ge, m));
@@ -865,17 +948,7 @@ int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int
   RET(lp->alloc(&lp->scratch, 64));
   RET(lp->alloc(&lp->S, 1));
   RET(lp->alloc(&lp->rep, 1));
-  (void)ntmax;
-  CK(cudaMemcpyAsync(lp->A_rp, P.A.row_ptr.data(), (m + 1) * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->T_rp, P.AT.row_ptr.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, st));
-  if (nz) {
-    CK(cudaMemcpyAsync(lp->A_col, P.A.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(lp->A_val, P.A.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(lp->T_col, P.AT.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(lp->T_val, P.AT.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
-  }
-  CK(cudaMemcpyAsync(lp->A_tiles, P.A.tiles.data(), lp->ntA * sizeof(Tile), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->T_tiles, P.AT.tiles.data(), lp->ntT * sizeof(Tile), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(lp->err, 0, sizeof(int), st));
   CK(cudaMemcpyAsync(lp->b_int, P.b_int.data(), (size_t)m * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->sign, P.sign.data(), (size_t)m * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->ge, P.ge.data(), (size_t)m, cudaMemcpyHostToDevice, st));
@@ -937,7 +1010,7 @@ int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_re
   cudaStream_t st = lp->stream;
   const DevModel md = model_orig(lp);
   // Algorithm 1: new bounds and objective (columns), new senses (rows)
-  RET(launch_tiles(lp, true, lp->T_hat,
+  RET(launch_tiles(lp, true, true,
                    CornerColsOp{lp->y1, lp->x1, lp->col_perm, md, lp->lhat_c, lp->uhat_c, lp->chat_c, cp.eps_abs,
                                 cp.obj_scale, (unsigned long long)cp.obj_seed},
                    lp->pT, st));
@@ -1012,7 +1085,7 @@ int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z,
   }
   if (z) {
     // the unpermute below reads pi_w; the stream orders it after the ZOp pass
-    RET(launch_tiles(lp, true, lp->T_hat, ZOp{lp->y1, model_orig(lp), lp->pi_w}, nullptr, st));
+    RET(launch_tiles(lp, true, true, ZOp{lp->y1, model_orig(lp), lp->pi_w}, nullptr, st));
     k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, lp->pi_w, nullptr, nullptr, lp->tmp_n);
     lp->launches++;
     CKL();
@@ -1104,6 +1177,50 @@ int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void*
 }
 
 int64_t pdhgc_kernel_launches(const pdhgc_lp* lp) { return lp ? lp->launches : 0; }
+
+int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
+  if (!lp || iters < 1 || !ms_out) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
+  cudaStream_t st = lp->stream;
+  const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
+  // the replay must not stop on the phase's done flag or iteration limit
+  Scalars S;
+  CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));
+  const int saved_done = S.done;
+  const long long saved_max = S.max_iters;
+  const int zero = 0;
+  const long long big = (long long)1 << 62;
+  CK(cudaMemcpy(&lp->S->done, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&lp->S->max_iters, &big, sizeof(long long), cudaMemcpyHostToDevice));
+  std::vector<cudaEvent_t> ev(3 * (size_t)iters);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  int rc = PDHGC_OK;
+  for (int i = 0; i < iters && rc == PDHGC_OK; ++i) {
+    CK(cudaEventRecord(ev[3 * i], st));
+    rc = launch_tiles(lp, true, true, PrimalOp{lp->S, 0, lp->it.y, md, lp->it}, nullptr, st);
+    if (rc != PDHGC_OK) break;
+    CK(cudaEventRecord(ev[3 * i + 1], st));
+    rc = launch_tiles(lp, false, true, DualOp{lp->S, 0, lp->it.xbar, md, lp->it}, nullptr, st);
+    if (rc != PDHGC_OK) break;
+    CK(cudaEventRecord(ev[3 * i + 2], st));
+  }
+  CK(cudaStreamSynchronize(st));
+  double tp = 0.0, td = 0.0;
+  for (int i = 0; i < iters && rc == PDHGC_OK; ++i) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
+    CK(cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]));
+    tp += a;
+    td += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  CK(cudaMemcpy(&lp->S->done, &saved_done, sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&lp->S->max_iters, &saved_max, sizeof(long long), cudaMemcpyHostToDevice));
+  if (rc != PDHGC_OK) return rc;
+  ms_out[0] = tp / iters;
+  ms_out[1] = td / iters;
+  return PDHGC_OK;
+}
 
 void pdhgc_lp_destroy(pdhgc_lp* lp) {
   if (!lp) return;

@@ -89,6 +89,7 @@ _sig = {
     "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
     "pdhgc_kernel_launches": (C.c_int64, [_vp]),
+    "pdhgc_profile_iteration": (C.c_int, [_vp, C.c_int32, _vp]),
     "pdhgc_lp_destroy": (None, [_vp]),
     "pdhgc_strerror": (C.c_char_p, [C.c_int]),
     "pdhgc_last_error_detail": (C.c_char_p, []),
@@ -213,6 +214,13 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    def profile_iteration(self, iters: int = 20):
+        """Mean ms per launch of the primal (A' pass) and dual (A pass)
+        kernels over `iters` event-bracketed replays (advances the iterates)."""
+        out = np.zeros(2)
+        _check(lib.pdhgc_profile_iteration(self._h, int(iters), out.ctypes.data), "pdhgc_profile_iteration")
+        return float(out[0]), float(out[1])
 
 
 def lp_create(m, n, row_ptr, col_idx, val, b, c, lb=None, ub=None, sense=None, stream=None) -> LP:
