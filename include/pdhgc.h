@@ -216,6 +216,28 @@ int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double
 int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalars, int on_device);
 
 /*
+ * pdhgc_kkt_eval — the Section 2 residuals, objectives and relative ratios,
+ * and the Section 2.1 / 4.2 metrics, of a caller-supplied point (x, y) on an
+ * LP given as device arrays, without creating a handle.  The LP arguments
+ * mean what they mean for pdhgc_lp_create (row_ptr int64[m+1], col_idx
+ * int32[nnz], val, b, c; lb, ub, sense may be NULL for their defaults); x
+ * (n) and y (m) are in the user's scale with the dual signs of this header
+ * (y <= 0 on '<' rows, y >= 0 on '>' rows); every pointer is a device
+ * pointer.  z = proj(c - A'y).  Fills the numeric fields of *out (host);
+ * status, iters and the phase fields are zero.  Work is enqueued on
+ * `cuda_stream`, which the call synchronises.  The inputs are not
+ * validated beyond NULL and size checks (use pdhgc_lp_create for that).
+ * Scratch (n + 13 * 1024 + 16 doubles) is taken with cudaMallocAsync on
+ * the stream and released before returning.  A'y is accumulated with
+ * atomic adds, so results may differ from run to run in the last bits.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int pdhgc_kkt_eval(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                   const double* val, const double* b, const double* c, const double* lb, const double* ub,
+                   const int8_t* sense, const double* x, const double* y, pdhgc_report* out,
+                   void* cuda_stream);
+
+/*
  * pdhgc_uniform — out[j] = obj_scale * U_j for j < n, where U_j is the top 53
  * bits of the (j+1)-th SplitMix64 output from state `seed`, times 2^-53
  * (the corner objective of Algorithm 1).  `out` is a device pointer; the

@@ -13,17 +13,24 @@
 #include "../../include/pdhgc.h"
 #include "host_prep.h"
 #include "kernels.cuh"
+#include "kkt_eval.h"
 
 using namespace pdhgc;
 
 namespace {
-
 thread_local std::string g_detail;
+}  // namespace
 
-int set_err(int code, const std::string& d) {
+namespace pdhgc {
+int set_error_detail(int code, const std::string& d) {
   g_detail = d;
   return code;
 }
+}  // namespace pdhgc
+
+namespace {
+
+int set_err(int code, const std::string& d) { return set_error_detail(code, d); }
 
 #define CK(call)                                                                          \
   do {                                                                                    \

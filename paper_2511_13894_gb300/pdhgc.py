@@ -88,6 +88,8 @@ _sig = {
     "pdhgc_get_iterates": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
+    "pdhgc_kkt_eval": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 _vp, C.POINTER(Report), _vp]),
     "pdhgc_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_profile_iteration": (C.c_int, [_vp, C.c_int32, _vp]),
     "pdhgc_lp_destroy": (None, [_vp]),
@@ -271,6 +273,36 @@ def lp_from_dict(lp: dict, stream=None, device=False) -> LP:
         arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
                 for a, dt in zip(arrs, dts)]
     return lp_create(lp["m"], lp["n"], *arrs, stream=stream)
+
+
+def _device_lp_args(lp: dict, x, y):
+    """CUDA tensors for the LP arrays of a generator dict and for (x, y)."""
+    torch = _torch()
+    dts = {"row_ptr": torch.int64, "col_idx": torch.int32, "val": torch.float64, "b": torch.float64,
+           "c": torch.float64, "lb": torch.float64, "ub": torch.float64, "sense": torch.int8}
+    t = {}
+    for k, dt in dts.items():
+        a = lp.get(k)
+        t[k] = None if a is None else torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    t["x"] = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).to(device="cuda")
+    t["y"] = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float64)).to(device="cuda")
+    return t
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def kkt_eval(lp: dict, x, y) -> dict:
+    """pdhgc_kkt_eval of the point (x, y) (user scale) on a generator-dict LP."""
+    t = _device_lp_args(lp, x, y)
+    r = Report()
+    nnz = int(lp["row_ptr"][-1])
+    _check(lib.pdhgc_kkt_eval(int(lp["m"]), int(lp["n"]), nnz, _ptr(t["row_ptr"]), _ptr(t["col_idx"]),
+                              _ptr(t["val"]), _ptr(t["b"]), _ptr(t["c"]), _ptr(t["lb"]), _ptr(t["ub"]),
+                              _ptr(t["sense"]), _ptr(t["x"]), _ptr(t["y"]), C.byref(r), _current_stream()),
+           "pdhgc_kkt_eval")
+    return r.as_dict()
 
 
 def uniform(seed: int, n: int, obj_scale: float = 1.0):

@@ -169,3 +169,24 @@ def test_iteration_and_time_limits_stop_the_device_loop():
     rep = g.solve(max_iters=10**9, eps_rel=1e-300, time_limit_s=0.05)
     assert rep["status_name"] == "TIME_LIMIT"
     assert rep["seconds"] < 5.0
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed"])
+def test_kkt_eval_of_a_point_matches_oracle(name):
+    # the oracle's phase-1 point, evaluated on the GPU without a handle
+    lp = _lp_cases()[name]()
+    ref = oracle.solve(lp, dict(max_iters=640))
+    model = ref["model"]
+    x, y, _ = oracle.unscale(model, ref["x_hat"], ref["y_hat"])
+    orep = oracle.kkt_report(model, ref["x_hat"], ref["y_hat"])
+    rep = P.kkt_eval(lp, x, y)
+    scale = 1.0 + float(np.linalg.norm(lp["b"])) + float(np.linalg.norm(lp["c"]))
+    for k in ("rP2", "rD2", "rPinf", "rDinf", "pobj", "dobj", "gap"):
+        assert abs(rep[k] - orep[k]) <= 1e-9 * (scale + abs(orep[k])), (k, rep[k], orep[k])
+    for k in ("rel_p", "rel_d", "rel_gap"):
+        assert abs(rep[k] - orep[k]) <= 1e-9 * (1.0 + abs(orep[k])), k
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure", "primal_push_est", "dual_push_est"):
+        assert rep[k] == orep[k], k
+    # the constructed optimum is optimal: every residual and the gap vanish
+    rep = P.kkt_eval(lp, lp["x_star"], lp["y_star"])
+    assert rep["rel_kkt"] <= 1e-12
