@@ -238,6 +238,34 @@ int pdhgc_kkt_eval(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
                    void* cuda_stream);
 
 /*
+ * pdhgc_kkt_eval_noalloc — pdhgc_kkt_eval for callers that cannot allocate
+ * device memory: services that run under a fixed device-memory budget,
+ * applications whose device memory is owned by a pool or framework allocator
+ * that must account for every byte, and code paths where the implicit
+ * synchronisation of cudaMalloc / cudaFree is not acceptable.  (The paper
+ * has no counterpart; this is a library convenience.)  Same arguments,
+ * results and errors as pdhgc_kkt_eval, plus:
+ *  - n must be <= 262,144 (1 << 18); a larger n returns PDHGC_ERR_TOO_LARGE
+ *    without touching the device.
+ *  - The scratch is a file-scope device array of 2,203,776 bytes ((1 << 18)
+ *    + 13 * 1024 + 16 doubles) that every GPU which loads the library holds
+ *    until the process exits.  The call itself allocates nothing and calls
+ *    no cudaMalloc, cudaFree or allocating library routine.
+ *  - The first call on a device (the current device of the calling thread)
+ *    looks up that array's device address with cudaGetSymbolAddress; make
+ *    that first call before any stream capture begins.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents; every call clears the part that must start at zero.  Calls
+ *    that overlap on the GPU (different streams, or different host threads
+ *    without ordering) race on the array and give wrong results: serialise
+ *    them on one stream.
+ */
+int pdhgc_kkt_eval_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                           const double* val, const double* b, const double* c, const double* lb,
+                           const double* ub, const int8_t* sense, const double* x, const double* y,
+                           pdhgc_report* out, void* cuda_stream);
+
+/*
  * pdhgc_uniform — out[j] = obj_scale * U_j for j < n, where U_j is the top 53
  * bits of the (j+1)-th SplitMix64 output from state `seed`, times 2^-53
  * (the corner objective of Algorithm 1).  `out` is a device pointer; the

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "../../include/pdhgc.h"
@@ -252,3 +253,71 @@ extern "C" int pdhgc_kkt_eval(int32_t m, int32_t n, int64_t nnz, const int64_t* 
   return PDHGC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// pdhgc_kkt_eval_noalloc: the same evaluation with its scratch in a
+// file-scope device array instead of cudaMallocAsync, for callers that must
+// not allocate device memory (see include/pdhgc.h).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int32_t kNoAllocMaxN = 1 << 18;  // largest n the static scratch holds
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxN + (size_t)(pdhgc::kEvRowQ + pdhgc::kEvColQ) *
+                                                               pdhgc::kEvBlocks + pdhgc::kEvOut;
+
+// Shared by every call on a device and kept until the process exits; each call
+// overwrites all of it that it reads (the A'y accumulator is zeroed first).
+static __device__ __align__(256) double g_kkt_eval_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// device address of g_kkt_eval_scratch for the current device, looked up
+// once per device with that device current
+int scratch_for_current_device(double** out, std::string& detail) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    detail = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return PDHGC_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    detail = "device ordinal out of range";
+    return PDHGC_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_kkt_eval_scratch);
+    if (e != cudaSuccess || !p) {
+      detail = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return PDHGC_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return PDHGC_OK;
+}
+
+}  // namespace
+
+extern "C" int pdhgc_kkt_eval_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                                      const int32_t* col_idx, const double* val, const double* b, const double* c,
+                                      const double* lb, const double* ub, const int8_t* sense, const double* x,
+                                      const double* y, pdhgc_report* out, void* cuda_stream) {
+  std::string detail;
+  int rc = pdhgc::kkt_eval_check(m, n, nnz, row_ptr, col_idx, val, b, c, x, y, out, detail);
+  if (rc != PDHGC_OK) return pdhgc::set_error_detail(rc, detail);
+  if (n > kNoAllocMaxN)
+    return pdhgc::set_error_detail(PDHGC_ERR_TOO_LARGE,
+                                   "pdhgc_kkt_eval_noalloc: n = " + std::to_string(n) +
+                                       " exceeds the static scratch capacity of " +
+                                       std::to_string(kNoAllocMaxN) + " columns; use pdhgc_kkt_eval");
+  double* scratch = nullptr;
+  rc = scratch_for_current_device(&scratch, detail);
+  if (rc != PDHGC_OK) return pdhgc::set_error_detail(rc, detail);
+  pdhgc::EvalInput in{m, n, row_ptr, col_idx, val, b, c, lb, ub, sense, x, y};
+  rc = pdhgc::kkt_eval_run(in, scratch, static_cast<cudaStream_t>(cuda_stream), out, detail);
+  if (rc != PDHGC_OK) return pdhgc::set_error_detail(rc, detail);
+  return PDHGC_OK;
+}
