@@ -84,6 +84,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the SpMV kernel and the data layout it reads: a recorded ncu traffic figure is
+# valid only while these files are unchanged
+KERNEL_SOURCES = ("kernels.cuh", "host_prep.h", "host_prep.cpp")
+
+
 def traffic_record():
     """dram bytes per launch recorded from an ncu capture (profiles/ncu_traffic.txt),
     valid only while the kernel sources hash to the recorded value."""
@@ -99,7 +104,7 @@ def traffic_record():
                 rec[k.strip()] = v.strip()
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2511_13894_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     if rec.get("sources_sha256") != h.hexdigest():
