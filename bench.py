@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="power_law_m100k_n400k")
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "both"], default="both",
+                    help="fp64: plain FP64 only; fp32: FP32 bulk only; both: FP64 headline plus an "
+                         "fp32_bulk block measured on the same workload")
     ap.add_argument("--phase1-max-iters", type=int, default=1_000_000)
     ap.add_argument("--corner-max-iters", type=int, default=200_000)
     ap.add_argument("--corner-seed", type=int, default=1)
@@ -168,14 +170,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8):
+def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8, s_sum=8):
     """Bytes one PDHG iteration must move (gathers counted once per element):
     primal (A' pass): values + indices, row pointers, reads of c, l, u, x and
     the running sum, writes of x, x_bar and the running sum, y gathered once;
     dual (A pass): values + indices, row pointers, reads of b, y, the running
-    sum and the sense byte, writes of y and the running sum, x_bar gathered once."""
-    primal = nnz * (s_v + 4) + n * 4 + n * 8 * s_x + m * s_x
-    dual = nnz * (s_v + 4) + m * 4 + m * (5 * s_x + 1) + n * s_x
+    sum and the sense byte, writes of y and the running sum, x_bar gathered once.
+    s_v, s_x, s_sum: bytes of a matrix value, an iterate / model entry and a
+    running-sum entry (8, 8, 8 in FP64; 4, 4, 8 in FP32 bulk)."""
+    primal = nnz * (s_v + 4) + n * 4 + n * (6 * s_x + 2 * s_sum) + m * s_x
+    dual = nnz * (s_v + 4) + m * 4 + m * (3 * s_x + 2 * s_sum + 1) + n * s_x
     return primal, dual
 
 
@@ -278,7 +282,7 @@ def main():
     stream = torch.cuda.current_stream()
     g = P.lp_from_dict(lp_dict, stream=stream.cuda_stream)
     if args.mode == "kernels":
-        g.solve(max_iters=64)
+        g.solve(max_iters=64, precision=P.FP32_BULK if args.precision == "fp32" else P.FP64)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("pdhg_kernels")
         ms = g.profile_iteration(args.profile_iters)
@@ -286,83 +290,118 @@ def main():
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"mode": "kernels", "workload": args.workload, "primal_ms": ms[0], "dual_ms": ms[1]}))
         return
-    params = P.default_params(max_iters=args.phase1_max_iters)
     cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        r1 = g.solve(params)
-        rc = g.corner_phase(cparams)
-        return r1, rc
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         uuid = None
-    clocks = ClockSampler(uuid)
-    clocks.start()
-    launches0 = g.kernel_launches()
-    step_ms, iters, reps = [], [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # L2 flush: 512 MiB write between steps
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r1, rc = step()
-        e1.record(stream)
-        e1.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        iters.append(r1["iters"] + rc["iters"])
-        reps.append((r1, rc))
-    launches = g.kernel_launches() - launches0
-    clk = clocks.stop()
-    total_ms = sum(step_ms)
-    total_iters = sum(iters)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_iters_all = float(it.item())
-    else:
-        total_iters_all = float(total_iters)
-    value = total_iters_all / (total_ms * 1e-3)
-
-    # kernel durations: event-bracketed replays of the two iteration kernels
-    ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
-    b_primal, b_dual = algorithmic_bytes(m, n, nnz)
-    f_primal, f_dual = fp64_ops(m, n, nnz)
-    dom = "primal" if ms_primal >= ms_dual else "dual"
-    ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
     peak, peak_kind = measured_peaks()
-    achieved = b_dom / (ms_dom * 1e-3) / 1e9
-    tr = traffic_record()
-    roofline = {
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": (float(tr["dram_bytes_per_launch_" + dom]) if tr and ("dram_bytes_per_launch_" + dom) in tr
-                    else None),
-        "kernel": f"tile_spmv<{'PrimalOp' if dom == 'primal' else 'DualOp'}> ({dom} step)",
-        "peak_source": f"{peak_kind} hbm_gbs",
-        "algorithmic_bytes_per_launch": b_dom, "launch_ms": ms_dom,
-        "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
-        "fp64": {"ops_per_launch": f_dom, "achieved_tflops": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12,
-                 "peak_tflops": FP64_PEAK_TFLOPS,
-                 "frac": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                 "note": "every FP64 pipe operation counted as one FMA (2 flops) against 1.25 TFLOP/s"},
-    }
-    if roofline["fp64"]["frac"] > roofline["frac"]:
-        roofline["bound"] = "alu"
-    r1, rc = reps[-1]
+
+    def run_arm(precision):
+        params = P.default_params(max_iters=args.phase1_max_iters, precision=precision)
+
+        def step():
+            r1 = g.solve(params)
+            rc = g.corner_phase(cparams)
+            return r1, rc
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        launches0 = g.kernel_launches()
+        step_ms, iters, reps = [], [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # L2 flush: 512 MiB write between steps
+            torch.cuda.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r1, rc = step()
+            e1.record(stream)
+            e1.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            iters.append(r1["iters"] + rc["iters"])
+            reps.append((r1, rc))
+        launches = g.kernel_launches() - launches0
+        clk = clocks.stop()
+        total_ms = sum(step_ms)
+        total_iters = sum(iters)
+        if dist is not None:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
+            dist.all_reduce(it, op=dist.ReduceOp.SUM)
+            total_iters_all = float(it.item())
+        else:
+            total_iters_all = float(total_iters)
+        value = total_iters_all / (total_ms * 1e-3)
+        # kernel durations: event-bracketed replays of the two iteration kernels
+        ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
+        if precision == P.FP64:
+            b_primal, b_dual = algorithmic_bytes(m, n, nnz)
+            f_primal, f_dual = fp64_ops(m, n, nnz)
+        else:
+            b_primal, b_dual = algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8)
+            f_primal, f_dual = n, m  # FP64 ops left per launch: the running-sum adds
+        dom = "primal" if ms_primal >= ms_dual else "dual"
+        ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
+        achieved = b_dom / (ms_dom * 1e-3) / 1e9
+        tr = traffic_record() if precision == P.FP64 else None
+        key = "dram_bytes_per_launch_" + dom
+        roofline = {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": float(tr[key]) if tr and key in tr else None,
+            "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
+                      + ("32>" if precision == P.FP32_BULK else ">") + f" ({dom} step)",
+            "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": b_dom, "launch_ms": ms_dom,
+            "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
+            "fp64": {"ops_per_launch": f_dom, "achieved_tflops": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12,
+                     "peak_tflops": FP64_PEAK_TFLOPS,
+                     "frac": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "note": "every FP64 pipe operation counted as one FMA (2 flops) against 1.25 TFLOP/s"},
+        }
+        if roofline["fp64"]["frac"] > roofline["frac"]:
+            roofline["bound"] = "alu"
+        r1, rc = reps[-1]
+        return dict(value=value, total_ms=total_ms, total_iters=total_iters, launches=launches, clocks=clk,
+                    roofline=roofline, r1=r1, rc=rc, params=params)
+
+    def summary(res):
+        r1, rc = res["r1"], res["rc"]
+        return {
+            "phase1": {"status": r1["status_name"], "iters": r1["iters"], "restarts": r1["restarts"],
+                       "rel_kkt": r1["rel_kkt"], "seconds": r1["seconds"], "corner_measure": r1["corner_measure"],
+                       "candidates": r1["candidates"], "off_bound_p": r1["off_bound_p"],
+                       "should_corner": r1["should_corner"]},
+            "corner": {"status": rc["status_name"], "iters": rc["iters"], "restarts": rc["restarts"],
+                       "seconds": rc["seconds"], "corner_measure": rc["corner_measure"],
+                       "candidates": rc["candidates"], "off_bound_p": rc["off_bound_p"],
+                       "rel_p": rc["rel_p"], "rel_kkt": rc["rel_kkt"]},
+            "us_per_iter": res["total_ms"] * 1e3 / max(1, res["total_iters"]),
+        }
+
+    arms = {}
+    if args.precision in ("fp64", "both"):
+        arms["fp64"] = run_arm(P.FP64)
+    if args.precision in ("fp32", "both"):
+        arms["fp32"] = run_arm(P.FP32_BULK)
+    head = arms["fp64"] if "fp64" in arms else arms["fp32"]
+    params = head["params"]
+    value = head["value"]
+    total_ms = head["total_ms"]
+    launches = head["launches"]
+    clk = head["clocks"]
+    roofline = head["roofline"]
 
     # end-to-end through the public API with host buffers (pinned), per step:
     # H2D of the inputs in lp_create, solve, corner, D2H of x, y, z
@@ -404,30 +443,31 @@ def main():
         cpu = cpu_baseline_sample(lp_dict, args.cpu_iters)
 
     if rank == 0:
+        head_is_fp64 = "fp64" in arms
         out = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "m": m, "n": n, "nnz": nnz, "precision": args.precision,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head_is_fp64 else "f32+f32x2acc",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "m": m, "n": n, "nnz": nnz,
+                       "precision": "fp64" if head_is_fp64 else "fp32_bulk",
                        "phase1_max_iters": args.phase1_max_iters, "corner_max_iters": args.corner_max_iters,
                        "corner_seed": args.corner_seed, "eps_rel": 1e-6,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
-            "phase1": {"status": r1["status_name"], "iters": r1["iters"], "restarts": r1["restarts"],
-                       "rel_kkt": r1["rel_kkt"], "seconds": r1["seconds"], "corner_measure": r1["corner_measure"],
-                       "candidates": r1["candidates"], "off_bound_p": r1["off_bound_p"],
-                       "should_corner": r1["should_corner"]},
-            "corner": {"status": rc["status_name"], "iters": rc["iters"], "restarts": rc["restarts"],
-                       "seconds": rc["seconds"], "corner_measure": rc["corner_measure"],
-                       "candidates": rc["candidates"], "off_bound_p": rc["off_bound_p"],
-                       "rel_p": rc["rel_p"], "rel_kkt": rc["rel_kkt"]},
-            "us_per_iter": total_ms * 1e3 / max(1, total_iters),
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
         }
+        out.update(summary(head))
+        out.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                    "clocks": clk})
+        if head_is_fp64 and "fp32" in arms:
+            f = arms["fp32"]
+            blk = {"value": f["value"], "unit": "iters/s", "dtype": "f32 values and iterates, f32x2 row sums, "
+                                                                   "f64 running sums and KKT",
+                   "time_to_corner_s": f["total_ms"] / args.steps * 1e-3,
+                   "speedup_vs_fp64_time_to_corner": (total_ms / f["total_ms"]) if f["total_ms"] > 0 else None,
+                   "roofline": f["roofline"], "gpu_launches": f["launches"], "clocks": f["clocks"]}
+            blk.update(summary(f))
+            out["fp32_bulk"] = blk
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

@@ -33,7 +33,9 @@ def _stale(lib, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compiles and links libpdhgc.so; `extra_flags` are passed to nvcc (e.g.
+    -DPDHGC_GATHER_BATCH=16 for a tuning build)."""
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(HERE, "..", "include", "pdhgc.h"))
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(objdir, os.path.basename(s) + ".o")
         objs.append(o)
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-               "-diag-suppress", "177", "-c", s, "-o", o]
+               "-diag-suppress", "177", *extra_flags, "-c", s, "-o", o]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for cmd, p in procs:
         out, _ = p.communicate()

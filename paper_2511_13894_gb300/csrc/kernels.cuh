@@ -136,38 +136,52 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <int NG>
+template <class T, int NG>
 struct GV {
-  double v[NG];
+  T v[NG];
 };
 
-struct SpmvMat {
+// VT: value type of the matrix copy a pass reads (double, or float for the
+// FP32-bulk iteration)
+template <class VT>
+struct SpmvMatT {
   const int* __restrict__ row_ptr;
   const int* __restrict__ col;
-  const double* __restrict__ val;        // CSR values (CTA and warp rows)
+  const VT* __restrict__ val;            // CSR values (CTA and warp rows)
   const int* __restrict__ slice_ptr;
   const int* __restrict__ slice_w;
   const int* __restrict__ scol;          // SELL-32 indices
-  const double* __restrict__ sval;       // SELL-32 values
+  const VT* __restrict__ sval;           // SELL-32 values
   const SellBlock* __restrict__ sell_blocks;
   int rows, cta_rows, long_rows, nslices;
   int nb_cta, nb_warp, nb_sell;
 };
+using SpmvMat = SpmvMatT<double>;
 
-constexpr int kBatch = 8;  // gathers in flight per lane
+// gathers in flight per lane, and the minimum resident blocks per SM the
+// register allocation must allow (tuning knobs, overridable at build time)
+#ifndef PDHGC_GATHER_BATCH
+#define PDHGC_GATHER_BATCH 8
+#endif
+#ifndef PDHGC_MIN_BLOCKS
+#define PDHGC_MIN_BLOCKS 1
+#endif
+constexpr int kBatch = PDHGC_GATHER_BATCH;
 
 // acc += sum over k = k0, k0+step, ... < k1 of val[k] * gathered(col[k]), in
 // that order, with kBatch gathers in flight per lane (CSR rows)
 template <class Op>
 __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& acc, double rc,
-                                               const double* __restrict__ val, const int* __restrict__ col,
-                                               int k0, int k1, int step) {
+                                               const typename Op::VT* __restrict__ val,
+                                               const int* __restrict__ col, int k0, int k1, int step) {
   constexpr int NG = Op::NG;
+  using VT = typename Op::VT;
+  using GT = typename Op::GT;
   int k = k0;
   for (; k + (kBatch - 1) * step < k1; k += kBatch * step) {
-    double v[kBatch];
+    VT v[kBatch];
     int c[kBatch];
-    GV<NG> g[kBatch];
+    GV<GT, NG> g[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       v[u] = val[k + u * step];
@@ -181,7 +195,7 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
     for (int u = 0; u < kBatch; ++u) op.accum(acc, rc, v[u], g[u]);
   }
   for (; k < k1; k += step) {
-    GV<NG> g;
+    GV<GT, NG> g;
     const int c = col[k];
 #pragma unroll
     for (int i = 0; i < NG; ++i) g.v[i] = __ldg(op.gsrc(i) + c);
@@ -190,7 +204,10 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
 }
 
 template <class Op, bool kPdl>
-__global__ void __launch_bounds__(kBlock) spmv(SpmvMat M, Op op, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
+    spmv(SpmvMatT<typename Op::VT> M, Op op, double* __restrict__ partials) {
+  using VT = typename Op::VT;
+  using GT = typename Op::GT;
   constexpr int NG = Op::NG;
   constexpr int NQ = Op::NQ;
   constexpr int NQS = NQ > 0 ? NQ : 1;
@@ -272,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) spmv(SpmvMat M, Op op, double* __restr
       }
     }
     const int jend = min(je, len);  // this lane's last column + 1
-    double v[kBatch];
+    VT v[kBatch];
     int c[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(kBlock) spmv(SpmvMat M, Op op, double* __restr
           }
         }
       }
-      GV<NG> g[kBatch];
+      GV<GT, NG> g[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; ++u)
         if (j + u < jend)
@@ -360,8 +377,10 @@ struct PrimalOp {
   __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return y; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double*) const {
     const double tau = S->tau;
     const double g = md.chat[j] - a.v[0];
@@ -386,8 +405,10 @@ struct DualOp {
   __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return xbar; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int i, const Acc& a, double*) const {
     const double sigma = S->sigma;
     double yn = w.y[i] + sigma * (md.bhat[i] - a.v[0]);
@@ -414,8 +435,10 @@ struct EvalRowsOp {
   __device__ bool skip() const { return S->done; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 2;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int i) const { return i == 0 ? x : sum_x; }
-  __device__ void accum(Acc& a, double, double v, const GV<2>& g) const {
+  __device__ void accum(Acc& a, double, double v, const GV<double, 2>& g) const {
     a.v[0] = fma(v, g.v[0], a.v[0]);
     a.v[1] = fma(v, g.v[1], a.v[1]);
   }
@@ -457,8 +480,10 @@ struct EvalColsOp {
   __device__ bool skip() const { return S->done; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 2;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int i) const { return i == 0 ? y : sum_y; }
-  __device__ void accum(Acc& a, double, double v, const GV<2>& g) const {
+  __device__ void accum(Acc& a, double, double v, const GV<double, 2>& g) const {
     a.v[0] = fma(v, g.v[0], a.v[0]);
     a.v[1] = fma(v, g.v[1], a.v[1]);
   }
@@ -501,8 +526,10 @@ struct ScaleMaxOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int r) const { return d_own[r]; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return d_other; }
-  __device__ void accum(Acc& a, double rc, double v, const GV<1>& g) const {
+  __device__ void accum(Acc& a, double rc, double v, const GV<double, 1>& g) const {
     const double d = g.v[0];
     const double e = kTransposed ? (d * fabs(v)) * rc : (rc * fabs(v)) * d;
     a.v[0] = fmax(a.v[0], e);
@@ -523,8 +550,10 @@ struct ScaleSumOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int r) const { return d_own[r]; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return d_other; }
-  __device__ void accum(Acc& a, double rc, double v, const GV<1>& g) const {
+  __device__ void accum(Acc& a, double rc, double v, const GV<double, 1>& g) const {
     const double d = g.v[0];
     const double e = kTransposed ? (d * fabs(v)) * rc : (rc * fabs(v)) * d;
     a.v[0] += e;
@@ -546,8 +575,10 @@ struct SpmvOp {
   __device__ bool skip() const { return S->pi_zero != 0; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return v; }
-  __device__ void accum(Acc& a, double, double val, const GV<1>& g) const { a.v[0] = fma(val, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double val, const GV<double, 1>& g) const { a.v[0] = fma(val, g.v[0], a.v[0]); }
   __device__ void epilogue(int r, const Acc& a, double* part) const {
     out[r] = a.v[0];
     if constexpr (kNorm) part[0] += a.v[0] * a.v[0];
@@ -567,8 +598,10 @@ struct ReportRowsOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return x; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int i, const Acc& a, double* part) const {
     const double b = md.bhat[i], dr = md.Dr[i];
     const bool ge = md.ge[i];
@@ -603,8 +636,10 @@ struct ReportColsOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return y; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double* part) const {
     const double c = md.chat[j], l = md.lhat[j], u = md.uhat[j], dc = md.Dc[j];
     const double lam = c - a.v[0];
@@ -656,8 +691,10 @@ struct CornerColsOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return y1; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double* part) const {
     const double dc = md.Dc[j];
     const double lam = md.chat[j] - a.v[0];
@@ -691,5 +728,129 @@ __device__ double block_fold(const double* __restrict__ p, int ntiles, bool is_m
   for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = is_max ? fmax(tot, s_tmp[w]) : tot + s_tmp[w];
   return tot;  // same value in every thread
 }
+
+
+// ---------------------------------------------------------------------------
+// FP32-bulk iteration (precision PDHGC_FP32_BULK)
+//
+// Matrix values, x, x_bar, y and the model vectors are FP32; each product
+// v * g is formed exactly as a float pair (p, fma(v, g, -p)) and the row sum
+// is kept as an unevaluated float pair (hi, lo) with Knuth's TwoSum, so the
+// only error of a row sum is that of its FP32 inputs.  The running sums of
+// the averages stay FP64.  Every KKT, gap, restart and step-size quantity is
+// computed in FP64 by the evaluation operators above, from FP64 copies.
+// ---------------------------------------------------------------------------
+struct SumFF {
+  float hi[1], lo[1];
+  __device__ __forceinline__ void zero() {
+    hi[0] = 0.f;
+    lo[0] = 0.f;
+  }
+  // (hi, lo) += (a, b): TwoSum of the high parts, low parts added
+  __device__ __forceinline__ void add_pair(float a, float b) {
+    const float s = hi[0] + a;
+    const float bb = s - hi[0];
+    const float err = (hi[0] - (s - bb)) + (a - bb);
+    hi[0] = s;
+    lo[0] += err + b;
+  }
+  __device__ __forceinline__ void add(const SumFF& o) { add_pair(o.hi[0], o.lo[0]); }
+  __device__ __forceinline__ SumFF shfl_xor(unsigned mask, int off) const {
+    SumFF r;
+    r.hi[0] = __shfl_xor_sync(mask, hi[0], off);
+    r.lo[0] = __shfl_xor_sync(mask, lo[0], off);
+    return r;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi[0] + (double)lo[0]; }
+};
+
+__device__ __forceinline__ void ff_fma(SumFF& a, float v, float g) {
+  const float p = v * g;
+  const float e = fmaf(v, g, -p);  // exact: v * g = p + e
+  a.add_pair(p, e);
+}
+
+// float clamp on the integer pipe (same ordering key as dkey)
+__device__ __forceinline__ int fkey(float x) {
+  const int b = __float_as_int(x);
+  return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float clamp_f(float x, float lo, float hi) {
+  const int k = fkey(x);
+  if (k < fkey(lo)) return lo;
+  if (k > fkey(hi)) return hi;
+  return x;
+}
+
+struct DevModel32 {
+  const float* chat;
+  const float* lhat;
+  const float* uhat;
+  const float* bhat;
+  const int8_t* ge;
+};
+
+struct DevIter32 {
+  float* x;
+  float* y;
+  float* xbar;
+  double* sum_x;
+  double* sum_y;
+};
+
+// x' = proj_[l,u](x - tau (c - A'y)),  x_bar = 2x' - x,  sum_x += x'  (FP32 bulk)
+struct PrimalOp32 {
+  using Acc = SumFF;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = float;
+  using GT = float;
+  const Scalars* S;
+  int it;
+  const float* __restrict__ y;
+  DevModel32 md;
+  DevIter32 w;
+  __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const float* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double*) const {
+    const float tau = (float)S->tau;
+    const float g = (float)((double)md.chat[j] - a.value());
+    const float xo = w.x[j];
+    const float xn = clamp_f(fmaf(-tau, g, xo), md.lhat[j], md.uhat[j]);
+    w.xbar[j] = 2.0f * xn - xo;
+    w.sum_x[j] += (double)xn;
+    w.x[j] = xn;
+  }
+};
+
+// y' = y + sigma (b - A x_bar), y' >= 0 on '>' rows,  sum_y += y'  (FP32 bulk)
+struct DualOp32 {
+  using Acc = SumFF;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = float;
+  using GT = float;
+  const Scalars* S;
+  int it;
+  const float* __restrict__ xbar;
+  DevModel32 md;
+  DevIter32 w;
+  __device__ bool skip() const { return S->done || S->k + it >= S->max_iters; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const float* gsrc(int) const { return xbar; }
+  __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
+  __device__ void epilogue(int i, const Acc& a, double*) const {
+    const float sigma = (float)S->sigma;
+    const float r = (float)((double)md.bhat[i] - a.value());
+    float yn = fmaf(sigma, r, w.y[i]);
+    if (md.ge[i] && __float_as_int(yn) < 0) yn = 0.0f;  // y >= 0 on '>' rows (sign bit test)
+    w.sum_y[i] += (double)yn;
+    w.y[i] = yn;
+  }
+};
 
 }  // namespace pdhgc

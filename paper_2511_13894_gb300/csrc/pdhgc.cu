@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -152,7 +153,14 @@ __global__ void k_pi_final(Scalars* S, const double* partials, int ntiles, doubl
 }
 
 // start of a phase: x (from x_start, or proj(0)), y = 0, sums = 0, restart point
-__global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start) {
+// FP32 copies of the iterates (FP32-bulk precision only; all null otherwise)
+struct Iter32 {
+  float* x;
+  float* xbar;
+  float* y;
+};
+
+__global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double x0 = x_start ? x_start[i] : fmin(fmax(0.0, md.lhat[i]), md.uhat[i]);
@@ -160,12 +168,34 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
     w.xbar[i] = x0;
     w.x_r[i] = x0;
     w.sum_x[i] = 0.0;
+    if (w32.x) {
+      w32.x[i] = (float)x0;
+      w32.xbar[i] = (float)x0;
+    }
   }
   if (i < m) {
     w.y[i] = 0.0;
     w.y_r[i] = 0.0;
     w.sum_y[i] = 0.0;
+    if (w32.y) w32.y[i] = 0.0f;
   }
+}
+
+// FP32 bulk: FP64 copies of the current iterates for the FP64 evaluation; x is
+// clamped to the FP64 bounds (an FP32-rounded bound may lie an ulp outside)
+__global__ void k_to64(const Scalars* S, int n, int m, const float* __restrict__ x32, const float* __restrict__ y32,
+                       const double* __restrict__ lhat, const double* __restrict__ uhat, double* __restrict__ x,
+                       double* __restrict__ y) {
+  if (S->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = fmin(fmax((double)x32[i], lhat[i]), uhat[i]);
+  if (i < m) y[i] = (double)y32[i];
+}
+
+// FP64 -> FP32 copy
+__global__ void k_to32(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
 }
 
 struct PhaseInit {
@@ -336,7 +366,7 @@ __global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, con
 }
 
 // restart: jump to the candidate, new restart point, sums cleared
-__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w) {
+__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter32 w32) {
   const int rt = S->restart_to;
   if (rt == 0 || S->done) return;
   const double inv_t = S->inv_t;
@@ -346,24 +376,30 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w) {
     w.x[i] = xn;
     w.x_r[i] = xn;
     w.sum_x[i] = 0.0;
+    if (w32.x && rt == 2) w32.x[i] = (float)xn;
   }
   if (i < m) {
     const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
     w.y[i] = yn;
     w.y_r[i] = yn;
     w.sum_y[i] = 0.0;
+    if (w32.y && rt == 2) w32.y[i] = (float)yn;
   }
 }
 
 // end of a phase: the returned point (current or average; the phase-1 x on a
 // corner limit)
+// The returned x is clamped to the phase's box: an average of FP32-bulk
+// iterates may lie an FP32 ulp outside it (a no-op for the FP64 iteration)
 __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo, double* yo,
-                           const double* x_fallback) {
+                           const double* x_fallback, const double* __restrict__ lhat,
+                           const double* __restrict__ uhat) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool avg = S->chosen == 1 && S->t > 0;
   const double inv_t = S->inv_t;
   const bool fallback = x_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
-  if (i < n) xo[i] = fallback ? x_fallback[i] : (avg ? w.sum_x[i] * inv_t : w.x[i]);
+  if (i < n)
+    xo[i] = fallback ? x_fallback[i] : fmin(fmax(avg ? w.sum_x[i] * inv_t : w.x[i], lhat[i]), uhat[i]);
   if (yo && i < m) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
 }
 
@@ -417,8 +453,10 @@ struct ZOp {
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
   __device__ const double* gsrc(int) const { return y; }
-  __device__ void accum(Acc& a, double, double v, const GV<1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   __device__ void epilogue(int j, const Acc& a, double*) const {
     z[j] = proj_dual(md.chat[j] - a.v[0], md.lhat[j], md.uhat[j]) / md.Dc[j];
   }
@@ -478,7 +516,12 @@ struct pdhgc_lp {
     int *rp = nullptr, *col = nullptr, *slice_ptr = nullptr, *slice_w = nullptr, *scol = nullptr, *smap = nullptr;
     SellBlock* sblocks = nullptr;
     double *val = nullptr, *hat = nullptr, *sval = nullptr, *shat = nullptr;  // original / scaled values
+    float *hat32 = nullptr, *shat32 = nullptr;  // FP32 copies of the scaled values (FP32 bulk)
     int nblocks() const { return nb_cta + nb_warp + nb_sell; }
+    SpmvMatT<float> view32() const {
+      return SpmvMatT<float>{rp,     col,  hat32,     slice_ptr, slice_w, scol,    shat32,
+                             sblocks, rows, cta_rows, long_rows, nslices, nb_cta, nb_warp, nb_sell};
+    }
     SpmvMat view(bool scaled) const {
       return SpmvMat{rp,   col,      scaled ? hat : val, slice_ptr, slice_w, scol,   scaled ? shat : sval,
                      sblocks, rows, cta_rows, long_rows, nslices,  nb_cta,  nb_warp, nb_sell};
@@ -493,6 +536,11 @@ struct pdhgc_lp {
   int *row_perm = nullptr, *col_perm = nullptr;
   // iterates
   DevIter it{};
+  // FP32-bulk buffers, allocated on the first FP32 solve
+  bool have32 = false;
+  Iter32 it32{};
+  float *chat32 = nullptr, *lhat32 = nullptr, *uhat32 = nullptr, *bhat32 = nullptr;
+  float *chat_c32 = nullptr, *lhat_c32 = nullptr, *uhat_c32 = nullptr;
   double *x1 = nullptr, *y1 = nullptr, *xc = nullptr;
   double *chat_c = nullptr, *lhat_c = nullptr, *uhat_c = nullptr;
   int8_t* ge_c = nullptr;
@@ -533,7 +581,12 @@ int launch_tiles(pdhgc_lp* lp, bool transposed, bool scaled, const Op& op, doubl
   const pdhgc_lp::Mat& M = transposed ? lp->T : lp->A;
   const int nb = M.nblocks();
   if (nb == 0) return PDHGC_OK;
-  const SpmvMat view = M.view(scaled);
+  SpmvMatT<typename Op::VT> view;
+  if constexpr (std::is_same<typename Op::VT, float>::value) {
+    view = M.view32();
+  } else {
+    view = M.view(scaled);
+  }
   if (pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
@@ -557,6 +610,12 @@ int launch_tiles(pdhgc_lp* lp, bool transposed, bool scaled, const Op& op, doubl
 DevModel model_orig(const pdhgc_lp* lp) {
   return DevModel{lp->chat, lp->lhat, lp->uhat, lp->bhat, lp->Dr, lp->Dc, lp->ge};
 }
+DevModel32 model32_orig(const pdhgc_lp* lp) {
+  return DevModel32{lp->chat32, lp->lhat32, lp->uhat32, lp->bhat32, lp->ge};
+}
+DevModel32 model32_corner(const pdhgc_lp* lp) {
+  return DevModel32{lp->chat_c32, lp->lhat_c32, lp->uhat_c32, lp->bhat32, lp->ge_c};
+}
 DevModel model_corner(const pdhgc_lp* lp) {
   return DevModel{lp->chat_c, lp->lhat_c, lp->uhat_c, lp->bhat, lp->Dr, lp->Dc, lp->ge_c};
 }
@@ -566,6 +625,49 @@ DevModel model_corner(const pdhgc_lp* lp) {
     int r_ = (x);              \
     if (r_ != PDHGC_OK) return r_; \
   } while (0)
+
+int to32(pdhgc_lp* lp, const double* a, float* b, long long n, cudaStream_t st) {
+  if (n <= 0) return PDHGC_OK;
+  k_to32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  lp->launches++;
+  CKL();
+  return PDHGC_OK;
+}
+
+// FP32-bulk buffers (allocated once per handle, on the first FP32 solve)
+int ensure_fp32(pdhgc_lp* lp) {
+  if (lp->have32) return PDHGC_OK;
+  const size_t n = lp->n, m = lp->m;
+  for (pdhgc_lp::Mat* M : {&lp->A, &lp->T}) {
+    RET(lp->alloc(&M->hat32, (size_t)lp->nnz + kPad));
+    RET(lp->alloc(&M->shat32, (size_t)M->nslots + kPad));
+  }
+  RET(lp->alloc(&lp->it32.x, n));
+  RET(lp->alloc(&lp->it32.xbar, n));
+  RET(lp->alloc(&lp->it32.y, m));
+  RET(lp->alloc(&lp->chat32, n));
+  RET(lp->alloc(&lp->lhat32, n));
+  RET(lp->alloc(&lp->uhat32, n));
+  RET(lp->alloc(&lp->bhat32, m));
+  RET(lp->alloc(&lp->chat_c32, n));
+  RET(lp->alloc(&lp->lhat_c32, n));
+  RET(lp->alloc(&lp->uhat_c32, n));
+  lp->have32 = true;
+  return PDHGC_OK;
+}
+
+// FP32 copies of the scaled matrix and model (after setup_scaling)
+int convert_fp32(pdhgc_lp* lp, cudaStream_t st) {
+  for (pdhgc_lp::Mat* M : {&lp->A, &lp->T}) {
+    RET(to32(lp, M->hat, M->hat32, lp->nnz, st));
+    RET(to32(lp, M->shat, M->shat32, M->nslots, st));
+  }
+  RET(to32(lp, lp->chat, lp->chat32, lp->n, st));
+  RET(to32(lp, lp->lhat, lp->lhat32, lp->n, st));
+  RET(to32(lp, lp->uhat, lp->uhat32, lp->n, st));
+  RET(to32(lp, lp->bhat, lp->bhat32, lp->m, st));
+  return PDHGC_OK;
+}
 
 // a0: Ruiz + Pock-Chambolle scaling, scaled copies, power iteration
 int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
@@ -630,12 +732,15 @@ int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st) {
 }
 
 // Runs one phase: init, the device-driven loop graph, finalize.
-int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const double* x_start, const double* cc2,
-              double* xo, double* yo, const double* x_fallback) {
+int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi,
+              const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback) {
   cudaStream_t st = lp->stream;
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
-  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start);
+  const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
+  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr};
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y};
+  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
   lp->launches += 2;
   CKL();
@@ -664,9 +769,19 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
   const int64_t before = lp->launches;
   int rc = PDHGC_OK;
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
-    rc = launch_tiles(lp, true, true, PrimalOp{lp->S, i, lp->it.y, md, lp->it}, nullptr, cs, true);
-    if (rc == PDHGC_OK)
-      rc = launch_tiles(lp, false, true, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs, true);
+    if (fp32) {
+      rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, i, lp->it32.y, md32, it32}, nullptr, cs, true);
+      if (rc == PDHGC_OK)
+        rc = launch_tiles(lp, false, true, DualOp32{lp->S, i, lp->it32.xbar, md32, it32}, nullptr, cs, true);
+    } else {
+      rc = launch_tiles(lp, true, true, PrimalOp{lp->S, i, lp->it.y, md, lp->it}, nullptr, cs, true);
+      if (rc == PDHGC_OK)
+        rc = launch_tiles(lp, false, true, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs, true);
+    }
+  }
+  if (rc == PDHGC_OK && fp32) {
+    k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, md.lhat, md.uhat, lp->it.x, lp->it.y);
+    lp->launches++;
   }
   if (rc == PDHGC_OK) {
     k_pre_check<<<1, 32, 0, cs>>>(lp->S);
@@ -675,7 +790,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
   }
   if (rc == PDHGC_OK) {
     k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
-    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it);
+    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32);
     lp->launches += 2;
   }
   cudaGraph_t captured = nullptr;
@@ -688,7 +803,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const PhaseInit& pi, const doubl
   std::unique_ptr<CUgraphExec_st, void (*)(cudaGraphExec_t)> e_guard(exec,
                                                                     [](cudaGraphExec_t e) { cudaGraphExecDestroy(e); });
   CK(cudaGraphLaunch(exec, st));
-  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback);
+  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat);
   lp->launches++;
   CKL();
   CK(cudaStreamSynchronize(st));
@@ -757,8 +872,8 @@ int check_params(const pdhgc_params* p) {
       p->ruiz_iters > 100 || p->power_iters < 1 || p->power_iters > 10000 || !(p->eta_factor > 0.0) ||
       !(p->eta_factor < 1.0) || !(p->time_limit_s > 0.0) || !(p->theta >= 0.0 && p->theta <= 1.0))
     return set_err(PDHGC_ERR_INVALID_ARG, "parameter out of range");
-  if (p->precision != PDHGC_FP64)
-    return set_err(PDHGC_ERR_INVALID_ARG, "precision not supported by this build");
+  if (p->precision != PDHGC_FP64 && p->precision != PDHGC_FP32_BULK)
+    return set_err(PDHGC_ERR_INVALID_ARG, "precision must be PDHGC_FP64 or PDHGC_FP32_BULK");
   return PDHGC_OK;
 }
 
@@ -980,6 +1095,10 @@ int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out) {
   lp->have_phase1 = false;
   lp->have_corner = false;
   RET(setup_scaling(lp, p));
+  if (p.precision == PDHGC_FP32_BULK) {
+    RET(ensure_fp32(lp));
+    RET(convert_fp32(lp, lp->stream));
+  }
   PhaseInit pi{};
   pi.eps_rel = p.eps_rel;
   pi.beta_suff = p.beta_suff;
@@ -995,7 +1114,7 @@ int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out) {
   pi.phase = 0;
   pi.stop_rule = 0;
   pi.use_cc2 = 0;
-  RET(run_phase(lp, model_orig(lp), pi, nullptr, nullptr, lp->x1, lp->y1, nullptr));
+  RET(run_phase(lp, model_orig(lp), model32_orig(lp), pi, nullptr, nullptr, lp->x1, lp->y1, nullptr));
   pdhgc_report r{};
   RET(fill_phase_report(lp, &r));
   RET(run_report(lp, lp->x1, lp->y1, &r));
@@ -1043,7 +1162,12 @@ int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_re
   pi.phase = 1;
   pi.stop_rule = cp.stop_rule;
   pi.use_cc2 = 1;
-  RET(run_phase(lp, model_corner(lp), pi, lp->x1, lp->scratch + 8, lp->xc, nullptr, lp->x1));
+  if (p.precision == PDHGC_FP32_BULK) {
+    RET(to32(lp, lp->chat_c, lp->chat_c32, lp->n, st));
+    RET(to32(lp, lp->lhat_c, lp->lhat_c32, lp->n, st));
+    RET(to32(lp, lp->uhat_c, lp->uhat_c32, lp->n, st));
+  }
+  RET(run_phase(lp, model_corner(lp), model32_corner(lp), pi, lp->x1, lp->scratch + 8, lp->xc, nullptr, lp->x1));
   pdhgc_report r{};
   RET(fill_phase_report(lp, &r));
   RET(run_report(lp, lp->xc, lp->y1, &r));
@@ -1190,6 +1314,9 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
   cudaStream_t st = lp->stream;
   const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
+  const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
+  const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y};
   // the replay must not stop on the phase's done flag or iteration limit
   Scalars S;
   CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));
@@ -1204,10 +1331,16 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   int rc = PDHGC_OK;
   for (int i = 0; i < iters && rc == PDHGC_OK; ++i) {
     CK(cudaEventRecord(ev[3 * i], st));
-    rc = launch_tiles(lp, true, true, PrimalOp{lp->S, 0, lp->it.y, md, lp->it}, nullptr, st);
+    if (fp32)
+      rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, 0, lp->it32.y, md32, it32}, nullptr, st);
+    else
+      rc = launch_tiles(lp, true, true, PrimalOp{lp->S, 0, lp->it.y, md, lp->it}, nullptr, st);
     if (rc != PDHGC_OK) break;
     CK(cudaEventRecord(ev[3 * i + 1], st));
-    rc = launch_tiles(lp, false, true, DualOp{lp->S, 0, lp->it.xbar, md, lp->it}, nullptr, st);
+    if (fp32)
+      rc = launch_tiles(lp, false, true, DualOp32{lp->S, 0, lp->it32.xbar, md32, it32}, nullptr, st);
+    else
+      rc = launch_tiles(lp, false, true, DualOp{lp->S, 0, lp->it.xbar, md, lp->it}, nullptr, st);
     if (rc != PDHGC_OK) break;
     CK(cudaEventRecord(ev[3 * i + 2], st));
   }

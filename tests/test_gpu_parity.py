@@ -190,3 +190,49 @@ def test_kkt_eval_of_a_point_matches_oracle(name):
     # the constructed optimum is optimal: every residual and the gap vanish
     rep = P.kkt_eval(lp, lp["x_star"], lp["y_star"])
     assert rep["rel_kkt"] <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# FP32 bulk (FP32 matrix and iterates, float-float row sums, FP64 KKT)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed", "transport_30x70"])
+def test_fp32_bulk_reaches_the_fp64_tolerance(name):
+    # no exact pin: the FP32 iteration is a different rounding of the same
+    # map; its result is judged by the FP64 KKT numbers and by the distance
+    # to the FP64 oracle's optimum
+    lp = _lp_cases()[name]()
+    g = P.lp_from_dict(lp)
+    rep = g.solve(precision=P.FP32_BULK)
+    assert rep["status_name"] == "OPTIMAL", rep
+    assert rep["precision"] == P.FP32_BULK
+    assert rep["rel_kkt"] <= 1e-6
+    full = oracle.solve(lp)
+    assert abs(rep["pobj"] - full["eval"]["pobj"]) <= 1e-5 * (1.0 + abs(full["eval"]["pobj"]))
+    x, _, _ = g.get_solution()
+    assert np.all(x >= lp["lb"] - 1e-12 * np.abs(lp["lb"])) and np.all(x <= lp["ub"] + 1e-12 * np.abs(lp["ub"]))
+
+
+def test_fp32_bulk_iterate_error_against_the_fp64_oracle():
+    # the stated error of the FP32-bulk iterates against the FP64 oracle:
+    # at k = 100 the max-norm relative error stays at the level of FP32
+    # rounding of the inputs (about 1e-7) amplified by the iteration
+    lp = lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000)
+    for k, bound in ((100, 1e-4), (1000, 1e-2)):
+        ref = oracle.run_iterations(lp, k)
+        s = ref["state"]
+        g = P.lp_from_dict(lp)
+        g.solve(max_iters=k, eps_rel=-1.0, precision=P.FP32_BULK)
+        it = g.get_iterates()
+        ex, ey = rel_err(it["x"], s.x), rel_err(it["y"], s.y)
+        print(f"FP32 bulk vs FP64 oracle at k={k}: x {ex:.3e}, y {ey:.3e}")
+        assert ex <= bound and ey <= bound
+
+
+def test_fp32_bulk_corner_phase():
+    lp = _lp_cases()["face_200x500_s0"]()
+    g = P.lp_from_dict(lp)
+    g.solve(precision=P.FP32_BULK)
+    rep = g.corner_phase(obj_seed=11)
+    assert rep["status_name"] == "CORNER_DONE"
+    assert rep["rel_p"] <= 1e-6 * (1 + 1e-9)
