@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "host_prep.h"
 
 namespace pdhgc {
@@ -136,6 +138,40 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Loads of the streamed matrix (values and indices, read once per pass) skip
+// L1 allocation so that L1 keeps the gathered vector entries; the L2 policy
+// is untouched (the matrix is reused from L2 by the next iteration).
+#ifndef PDHGC_STREAM_NO_L1
+#define PDHGC_STREAM_NO_L1 1
+#endif
+__device__ __forceinline__ double ld_stream(const double* p) {
+#if PDHGC_STREAM_NO_L1
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+#if PDHGC_STREAM_NO_L1
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ int ld_stream(const int* p) {
+#if PDHGC_STREAM_NO_L1
+  int v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+
 template <class T, int NG>
 struct GV {
   T v[NG];
@@ -164,7 +200,7 @@ using SpmvMat = SpmvMatT<double>;
 #define PDHGC_GATHER_BATCH 8
 #endif
 #ifndef PDHGC_MIN_BLOCKS
-#define PDHGC_MIN_BLOCKS 1
+#define PDHGC_MIN_BLOCKS 4
 #endif
 constexpr int kBatch = PDHGC_GATHER_BATCH;
 
@@ -184,8 +220,8 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
     GV<GT, NG> g[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      v[u] = val[k + u * step];
-      c[u] = col[k + u * step];
+      v[u] = ld_stream(val + k + u * step);
+      c[u] = ld_stream(col + k + u * step);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u)
@@ -196,18 +232,51 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
   }
   for (; k < k1; k += step) {
     GV<GT, NG> g;
-    const int c = col[k];
+    const int c = ld_stream(col + k);
 #pragma unroll
     for (int i = 0; i < NG; ++i) g.v[i] = __ldg(op.gsrc(i) + c);
-    op.accum(acc, rc, val[k], g);
+    op.accum(acc, rc, ld_stream(val + k), g);
   }
 }
+
+// Operators whose epilogue reads per-row inputs can declare `Pre`,
+// `prefetch(row)` and `epilogue_pre(row, acc, pre, part)`: the kernel then
+// loads those inputs right after the grid-dependency wait, so that their
+// latency overlaps the gathers instead of following them.
+template <class Op, class = void>
+struct Prefetcher {
+  struct Pre {};
+  __device__ static Pre get(const Op&, int) { return Pre{}; }
+  __device__ static void epilogue(const Op& op, int r, const typename Op::Acc& a, const Pre&, double* part) {
+    op.epilogue(r, a, part);
+  }
+};
+#ifndef PDHGC_PREFETCH
+#define PDHGC_PREFETCH 1
+#endif
+template <class Op>
+struct Prefetcher<Op, std::void_t<typename Op::Pre>> {
+#if PDHGC_PREFETCH
+  using Pre = typename Op::Pre;
+  __device__ static Pre get(const Op& op, int r) { return op.prefetch(r); }
+  __device__ static void epilogue(const Op& op, int r, const typename Op::Acc& a, const Pre& p, double* part) {
+    op.epilogue_pre(r, a, p, part);
+  }
+#else  // the same inputs, loaded when the epilogue runs
+  struct Pre {};
+  __device__ static Pre get(const Op&, int) { return Pre{}; }
+  __device__ static void epilogue(const Op& op, int r, const typename Op::Acc& a, const Pre&, double* part) {
+    op.epilogue_pre(r, a, op.prefetch(r), part);
+  }
+#endif
+};
 
 template <class Op, bool kPdl>
 __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
     spmv(SpmvMatT<typename Op::VT> M, Op op, double* __restrict__ partials) {
   using VT = typename Op::VT;
   using GT = typename Op::GT;
+  using PF = Prefetcher<Op>;
   constexpr int NG = Op::NG;
   constexpr int NQ = Op::NQ;
   constexpr int NQS = NQ > 0 ? NQ : 1;
@@ -231,6 +300,8 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
       if (op.skip()) return;
     }
     const double rc = op.row_ctx(r);
+    typename PF::Pre pre{};
+    if (tid == 0) pre = PF::get(op, r);
     typename Op::Acc acc;
     acc.zero();
     row_dot_global(op, acc, rc, M.val, M.col, e0 + tid, e1, kBlock);
@@ -243,7 +314,7 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
       typename Op::Acc tot = s_acc[0];
 #pragma unroll
       for (int w = 1; w < kWarpsPerBlock; ++w) tot.add(s_acc[w]);
-      op.epilogue(r, tot, part);
+      PF::epilogue(op, r, tot, pre, part);
     }
   } else if (blk < M.nb_cta + M.nb_warp) {
     const int r = M.cta_rows + (blk - M.nb_cta) * kWarpsPerBlock + warp;
@@ -259,13 +330,15 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
     }
     if (has) {
       const double rc = op.row_ctx(r);
+      typename PF::Pre pre{};
+      if (lane == 0) pre = PF::get(op, r);
       typename Op::Acc acc;
       acc.zero();
       row_dot_global(op, acc, rc, M.val, M.col, e0 + lane, e1, 32);
       if constexpr (kPdl) grid_dep_launch();
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
-      if (lane == 0) op.epilogue(r, acc, part);
+      if (lane == 0) PF::epilogue(op, r, acc, pre, part);
     } else {
       if constexpr (kPdl) grid_dep_launch();
     }
@@ -294,14 +367,16 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       if (jb + u < jend) {
-        v[u] = M.sval[base + (jb + u) * kSellH + lane];
-        c[u] = M.scol[base + (jb + u) * kSellH + lane];
+        v[u] = ld_stream(M.sval + base + (jb + u) * kSellH + lane);
+        c[u] = ld_stream(M.scol + base + (jb + u) * kSellH + lane);
       }
     }
     if constexpr (kPdl) {
       grid_dep_wait();
       if (op.skip()) return;
     }
+    typename PF::Pre pre{};
+    if (kw == 0 && r >= 0) pre = PF::get(op, r);
     typename Op::Acc acc;
     acc.zero();
     const double rc = r >= 0 ? op.row_ctx(r) : 0.0;
@@ -310,8 +385,8 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           if (j + u < jend) {
-            v[u] = M.sval[base + (j + u) * kSellH + lane];
-            c[u] = M.scol[base + (j + u) * kSellH + lane];
+            v[u] = ld_stream(M.sval + base + (j + u) * kSellH + lane);
+            c[u] = ld_stream(M.scol + base + (j + u) * kSellH + lane);
           }
         }
       }
@@ -334,7 +409,7 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
         for (int q = 1; q < K; ++q) acc.add(s_part[warp + q][lane]);
       }
     }
-    if (kw == 0 && r >= 0) op.epilogue(r, acc, part);
+    if (kw == 0 && r >= 0) PF::epilogue(op, r, acc, pre, part);
   }
 
   if constexpr (NQ > 0) {
@@ -381,13 +456,15 @@ struct PrimalOp {
   using GT = double;
   __device__ const double* gsrc(int) const { return y; }
   __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
-  __device__ void epilogue(int j, const Acc& a, double*) const {
-    const double tau = S->tau;
-    const double g = md.chat[j] - a.v[0];
-    const double xo = w.x[j];
-    const double xn = clamp_i(xo - tau * g, md.lhat[j], md.uhat[j]);
-    w.xbar[j] = 2.0 * xn - xo;
-    w.sum_x[j] += xn;
+  struct Pre {
+    double c, l, u, x, sx, tau;
+  };
+  __device__ Pre prefetch(int j) const { return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.sum_x[j], S->tau}; }
+  __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
+    const double g = p.c - a.v[0];
+    const double xn = clamp_i(p.x - p.tau * g, p.l, p.u);
+    w.xbar[j] = 2.0 * xn - p.x;
+    w.sum_x[j] = p.sx + xn;
     w.x[j] = xn;
   }
 };
@@ -409,11 +486,15 @@ struct DualOp {
   using GT = double;
   __device__ const double* gsrc(int) const { return xbar; }
   __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
-  __device__ void epilogue(int i, const Acc& a, double*) const {
-    const double sigma = S->sigma;
-    double yn = w.y[i] + sigma * (md.bhat[i] - a.v[0]);
-    if (md.ge[i] && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
-    w.sum_y[i] += yn;
+  struct Pre {
+    double b, y, sy, sigma;
+    bool ge;
+  };
+  __device__ Pre prefetch(int i) const { return Pre{md.bhat[i], w.y[i], w.sum_y[i], S->sigma, md.ge[i] != 0}; }
+  __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
+    double yn = p.y + p.sigma * (p.b - a.v[0]);
+    if (p.ge && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
+    w.sum_y[i] = p.sy + yn;
     w.y[i] = yn;
   }
 };
@@ -815,13 +896,18 @@ struct PrimalOp32 {
   __device__ double row_ctx(int) const { return 0.0; }
   __device__ const float* gsrc(int) const { return y; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
-  __device__ void epilogue(int j, const Acc& a, double*) const {
-    const float tau = (float)S->tau;
-    const float g = (float)((double)md.chat[j] - a.value());
-    const float xo = w.x[j];
-    const float xn = clamp_f(fmaf(-tau, g, xo), md.lhat[j], md.uhat[j]);
-    w.xbar[j] = 2.0f * xn - xo;
-    w.sum_x[j] += (double)xn;
+  struct Pre {
+    float c, l, u, x, tau;
+    double sx;
+  };
+  __device__ Pre prefetch(int j) const {
+    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], (float)S->tau, w.sum_x[j]};
+  }
+  __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
+    const float g = (float)((double)p.c - a.value());
+    const float xn = clamp_f(fmaf(-p.tau, g, p.x), p.l, p.u);
+    w.xbar[j] = 2.0f * xn - p.x;
+    w.sum_x[j] = p.sx + (double)xn;
     w.x[j] = xn;
   }
 };
@@ -843,12 +929,19 @@ struct DualOp32 {
   __device__ double row_ctx(int) const { return 0.0; }
   __device__ const float* gsrc(int) const { return xbar; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
-  __device__ void epilogue(int i, const Acc& a, double*) const {
-    const float sigma = (float)S->sigma;
-    const float r = (float)((double)md.bhat[i] - a.value());
-    float yn = fmaf(sigma, r, w.y[i]);
-    if (md.ge[i] && __float_as_int(yn) < 0) yn = 0.0f;  // y >= 0 on '>' rows (sign bit test)
-    w.sum_y[i] += (double)yn;
+  struct Pre {
+    float b, y, sigma;
+    bool ge;
+    double sy;
+  };
+  __device__ Pre prefetch(int i) const {
+    return Pre{md.bhat[i], w.y[i], (float)S->sigma, md.ge[i] != 0, w.sum_y[i]};
+  }
+  __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
+    const float r = (float)((double)p.b - a.value());
+    float yn = fmaf(p.sigma, r, p.y);
+    if (p.ge && __float_as_int(yn) < 0) yn = 0.0f;  // y >= 0 on '>' rows (sign bit test)
+    w.sum_y[i] = p.sy + (double)yn;
     w.y[i] = yn;
   }
 };
