@@ -273,6 +273,65 @@ int pdhgc_kkt_eval_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row
  */
 int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void* cuda_stream);
 
+/* ---- batched solve: many independent LPs in one persistent launch ------- */
+
+/*
+ * pdhgc_batch_create — `count` LPs, each as for pdhgc_lp_create, given by
+ * host arrays of per-LP pointers (row_ptr[k], col_idx[k], ... are the k-th
+ * LP's arrays; lb, ub and sense may be NULL as a whole or per LP).  Every LP
+ * is validated and laid out as in pdhgc_lp_create and packed into one set of
+ * device arrays.  nnz summed over the batch must be < 2^31.  The batch owns
+ * its device memory; all work goes on `cuda_stream`.
+ * Errors: as pdhgc_lp_create (the detail names the offending LP).
+ */
+typedef struct pdhgc_batch pdhgc_batch;
+int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const int32_t* n, const int64_t* nnz,
+                       const int64_t* const* row_ptr, const int32_t* const* col_idx, const double* const* val,
+                       const double* const* b, const double* const* c, const double* const* lb,
+                       const double* const* ub, const int8_t* const* sense, void* cuda_stream);
+
+/*
+ * pdhgc_batch_solve — phase 1 (as pdhgc_solve, same parameters) for every
+ * LP of the batch in one persistent kernel launch: each CTA takes LPs from
+ * a work queue, largest first, and runs the whole method on one LP (scaling,
+ * power iteration, the restarted PDHG loop with its per-LP step size, primal
+ * weight, restarts and termination, then the report); an LP's x_bar and y
+ * live in the CTA's shared memory.  `reports` (count entries, may be NULL)
+ * receives one report per LP in the caller's order; `seconds` is that LP's
+ * device time.  Both precisions are supported.
+ */
+int pdhgc_batch_solve(pdhgc_batch* batch, const pdhgc_params* params, pdhgc_report* reports);
+
+/* pdhgc_batch_corner_phase — Algorithm 1 for every LP (as pdhgc_corner_phase). */
+int pdhgc_batch_corner_phase(pdhgc_batch* batch, const pdhgc_corner_params* params, pdhgc_report* reports);
+
+/* pdhgc_batch_get_solution — x (n) and y (m) of LP `lp`, user order, host pointers (either may be NULL). */
+int pdhgc_batch_get_solution(pdhgc_batch* batch, int32_t lp, int which, double* x, double* y);
+
+/*
+ * Schedule knobs of the batched kernel, set by the autotuner: threads per
+ * CTA (512 or 1024) and lanes per row of the A and A' passes (1..32, a power
+ * of two; 0 = chosen per LP from its mean row length).
+ */
+int pdhgc_batch_set_block(pdhgc_batch* batch, int32_t threads);
+int pdhgc_batch_set_lanes(pdhgc_batch* batch, int32_t lanes_a, int32_t lanes_t);
+/* layout of the matrix passes: 1 = SELL-32 slices (lane per row), 0 = CSR rows with the lanes above */
+int pdhgc_batch_set_layout(pdhgc_batch* batch, int32_t sell);
+
+/*
+ * pdhgc_batch_tune — the schedule autotuner.  For each candidate schedule
+ * (threads per CTA x layout x lanes per row; 7 candidates) it times
+ * `tune_iters` iterations of the whole batch (setup included, no early
+ * termination, so every candidate does the same work) with CUDA events on
+ * the batch's stream, and keeps the fastest.  chosen (4 ints, may be NULL)
+ * receives {threads, sell, lanes_a, lanes_t}; timings_ms (7 doubles, may be
+ * NULL) the candidates' times.  Discards any phase-1 / corner result.
+ */
+int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tune_iters, int32_t* chosen,
+                     double* timings_ms);
+
+void pdhgc_batch_destroy(pdhgc_batch* batch);
+
 /*
  * pdhgc_kernel_launches — number of CUDA kernels this handle has launched
  * so far (kernels inside the solve graph counted once per execution).

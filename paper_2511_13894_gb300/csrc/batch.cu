@@ -1,0 +1,1161 @@
+// Batched solve: many independent LPs in one persistent launch.
+//
+// A CTA takes LPs from a work queue (largest first) and runs the whole method
+// on each one: Ruiz + Pock-Chambolle scaling, power iteration, restarted PDHG
+// with its checks, restarts and termination, the report, and on request the
+// corner phase of Algorithm 1.  Between the two matrix passes of an iteration
+// only a CTA barrier is needed, and an LP's gathered vectors (x_bar and y)
+// live in the CTA's shared memory, so the random gathers of the SpMV are
+// shared-memory loads.  A finished LP drops out: its CTA pulls the next one.
+// The arithmetic of every step is the same operator code as the single-LP
+// path (kernels.cuh); only the scheduling differs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhgc.h"
+#include "batch.h"
+#include "host_prep.h"
+#include "kernels.cuh"
+#include "kkt_eval.h"
+
+namespace pdhgc {
+
+// ---------------------------------------------------------------------------
+// Per-LP device view (all pointers are device addresses of this LP's slices
+// of the batch's packed arrays; internal row / column order)
+// ---------------------------------------------------------------------------
+struct LpDesc {
+  int m, n, nnz;
+  int gA, gT;         // lanes per row of the A and A' passes in the CSR layout (autotuned)
+  int sell;           // 1: passes read the SELL-32 copies; 0: CSR rows with gA / gT lanes
+  int smem;           // 1: x_bar and y live in shared memory
+  double b_norm, c_norm;
+  const int *A_rp, *A_col, *T_rp, *T_col;
+  const double *A_val, *T_val;
+  double *A_hat, *T_hat;
+  float *A_hat32, *T_hat32;
+  // SELL-32 copies of the rows with <= kSellMaxLen nonzeros (rows [long, rows))
+  int A_long, A_ns, A_slots, T_long, T_ns, T_slots;
+  const int *A_sptr, *A_sw, *A_scol, *A_smap, *T_sptr, *T_sw, *T_scol, *T_smap;
+  const double *A_sval, *T_sval;
+  double *A_shat, *T_shat;
+  float *A_shat32, *T_shat32;
+  const double *b_int, *c, *l, *u;
+  const int8_t* ge;
+  int8_t* ge_c;
+  double *Dr, *Dc, *rfac, *cfac, *bhat, *chat, *lhat, *uhat;
+  double *chat_c, *lhat_c, *uhat_c;
+  float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32;
+  double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r;  // FP64 iterates (x_bar, y: global fallback)
+  float *x32, *xbar32, *y32;                          // FP32 iterates (global fallback)
+  double *x1, *y1, *xc;
+  double *pi_v, *pi_w, *pi_u;
+  double* keep;  // eta, sigma_max, ||b_hat||, ||c_hat|| from phase 1 (read by the corner phase)
+  const int *row_perm, *col_perm;
+};
+
+namespace {
+
+// ---- CTA-level building blocks --------------------------------------------
+
+// one pass over the rows of a CSR: G lanes per row, rows round-robin over the
+// CTA's groups; gathers by plain loads (shared or global memory)
+template <int BT, class Op>
+__device__ void cta_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                         const typename Op::VT* __restrict__ val, int rows, int G, const Op& op, double* part) {
+  using PF = Prefetcher<Op>;
+  using GT = typename Op::GT;
+  constexpr int NG = Op::NG;
+  const int tid = threadIdx.x;
+  const int lane = tid & (G - 1);
+  const int gid = tid / G;
+  const int ngroups = BT / G;
+  for (int r0 = 0; r0 < rows; r0 += ngroups) {
+    const int r = r0 + gid;
+    const bool has = r < rows;
+    typename Op::Acc acc;
+    acc.zero();
+    typename PF::Pre pre{};
+    if (has) {
+      if (lane == 0) pre = PF::get(op, r);
+      const double rc = op.row_ctx(r);
+      const int e0 = rp[r], e1 = rp[r + 1];
+      for (int e = e0 + lane; e < e1; e += G) {
+        const int cc = col[e];
+        GV<GT, NG> g;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) g.v[i] = op.gsrc(i)[cc];
+        op.accum(acc, rc, val[e], g);
+      }
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
+    if (has && lane == 0) PF::epilogue(op, r, acc, pre, part);
+  }
+}
+
+// one matrix of an LP as a pass reads it: CSR for the long rows, SELL-32
+// slices for the rest
+template <class VT>
+struct BMat {
+  const int* rp;
+  const int* col;
+  const VT* val;
+  int rows, long_rows, nslices;
+  const int* sptr;
+  const int* sw;
+  const int* scol;
+  const VT* sval;
+};
+
+// one pass: long rows with a warp each (CSR), then SELL-32 slices with a lane
+// per row and kBatch coalesced loads in flight, slices round-robin over warps
+template <int BT, class Op>
+__device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* part) {
+  using PF = Prefetcher<Op>;
+  using VT = typename Op::VT;
+  using GT = typename Op::GT;
+  constexpr int NG = Op::NG;
+  constexpr int W = BT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (M.long_rows > 0) cta_rows<BT>(M.rp, M.col, M.val, M.long_rows, 32, op, part);
+  for (int s = warp; s < M.nslices; s += W) {
+    const int base = M.sptr[s], w = M.sw[s];
+    const int r = M.long_rows + s * kSellH + lane;
+    const bool has = r < M.rows;
+    const int len = has ? M.rp[r + 1] - M.rp[r] : 0;
+    typename PF::Pre pre{};
+    if (has) pre = PF::get(op, r);
+    const double rc = has ? op.row_ctx(r) : 0.0;
+    typename Op::Acc acc;
+    acc.zero();
+    for (int j = 0; j < w; j += kBatch) {
+      VT v[kBatch];
+      int c[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < len) {
+          v[u] = ld_stream(M.sval + base + (j + u) * kSellH + lane);
+          c[u] = ld_stream(M.scol + base + (j + u) * kSellH + lane);
+        }
+      GV<GT, NG> g[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < len)
+#pragma unroll
+          for (int i = 0; i < NG; ++i) g[u].v[i] = op.gsrc(i)[c[u]];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < len) op.accum(acc, rc, v[u], g[u]);
+    }
+    if (has) PF::epilogue(op, r, acc, pre, part);
+  }
+}
+
+// deterministic CTA fold of part[0..nq) (sum, or max where mask bit set) into out[]
+template <int BT>
+__device__ void cta_fold(const double* part, int nq, unsigned max_mask, double* out, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int W = BT / 32;
+  for (int q = 0; q < nq; ++q) {
+    const bool is_max = (max_mask >> q) & 1u;
+    double v = part[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = is_max ? fmax(v, o) : v + o;
+    }
+    if (lane == 0) red[q * W + warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    const int q = threadIdx.x;
+    const bool is_max = (max_mask >> q) & 1u;
+    double v = red[q * W];
+    for (int w = 1; w < W; ++w) v = is_max ? fmax(v, red[q * W + w]) : v + red[q * W + w];
+    out[q] = v;
+  }
+  __syncthreads();
+}
+
+template <int BT>
+__device__ double cta_sum(double v, double* red) {
+  double part[1] = {v};
+  double out[1];
+  __shared__ double s_out[1];
+  cta_fold<BT>(part, 1, 0u, s_out, red);
+  out[0] = s_out[0];
+  __syncthreads();
+  return out[0];
+}
+
+struct BatchParams {
+  double eps_rel, beta_suff, beta_nec, beta_art, theta, eta_factor, time_limit_s;
+  long long max_iters;
+  int check_period, ruiz_iters, power_iters;
+  // corner
+  double eps_abs, c_eps_rel, obj_scale, c_time_limit_s;
+  long long c_min_iters, c_max_iters;
+  unsigned long long obj_seed;
+  int stop_rule;
+};
+
+// ---- one LP, one CTA ------------------------------------------------------
+
+template <class VT, int BT>
+struct LpSolver {
+  static constexpr bool kF32 = std::is_same<VT, float>::value;
+  const LpDesc& d;
+  const BatchParams& bp;
+  Scalars* S;
+  double* red;  // [32 * BT / 32] reduction scratch
+  double* q;    // [32] folded quantities
+  VT* s_y;      // gathered y (shared or global)
+  VT* s_xbar;   // gathered x_bar (shared or global)
+
+  __device__ void fill(double* a, int n, double v) const {
+    for (int i = threadIdx.x; i < n; i += BT) a[i] = v;
+  }
+  // one pass over A (or A') in the layout the tuner chose
+  template <class Op>
+  __device__ void passA(const BMat<typename Op::VT>& M, const Op& op, double* part) const {
+    if (d.sell) cta_pass<BT>(M, op, part);
+    else cta_rows<BT>(M.rp, M.col, M.val, M.rows, d.gA, op, part);
+  }
+  template <class Op>
+  __device__ void passT(const BMat<typename Op::VT>& M, const Op& op, double* part) const {
+    if (d.sell) cta_pass<BT>(M, op, part);
+    else cta_rows<BT>(M.rp, M.col, M.val, M.rows, d.gT, op, part);
+  }
+  // kind 0: original values, 1: scaled FP64
+  __device__ BMat<double> matA(int kind) const {
+    return BMat<double>{d.A_rp, d.A_col, kind ? d.A_hat : d.A_val, d.m, d.A_long, d.A_ns,
+                        d.A_sptr, d.A_sw, d.A_scol, kind ? d.A_shat : d.A_sval};
+  }
+  __device__ BMat<double> matT(int kind) const {
+    return BMat<double>{d.T_rp, d.T_col, kind ? d.T_hat : d.T_val, d.n, d.T_long, d.T_ns,
+                        d.T_sptr, d.T_sw, d.T_scol, kind ? d.T_shat : d.T_sval};
+  }
+  __device__ BMat<float> matA32() const {
+    return BMat<float>{d.A_rp, d.A_col, d.A_hat32, d.m, d.A_long, d.A_ns, d.A_sptr, d.A_sw, d.A_scol, d.A_shat32};
+  }
+  __device__ BMat<float> matT32() const {
+    return BMat<float>{d.T_rp, d.T_col, d.T_hat32, d.n, d.T_long, d.T_ns, d.T_sptr, d.T_sw, d.T_scol, d.T_shat32};
+  }
+
+  __device__ DevModel model(bool corner) const {
+    return corner ? DevModel{d.chat_c, d.lhat_c, d.uhat_c, d.bhat, d.Dr, d.Dc, d.ge_c}
+                  : DevModel{d.chat, d.lhat, d.uhat, d.bhat, d.Dr, d.Dc, d.ge};
+  }
+  __device__ DevModel32 model32(bool corner) const {
+    return corner ? DevModel32{d.chat_c32, d.lhat_c32, d.uhat_c32, d.bhat32, d.ge_c}
+                  : DevModel32{d.chat32, d.lhat32, d.uhat32, d.bhat32, d.ge};
+  }
+  // FP64 view of the current iterates for the evaluation operators
+  __device__ DevIter iter64() const {
+    double* y = kF32 ? d.y : (double*)s_y;
+    double* xbar = kF32 ? d.xbar : (double*)s_xbar;
+    return DevIter{d.x, y, xbar, d.sum_x, d.sum_y, d.x_r, d.y_r};
+  }
+
+  // a0: Ruiz + Pock-Chambolle, scaled copies, power iteration
+  __device__ void setup() {
+    const int m = d.m, n = d.n;
+    fill(d.Dr, m, 1.0);
+    fill(d.Dc, n, 1.0);
+    __syncthreads();
+    double part[1] = {0.0};
+    for (int pass = 0; pass < bp.ruiz_iters; ++pass) {
+      passA(matA(0), ScaleMaxOp<false>{d.Dr, d.Dc, d.rfac}, part);
+      passT(matT(0), ScaleMaxOp<true>{d.Dc, d.Dr, d.cfac}, part);
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += BT) d.Dr[i] *= d.rfac[i];
+      for (int j = threadIdx.x; j < n; j += BT) d.Dc[j] *= d.cfac[j];
+      __syncthreads();
+    }
+    passA(matA(0), ScaleSumOp<false>{d.Dr, d.Dc, d.rfac}, part);
+    passT(matT(0), ScaleSumOp<true>{d.Dc, d.Dr, d.cfac}, part);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += BT) d.Dr[i] *= d.rfac[i];
+    for (int j = threadIdx.x; j < n; j += BT) d.Dc[j] *= d.cfac[j];
+    __syncthreads();
+    // scaled matrix and vectors: (D_r a) D_c, D_r b, D_c c, l / D_c, u / D_c
+    for (int r = threadIdx.x; r < m; r += BT)
+      for (int e = d.A_rp[r]; e < d.A_rp[r + 1]; ++e) {
+        const double v = (d.Dr[r] * d.A_val[e]) * d.Dc[d.A_col[e]];
+        d.A_hat[e] = v;
+        if (kF32) d.A_hat32[e] = (float)v;
+      }
+    for (int j = threadIdx.x; j < n; j += BT)
+      for (int e = d.T_rp[j]; e < d.T_rp[j + 1]; ++e) {
+        const double v = (d.Dr[d.T_col[e]] * d.T_val[e]) * d.Dc[j];
+        d.T_hat[e] = v;
+        if (kF32) d.T_hat32[e] = (float)v;
+      }
+    __syncthreads();
+    for (int k = threadIdx.x; k < d.A_slots; k += BT) {
+      const int e = d.A_smap[k];
+      const double v = e >= 0 ? d.A_hat[e] : 0.0;
+      d.A_shat[k] = v;
+      if (kF32) d.A_shat32[k] = (float)v;
+    }
+    for (int k = threadIdx.x; k < d.T_slots; k += BT) {
+      const int e = d.T_smap[k];
+      const double v = e >= 0 ? d.T_hat[e] : 0.0;
+      d.T_shat[k] = v;
+      if (kF32) d.T_shat32[k] = (float)v;
+    }
+    double nb2 = 0.0, nc2 = 0.0;
+    for (int i = threadIdx.x; i < m; i += BT) {
+      const double bh = d.Dr[i] * d.b_int[i];
+      d.bhat[i] = bh;
+      nb2 += bh * bh;
+      if (kF32) d.bhat32[i] = (float)bh;
+    }
+    for (int j = threadIdx.x; j < n; j += BT) {
+      const double ch = d.Dc[j] * d.c[j];
+      d.chat[j] = ch;
+      d.lhat[j] = d.l[j] / d.Dc[j];
+      d.uhat[j] = d.u[j] / d.Dc[j];
+      nc2 += ch * ch;
+      if (kF32) {
+        d.chat32[j] = (float)ch;
+        d.lhat32[j] = (float)d.lhat[j];
+        d.uhat32[j] = (float)d.uhat[j];
+      }
+    }
+    nb2 = cta_sum<BT>(nb2, red);
+    nc2 = cta_sum<BT>(nc2, red);
+    // power iteration on A_hat' A_hat from v = 1/sqrt(n)
+    fill(d.pi_v, n, 1.0 / sqrt((double)n));
+    __syncthreads();
+    bool zero = false;
+    for (int k = 0; k < bp.power_iters && !zero; ++k) {
+      passA(matA(1), SpmvOp<false>{S, d.pi_v, d.pi_u}, part);
+      __syncthreads();
+      double pw[1] = {0.0};
+      passT(matT(1), SpmvOp<true>{S, d.pi_u, d.pi_w}, pw);
+      const double nw = sqrt(cta_sum<BT>(pw[0], red));
+      if (nw == 0.0) {
+        zero = true;
+        break;
+      }
+      for (int j = threadIdx.x; j < n; j += BT) d.pi_v[j] = d.pi_w[j] / nw;
+      __syncthreads();
+    }
+    double sigma_max = 0.0;
+    if (!zero) {
+      double pu[1] = {0.0};
+      passA(matA(1), SpmvOp<true>{S, d.pi_v, d.pi_u}, pu);
+      sigma_max = sqrt(cta_sum<BT>(pu[0], red));
+    }
+    if (threadIdx.x == 0) {
+      S->sigma_max = sigma_max;
+      S->eta = sigma_max > 0.0 ? bp.eta_factor / sigma_max : 1.0;
+      S->nb_hat = sqrt(nb2);
+      S->nc_hat = sqrt(nc2);
+      d.keep[0] = S->eta;
+      d.keep[1] = S->sigma_max;
+      d.keep[2] = S->nb_hat;
+      d.keep[3] = S->nc_hat;
+    }
+    __syncthreads();
+  }
+
+  // start of a phase (mirrors k_init_scalars / k_init_iterates)
+  __device__ void init_phase(int phase, const double* x_start, double nch, double nc_user) {
+    const int m = d.m, n = d.n;
+    const DevModel md = model(phase == 1);
+    for (int j = threadIdx.x; j < n; j += BT) {
+      const double x0 = x_start ? x_start[j] : fmin(fmax(0.0, md.lhat[j]), md.uhat[j]);
+      d.x[j] = x0;
+      d.x_r[j] = x0;
+      d.sum_x[j] = 0.0;
+      if (kF32) {
+        d.x32[j] = (float)x0;
+        s_xbar[j] = (VT)x0;
+      } else {
+        ((double*)s_xbar)[j] = x0;
+      }
+    }
+    for (int i = threadIdx.x; i < m; i += BT) {
+      s_y[i] = (VT)0;
+      if (kF32) d.y[i] = 0.0;
+      d.y_r[i] = 0.0;
+      d.sum_y[i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+      S->eps_rel = phase ? bp.c_eps_rel : bp.eps_rel;
+      S->beta_suff = bp.beta_suff;
+      S->beta_nec = bp.beta_nec;
+      S->beta_art = bp.beta_art;
+      S->theta = bp.theta;
+      S->time_limit_s = phase ? bp.c_time_limit_s : bp.time_limit_s;
+      S->nb = d.b_norm;
+      S->nc = nc_user;
+      S->max_iters = phase ? bp.c_max_iters : bp.max_iters;
+      S->min_iters = phase ? bp.c_min_iters : 0;
+      S->check_period = bp.check_period;
+      S->phase = phase;
+      S->stop_rule = phase ? bp.stop_rule : 0;
+      S->omega = (nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0;
+      S->tau = S->eta / S->omega;
+      S->sigma = S->eta * S->omega;
+      S->k = 0;
+      S->t = 0;
+      S->restarts = 0;
+      S->chunks = 0;
+      S->max_chunks = S->max_iters / S->check_period + 2;
+      S->done = 0;
+      S->status = PDHGC_STATUS_NONE;
+      S->chosen = 0;
+      S->restart_to = 0;
+      S->inv_t = 0.0;
+      S->at_check = 0;
+      S->at_limit = 0;
+      S->kkt_prev = INFINITY;
+      S->t0_ns = global_ns();
+    }
+    __syncthreads();
+  }
+
+  // the 22 KKT quantities of the current and average points, folded
+  __device__ void evaluate(bool corner) {
+    const DevModel md = model(corner);
+    const DevIter w = iter64();
+    double pr[10];
+    for (int i = 0; i < 10; ++i) pr[i] = 0.0;
+    passA(matA(1), EvalRowsOp{S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, pr);
+    cta_fold<BT>(pr, 10, EvalRowsOp::kMaxMask, q, red);
+    double pc[12];
+    for (int i = 0; i < 12; ++i) pc[i] = 0.0;
+    passT(matT(1), EvalColsOp{S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, pc);
+    cta_fold<BT>(pc, 12, EvalColsOp::kMaxMask, q + 10, red);
+  }
+
+  __device__ void iterate(bool corner, int it) {
+    double part[1] = {0.0};
+    if constexpr (kF32) {
+      const DevModel32 md = model32(corner);
+      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sum_x, d.sum_y};
+      passT(matT32(), PrimalOp32{S, it, (float*)s_y, md, w}, part);
+      __syncthreads();
+      passA(matA32(), DualOp32{S, it, (float*)s_xbar, md, w}, part);
+      __syncthreads();
+    } else {
+      const DevModel md = model(corner);
+      const DevIter w{d.x, (double*)s_y, (double*)s_xbar, d.sum_x, d.sum_y, d.x_r, d.y_r};
+      passT(matT(1), PrimalOp{S, it, (double*)s_y, md, w}, part);
+      __syncthreads();
+      passA(matA(1), DualOp{S, it, (double*)s_xbar, md, w}, part);
+      __syncthreads();
+    }
+  }
+
+  // the restarted loop of one phase (mirrors the graph body of run_phase)
+  __device__ void loop(bool corner) {
+    const int m = d.m, n = d.n;
+    const DevModel md = model(corner);
+    if (kF32) {
+      for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i];
+    }
+    __syncthreads();
+    evaluate(corner);
+    if (threadIdx.x == 0) decide_step(S, q, 0);
+    __syncthreads();
+    while (true) {
+      const long long k0 = S->k, kmax = S->max_iters;
+      const int P = S->check_period;
+      for (int i = 0; i < P && k0 + i < kmax; ++i) iterate(corner, i);
+      if (threadIdx.x == 0) {
+        long long run = kmax - k0;
+        if (run > P) run = P;
+        if (run < 0) run = 0;
+        S->k += run;
+        S->t += run;
+        S->inv_t = S->t > 0 ? 1.0 / (double)S->t : 0.0;
+        S->at_check = (S->k % P) == 0;
+        S->at_limit = S->k >= kmax;
+        S->chunks += 1;
+        if (S->chunks > S->max_chunks) S->at_limit = 1;
+      }
+      if (kF32) {
+        for (int j = threadIdx.x; j < n; j += BT) d.x[j] = fmin(fmax((double)d.x32[j], md.lhat[j]), md.uhat[j]);
+        for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i];
+      }
+      __syncthreads();
+      evaluate(corner);
+      if (threadIdx.x == 0) decide_step(S, q, 1);
+      __syncthreads();
+      if (S->done) break;
+      const int rt = S->restart_to;
+      if (rt != 0) {
+        const double inv_t = S->inv_t;
+        const DevIter w = iter64();
+        for (int j = threadIdx.x; j < n; j += BT) {
+          const double xn = rt == 2 ? w.sum_x[j] * inv_t : w.x[j];
+          w.x[j] = xn;
+          w.x_r[j] = xn;
+          w.sum_x[j] = 0.0;
+          if (kF32 && rt == 2) d.x32[j] = (float)xn;
+        }
+        for (int i = threadIdx.x; i < m; i += BT) {
+          const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
+          w.y[i] = yn;
+          w.y_r[i] = yn;
+          w.sum_y[i] = 0.0;
+          if (kF32 && rt == 2) ((float*)s_y)[i] = (float)yn;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // the returned point (mirrors k_finalize)
+  __device__ void finalize(double* xo, double* yo, const double* x_fallback, bool corner) {
+    const DevModel md = model(corner);
+    const DevIter w = iter64();
+    const bool avg = S->chosen == 1 && S->t > 0;
+    const double inv_t = S->inv_t;
+    const bool fallback = x_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
+    for (int j = threadIdx.x; j < d.n; j += BT)
+      xo[j] = fallback ? x_fallback[j] : fmin(fmax(avg ? w.sum_x[j] * inv_t : w.x[j], md.lhat[j]), md.uhat[j]);
+    if (yo)
+      for (int i = threadIdx.x; i < d.m; i += BT) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
+    __syncthreads();
+  }
+
+  // KKT numbers and metrics of (x, y) on the original model (mirrors run_report)
+  __device__ void report(const double* x, const double* y, BatchReport* out) {
+    const DevModel md = model(false);
+    double pr[7];
+    for (int i = 0; i < 7; ++i) pr[i] = 0.0;
+    passA(matA(1), ReportRowsOp{x, y, md, 1e-6}, pr);
+    cta_fold<BT>(pr, 7, ReportRowsOp::kMaxMask, q, red);
+    double pc[8];
+    for (int i = 0; i < 8; ++i) pc[i] = 0.0;
+    passT(matT(1), ReportColsOp{y, x, d.l, d.u, md, 1e-6}, pc);
+    cta_fold<BT>(pc, 8, ReportColsOp::kMaxMask, q + 7, red);
+    if (threadIdx.x == 0) {
+      BatchReport r;
+      r.status = S->status;
+      r.chosen = S->chosen;
+      r.iters = S->k;
+      r.restarts = S->restarts;
+      r.rP2 = sqrt(q[1]);
+      r.rPinf = q[2];
+      r.rD2 = sqrt(q[8]);
+      r.rDinf = q[9];
+      r.pobj = q[10];
+      r.dobj = q[3] + q[11];
+      r.p = q[4] + q[12];
+      r.dd = q[5] + q[13];
+      r.cand = q[6] + q[14];
+      r.omega = S->omega;
+      r.eta = S->eta;
+      r.sigma_max = S->sigma_max;
+      r.seconds = (double)(global_ns() - S->t0_ns) * 1e-9;
+      *out = r;
+    }
+    __syncthreads();
+  }
+
+  __device__ void phase1(BatchReport* out) {
+    setup();
+    init_phase(0, nullptr, S->nc_hat, d.c_norm);
+    loop(false);
+    finalize(d.x1, d.y1, nullptr, false);
+    report(d.x1, d.y1, out);
+  }
+
+  // Algorithm 1 (mirrors pdhgc_corner_phase)
+  __device__ void corner(BatchReport* out) {
+    if (threadIdx.x == 0) {
+      S->eta = d.keep[0];
+      S->sigma_max = d.keep[1];
+      S->nb_hat = d.keep[2];
+      S->nc_hat = d.keep[3];
+    }
+    __syncthreads();
+    double pc[2] = {0.0, 0.0};
+    passT(matT(1),
+                 CornerColsOp{d.y1, d.x1, d.col_perm, model(false), d.lhat_c, d.uhat_c, d.chat_c, bp.eps_abs,
+                              bp.obj_scale, bp.obj_seed},
+                 pc);
+    cta_fold<BT>(pc, 2, 0u, q, red);
+    const double cc2 = q[0], cu2 = q[1];
+    for (int i = threadIdx.x; i < d.m; i += BT)
+      d.ge_c[i] = (d.ge[i] && !(fabs(d.Dr[i] * d.y1[i]) > bp.eps_abs)) ? 1 : 0;
+    if (kF32)
+      for (int j = threadIdx.x; j < d.n; j += BT) {
+        d.chat_c32[j] = (float)d.chat_c[j];
+        d.lhat_c32[j] = (float)d.lhat_c[j];
+        d.uhat_c32[j] = (float)d.uhat_c[j];
+      }
+    __syncthreads();
+    init_phase(1, d.x1, sqrt(cc2), sqrt(cu2));
+    loop(true);
+    finalize(d.xc, nullptr, d.x1, true);
+    report(d.xc, d.y1, out);
+  }
+};
+
+template <class VT, int BT>
+__global__ void __launch_bounds__(BT) k_batch(const LpDesc* __restrict__ descs, const int* __restrict__ order,
+                                              int count, int* queue, BatchParams bp, int phase,
+                                              BatchReport* reps) {
+  extern __shared__ __align__(16) unsigned char s_vec[];
+  __shared__ Scalars S;
+  __shared__ double red[32 * (BT / 32)];
+  __shared__ double q[32];
+  __shared__ int job;
+  while (true) {
+    if (threadIdx.x == 0) job = atomicAdd(queue, 1);
+    __syncthreads();
+    const int jj = job;
+    __syncthreads();
+    if (jj >= count) break;
+    const int lp = order[jj];
+    const LpDesc& d = descs[lp];
+    VT* sy = d.smem ? reinterpret_cast<VT*>(s_vec) : (std::is_same<VT, float>::value ? (VT*)d.y32 : (VT*)d.y);
+    VT* sxb = d.smem ? reinterpret_cast<VT*>(s_vec) + d.m
+                     : (std::is_same<VT, float>::value ? (VT*)d.xbar32 : (VT*)d.xbar);
+    LpSolver<VT, BT> sol{d, bp, &S, red, q, sy, sxb};
+    if (phase == 0)
+      sol.phase1(&reps[lp]);
+    else
+      sol.corner(&reps[lp]);
+  }
+}
+
+template <class T>
+int dalloc(std::vector<void*>& allocs, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (count > 0 ? count : 1) * sizeof(T));
+  if (e != cudaSuccess) return PDHGC_ERR_OOM;
+  allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return PDHGC_OK;
+}
+
+}  // namespace
+
+}  // namespace pdhgc
+
+using namespace pdhgc;
+
+struct pdhgc_batch {
+  int count = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<void*> allocs;
+  std::vector<LpDesc> h_desc;
+  std::vector<int> order;
+  std::vector<std::vector<int32_t>> row_perm, col_perm;
+  std::vector<std::vector<double>> sign;
+  LpDesc* d_desc = nullptr;
+  int* d_order = nullptr;
+  int* d_queue = nullptr;
+  BatchReport* d_rep = nullptr;
+  std::vector<BatchReport> h_rep1, h_repc;
+  size_t smem_f32 = 0, smem_f64 = 0;
+  int block = 1024;
+  int have_phase1 = 0, have_corner = 0;
+  int precision = PDHGC_FP32_BULK;
+  pdhgc_params params{};
+  double tune_ms[4] = {0, 0, 0, 0};
+  ~pdhgc_batch() {
+    for (void* q : allocs) cudaFree(q);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+namespace {
+
+int set_berr(int code, const std::string& s) { return pdhgc::set_error_detail(code, s); }
+
+#define RET(x)                     \
+  do {                             \
+    const int r_ = (x);            \
+    if (r_ != PDHGC_OK) return r_; \
+  } while (0)
+
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_berr(e_ == cudaErrorMemoryAllocation ? PDHGC_ERR_OOM : PDHGC_ERR_CUDA,   \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+// lanes per row from the mean row length (a starting point the tuner refines)
+int lanes_for(double mean_len) {
+  int g = 1;
+  while (g < 32 && g * 4 < mean_len) g <<= 1;
+  return g;
+}
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+BatchParams make_params(const pdhgc_params& p, const pdhgc_corner_params* cp) {
+  BatchParams b{};
+  b.eps_rel = p.eps_rel;
+  b.beta_suff = p.beta_suff;
+  b.beta_nec = p.beta_nec;
+  b.beta_art = p.beta_art;
+  b.theta = p.theta;
+  b.eta_factor = p.eta_factor;
+  b.time_limit_s = p.time_limit_s;
+  b.max_iters = p.max_iters;
+  b.check_period = p.check_period;
+  b.ruiz_iters = p.ruiz_iters;
+  b.power_iters = p.power_iters;
+  if (cp) {
+    b.eps_abs = cp->eps_abs;
+    b.c_eps_rel = cp->eps_rel;
+    b.obj_scale = cp->obj_scale;
+    b.c_time_limit_s = cp->time_limit_s;
+    b.c_min_iters = cp->min_iters;
+    b.c_max_iters = cp->max_iters;
+    b.obj_seed = cp->obj_seed;
+    b.stop_rule = cp->stop_rule;
+  }
+  return b;
+}
+
+template <class VT, int BT>
+int launch_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t st) {
+  const size_t smem = std::is_same<VT, float>::value ? B->smem_f32 : B->smem_f64;
+  BCK(cudaFuncSetAttribute(k_batch<VT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<VT, BT>, BT, smem));
+  if (per_sm < 1) return set_berr(PDHGC_ERR_CUDA, "batched kernel does not fit on an SM");
+  int grid = sms * per_sm;
+  if (grid > B->count) grid = B->count;
+  BCK(cudaMemsetAsync(B->d_queue, 0, sizeof(int), st));
+  k_batch<VT, BT><<<grid, BT, smem, st>>>(B->d_desc, B->d_order, B->count, B->d_queue, bp, phase, B->d_rep);
+  BCK(cudaGetLastError());
+  return PDHGC_OK;
+}
+
+int run_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t st) {
+  const bool f32 = B->precision == PDHGC_FP32_BULK;
+  if (B->block == 512) return f32 ? launch_batch<float, 512>(B, bp, phase, st) : launch_batch<double, 512>(B, bp, phase, st);
+  return f32 ? launch_batch<float, 1024>(B, bp, phase, st) : launch_batch<double, 1024>(B, bp, phase, st);
+}
+
+void to_report(const BatchReport& r, int64_t m, double nb, double nc, int precision, pdhgc_report* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->status = r.status;
+  out->chosen = r.chosen;
+  out->iters = r.iters;
+  out->restarts = r.restarts;
+  out->rP2 = r.rP2;
+  out->rD2 = r.rD2;
+  out->rPinf = r.rPinf;
+  out->rDinf = r.rDinf;
+  out->pobj = r.pobj;
+  out->dobj = r.dobj;
+  out->gap = r.pobj - r.dobj;
+  out->rel_p = r.rP2 / (1.0 + nb);
+  out->rel_d = r.rD2 / (1.0 + nc);
+  out->rel_gap = std::fabs(out->gap) / (1.0 + std::fabs(r.pobj) + std::fabs(r.dobj));
+  out->rel_kkt = std::fmax(out->rel_p, std::fmax(out->rel_d, out->rel_gap));
+  out->off_bound_p = (int64_t)std::llround(r.p);
+  out->zero_rc_d = (int64_t)std::llround(r.dd);
+  out->candidates = (int64_t)std::llround(r.cand);
+  out->corner_measure = out->candidates > m ? out->candidates - m : 0;
+  out->primal_push_est = out->off_bound_p > m ? out->off_bound_p - m : 0;
+  out->dual_push_est = m > out->zero_rc_d ? m - out->zero_rc_d : 0;
+  const int64_t thr = 2 * m > 100000 ? 2 * m : 100000;
+  out->should_corner = out->candidates >= thr ? 1 : 0;
+  out->precision = precision;
+  out->seconds = r.seconds;
+  out->omega = r.omega;
+  out->eta = r.eta;
+  out->sigma_max = r.sigma_max;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const int32_t* n, const int64_t* nnz,
+                       const int64_t* const* row_ptr, const int32_t* const* col_idx, const double* const* val,
+                       const double* const* b, const double* const* c, const double* const* lb,
+                       const double* const* ub, const int8_t* const* sense, void* cuda_stream) {
+  if (!out || count < 1 || !m || !n || !nnz || !row_ptr || !col_idx || !val || !b || !c)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  std::unique_ptr<pdhgc_batch> B(new pdhgc_batch());
+  B->count = count;
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<Prepared> P(count);
+  int64_t sm = 0, sn = 0, snz = 0;
+  for (int k = 0; k < count; ++k) {
+    std::string detail;
+    const int rc = prepare_lp(P[k], m[k], n[k], nnz[k], row_ptr[k], col_idx[k], val[k], b[k], c[k],
+                              lb ? lb[k] : nullptr, ub ? ub[k] : nullptr, sense ? sense[k] : nullptr, detail);
+    if (rc != PDHGC_OK) return set_berr(rc, "LP " + std::to_string(k) + ": " + detail);
+    sm += m[k];
+    sn += n[k];
+    snz += nnz[k];
+  }
+  if (snz >= (int64_t(1) << 31)) return set_berr(PDHGC_ERR_TOO_LARGE, "total nnz must be < 2^31");
+  auto& A = B->allocs;
+  // packed arrays
+  int *rpA, *colA, *rpT, *colT, *rperm, *cperm;
+  double *valA, *valT, *hatA, *hatT;
+  float *hatA32, *hatT32;
+  const size_t M = (size_t)sm, N = (size_t)sn, NZ = (size_t)snz, K = (size_t)count;
+  int rc = PDHGC_OK;
+#define BAL(p, cnt)                                   \
+  do {                                                \
+    rc = dalloc(A, &p, cnt);                          \
+    if (rc != PDHGC_OK) return set_berr(rc, "cudaMalloc failed"); \
+  } while (0)
+  BAL(rpA, M + K);
+  BAL(colA, NZ);
+  BAL(rpT, N + K);
+  BAL(colT, NZ);
+  BAL(rperm, M);
+  BAL(cperm, N);
+  BAL(valA, NZ);
+  BAL(valT, NZ);
+  BAL(hatA, NZ);
+  BAL(hatT, NZ);
+  BAL(hatA32, NZ);
+  BAL(hatT32, NZ);
+  size_t SA = 0, ST = 0, SNA = 0, SNT = 0;  // SELL slots and slices of A and A'
+  for (int k = 0; k < count; ++k) {
+    SA += P[k].A.sell_map.size();
+    ST += P[k].AT.sell_map.size();
+    SNA += P[k].A.nslices;
+    SNT += P[k].AT.nslices;
+  }
+  int *sptrA, *swA, *scolA, *smapA, *sptrT, *swT, *scolT, *smapT;
+  double *svalA, *svalT, *shatA, *shatT;
+  float *shatA32, *shatT32;
+  BAL(sptrA, SNA + K); BAL(swA, SNA + 1); BAL(scolA, SA + kPad); BAL(smapA, SA + 1);
+  BAL(sptrT, SNT + K); BAL(swT, SNT + 1); BAL(scolT, ST + kPad); BAL(smapT, ST + 1);
+  BAL(svalA, SA + kPad); BAL(svalT, ST + kPad); BAL(shatA, SA + kPad); BAL(shatT, ST + kPad);
+  BAL(shatA32, SA + kPad); BAL(shatT32, ST + kPad);
+  double *b_int, *cc, *l, *u, *Dr, *Dc, *rfac, *cfac, *bhat, *chat, *lhat, *uhat, *chat_c, *lhat_c, *uhat_c;
+  double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r, *x1, *y1, *xc, *pi_v, *pi_w, *pi_u;
+  float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32, *x32, *xbar32, *y32;
+  int8_t *ge, *ge_c;
+  BAL(b_int, M); BAL(cc, N); BAL(l, N); BAL(u, N); BAL(Dr, M); BAL(Dc, N); BAL(rfac, M); BAL(cfac, N);
+  BAL(bhat, M); BAL(chat, N); BAL(lhat, N); BAL(uhat, N); BAL(chat_c, N); BAL(lhat_c, N); BAL(uhat_c, N);
+  BAL(x, N); BAL(xbar, N); BAL(sum_x, N); BAL(x_r, N); BAL(y, M); BAL(sum_y, M); BAL(y_r, M);
+  BAL(x1, N); BAL(y1, M); BAL(xc, N); BAL(pi_v, N); BAL(pi_w, N); BAL(pi_u, M);
+  double* keep;
+  BAL(keep, 4 * K);
+  BAL(bhat32, M); BAL(chat32, N); BAL(lhat32, N); BAL(uhat32, N); BAL(chat_c32, N); BAL(lhat_c32, N);
+  BAL(uhat_c32, N); BAL(x32, N); BAL(xbar32, N); BAL(y32, M);
+  BAL(ge, M); BAL(ge_c, M);
+  BAL(B->d_desc, K);
+  BAL(B->d_order, K);
+  BAL(B->d_queue, 1);
+  BAL(B->d_rep, K);
+#undef BAL
+  cudaStream_t st = B->stream;
+  B->h_desc.resize(count);
+  B->row_perm.resize(count);
+  B->col_perm.resize(count);
+  B->sign.resize(count);
+  size_t om = 0, on = 0, onz = 0, orA = 0, orT = 0;
+  size_t osA = 0, osT = 0, onsA = 0, onsT = 0;  // SELL slot and slice offsets
+  size_t max_f32 = 0, max_f64 = 0;
+  for (int k = 0; k < count; ++k) {
+    const Prepared& Q = P[k];
+    LpDesc& d = B->h_desc[k];
+    std::memset(&d, 0, sizeof(d));
+    d.m = Q.m;
+    d.n = Q.n;
+    d.nnz = (int)Q.nnz;
+    d.gA = lanes_for(Q.m ? (double)Q.nnz / Q.m : 1.0);
+    d.gT = lanes_for(Q.n ? (double)Q.nnz / Q.n : 1.0);
+    d.sell = 0;  // CSR rows; pdhgc_batch_tune may switch to SELL-32
+    d.b_norm = Q.b_norm;
+    d.c_norm = Q.c_norm;
+    const size_t v32 = (size_t)(Q.m + Q.n) * 4, v64 = (size_t)(Q.m + Q.n) * 8;
+    d.smem = v64 <= kSmemBudget ? 1 : 0;  // FP64 decides; an FP32 run also fits then
+    if (d.smem) {
+      max_f32 = std::max(max_f32, v32);
+      max_f64 = std::max(max_f64, v64);
+    }
+    d.A_rp = rpA + orA;
+    d.A_col = colA + onz;
+    d.T_rp = rpT + orT;
+    d.T_col = colT + onz;
+    d.A_val = valA + onz;
+    d.T_val = valT + onz;
+    d.A_hat = hatA + onz;
+    d.T_hat = hatT + onz;
+    d.A_hat32 = hatA32 + onz;
+    d.T_hat32 = hatT32 + onz;
+    d.b_int = b_int + om;
+    d.c = cc + on;
+    d.l = l + on;
+    d.u = u + on;
+    d.ge = ge + om;
+    d.ge_c = ge_c + om;
+    d.Dr = Dr + om; d.Dc = Dc + on; d.rfac = rfac + om; d.cfac = cfac + on;
+    d.bhat = bhat + om; d.chat = chat + on; d.lhat = lhat + on; d.uhat = uhat + on;
+    d.chat_c = chat_c + on; d.lhat_c = lhat_c + on; d.uhat_c = uhat_c + on;
+    d.bhat32 = bhat32 + om; d.chat32 = chat32 + on; d.lhat32 = lhat32 + on; d.uhat32 = uhat32 + on;
+    d.chat_c32 = chat_c32 + on; d.lhat_c32 = lhat_c32 + on; d.uhat_c32 = uhat_c32 + on;
+    d.x = x + on; d.xbar = xbar + on; d.sum_x = sum_x + on; d.x_r = x_r + on;
+    d.y = y + om; d.sum_y = sum_y + om; d.y_r = y_r + om;
+    d.x32 = x32 + on; d.xbar32 = xbar32 + on; d.y32 = y32 + om;
+    d.x1 = x1 + on; d.y1 = y1 + om; d.xc = xc + on;
+    d.pi_v = pi_v + on; d.pi_w = pi_w + on; d.pi_u = pi_u + om;
+    d.keep = keep + 4 * (size_t)k;
+    d.row_perm = rperm + om;
+    d.col_perm = cperm + on;
+    // SELL-32 copies (indices and original values filled here from the slot map)
+    for (int which = 0; which < 2; ++which) {
+      const Csr& C = which ? Q.AT : Q.A;
+      const size_t os = which ? osT : osA, ons = which ? onsT : onsA;
+      int* sptr = (which ? sptrT : sptrA) + ons + k;  // nslices + 1 per LP
+      int* sw = (which ? swT : swA) + ons;
+      int* scol = (which ? scolT : scolA) + os;
+      int* smap = (which ? smapT : smapA) + os;
+      double* sval = (which ? svalT : svalA) + os;
+      const size_t slots = C.sell_map.size();
+      std::vector<int32_t> hc(slots);
+      std::vector<double> hv(slots);
+      for (size_t t = 0; t < slots; ++t) {
+        const int32_t e = C.sell_map[t];
+        hc[t] = e >= 0 ? C.col[e] : 0;
+        hv[t] = e >= 0 ? C.val[e] : 0.0;
+      }
+      BCK(cudaMemcpyAsync(sptr, C.slice_ptr.data(), (C.nslices + 1) * 4, cudaMemcpyHostToDevice, st));
+      if (C.nslices) BCK(cudaMemcpyAsync(sw, C.slice_w.data(), (size_t)C.nslices * 4, cudaMemcpyHostToDevice, st));
+      if (slots) {
+        BCK(cudaMemcpyAsync(scol, hc.data(), slots * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(smap, C.sell_map.data(), slots * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(sval, hv.data(), slots * 8, cudaMemcpyHostToDevice, st));
+        BCK(cudaStreamSynchronize(st));  // the host staging vectors go out of scope
+      }
+      if (which) {
+        d.T_long = C.long_rows; d.T_ns = C.nslices; d.T_slots = (int)slots;
+        d.T_sptr = sptr; d.T_sw = sw; d.T_scol = scol; d.T_smap = smap; d.T_sval = sval;
+        d.T_shat = shatT + os; d.T_shat32 = shatT32 + os;
+      } else {
+        d.A_long = C.long_rows; d.A_ns = C.nslices; d.A_slots = (int)slots;
+        d.A_sptr = sptr; d.A_sw = sw; d.A_scol = scol; d.A_smap = smap; d.A_sval = sval;
+        d.A_shat = shatA + os; d.A_shat32 = shatA32 + os;
+      }
+    }
+    const size_t nz = (size_t)Q.nnz;
+    BCK(cudaMemcpyAsync((void*)d.A_rp, Q.A.row_ptr.data(), (Q.m + 1) * 4, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.T_rp, Q.AT.row_ptr.data(), ((size_t)Q.n + 1) * 4, cudaMemcpyHostToDevice, st));
+    if (nz) {
+      BCK(cudaMemcpyAsync((void*)d.A_col, Q.A.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
+      BCK(cudaMemcpyAsync((void*)d.T_col, Q.AT.col.data(), nz * 4, cudaMemcpyHostToDevice, st));
+      BCK(cudaMemcpyAsync((void*)d.A_val, Q.A.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
+      BCK(cudaMemcpyAsync((void*)d.T_val, Q.AT.val.data(), nz * 8, cudaMemcpyHostToDevice, st));
+    }
+    BCK(cudaMemcpyAsync((void*)d.b_int, Q.b_int.data(), (size_t)Q.m * 8, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.c, Q.c.data(), (size_t)Q.n * 8, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.l, Q.l.data(), (size_t)Q.n * 8, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.u, Q.u.data(), (size_t)Q.n * 8, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.ge, Q.ge.data(), (size_t)Q.m, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.row_perm, Q.row_perm.data(), (size_t)Q.m * 4, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync((void*)d.col_perm, Q.col_perm.data(), (size_t)Q.n * 4, cudaMemcpyHostToDevice, st));
+    B->row_perm[k] = Q.row_perm;
+    B->col_perm[k] = Q.col_perm;
+    B->sign[k] = Q.sign;
+    om += Q.m;
+    on += Q.n;
+    onz += nz;
+    osA += Q.A.sell_map.size();
+    osT += Q.AT.sell_map.size();
+    onsA += Q.A.nslices;
+    onsT += Q.AT.nslices;
+    orA += Q.m + 1;
+    orT += Q.n + 1;
+  }
+  B->smem_f32 = std::max<size_t>(max_f32, 16);
+  B->smem_f64 = std::max<size_t>(max_f64, 16);
+  // largest LPs first
+  B->order.resize(count);
+  std::iota(B->order.begin(), B->order.end(), 0);
+  std::stable_sort(B->order.begin(), B->order.end(),
+                   [&](int a, int b2) { return P[a].nnz + P[a].n > P[b2].nnz + P[b2].n; });
+  BCK(cudaMemcpyAsync(B->d_desc, B->h_desc.data(), K * sizeof(LpDesc), cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(B->d_order, B->order.data(), K * sizeof(int), cudaMemcpyHostToDevice, st));
+  BCK(cudaStreamSynchronize(st));
+  BCK(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+  B->h_rep1.resize(count);
+  B->h_repc.resize(count);
+  pdhgc_default_params(&B->params);
+  *out = B.release();
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* reports) {
+  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
+  pdhgc_params p;
+  if (params) p = *params; else pdhgc_default_params(&p);
+  if (p.max_iters < 1 || p.check_period < 1 || p.check_period > 4096 || p.ruiz_iters < 0 || p.power_iters < 1 ||
+      !(p.eta_factor > 0.0 && p.eta_factor < 1.0) || !(p.time_limit_s > 0.0) ||
+      (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK))
+    return set_berr(PDHGC_ERR_INVALID_ARG, "parameter out of range");
+  B->params = p;
+  B->precision = p.precision;
+  B->have_phase1 = 0;
+  B->have_corner = 0;
+  cudaStream_t st = B->stream;
+  RET(run_batch(B, make_params(p, nullptr), 0, st));
+  BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  for (int k = 0; k < B->count; ++k)
+    if (reports)
+      to_report(B->h_rep1[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, p.precision, &reports[k]);
+  B->have_phase1 = 1;
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, pdhgc_report* reports) {
+  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
+  if (!B->have_phase1) return set_berr(PDHGC_ERR_NO_PHASE1, "pdhgc_batch_solve has not run");
+  pdhgc_corner_params cp;
+  if (params) cp = *params; else pdhgc_default_corner_params(&cp);
+  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
+    return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  cudaStream_t st = B->stream;
+  RET(run_batch(B, make_params(B->params, &cp), 1, st));
+  BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  for (int k = 0; k < B->count; ++k)
+    if (reports)
+      to_report(B->h_repc[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, B->precision,
+                &reports[k]);
+  B->have_corner = 1;
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_get_solution(pdhgc_batch* B, int32_t lp, int which, double* x, double* y) {
+  if (!B || lp < 0 || lp >= B->count || (which != PDHGC_PHASE1 && which != PDHGC_CORNER))
+    return set_berr(PDHGC_ERR_INVALID_ARG, "bad argument");
+  if (!B->have_phase1) return set_berr(PDHGC_ERR_NO_PHASE1, "pdhgc_batch_solve has not run");
+  if (which == PDHGC_CORNER && !B->have_corner) return set_berr(PDHGC_ERR_NO_CORNER, "no corner result");
+  const LpDesc& d = B->h_desc[lp];
+  std::vector<double> xs(d.n), ys(d.m), Dc(d.n), Dr(d.m);
+  cudaStream_t st = B->stream;
+  BCK(cudaMemcpyAsync(xs.data(), which == PDHGC_PHASE1 ? d.x1 : d.xc, (size_t)d.n * 8, cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(ys.data(), d.y1, (size_t)d.m * 8, cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(Dc.data(), d.Dc, (size_t)d.n * 8, cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(Dr.data(), d.Dr, (size_t)d.m * 8, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  if (x)
+    for (int j = 0; j < d.n; ++j) x[B->col_perm[lp][j]] = Dc[j] * xs[j];
+  if (y)
+    for (int i = 0; i < d.m; ++i) y[B->row_perm[lp][i]] = B->sign[lp][i] * (Dr[i] * ys[i]);
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_set_block(pdhgc_batch* B, int32_t threads) {
+  if (!B || (threads != 512 && threads != 1024)) return set_berr(PDHGC_ERR_INVALID_ARG, "threads must be 512 or 1024");
+  B->block = threads;
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_set_lanes(pdhgc_batch* B, int32_t lanes_a, int32_t lanes_t) {
+  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
+  auto ok = [](int g) { return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; };
+  if (!ok(lanes_a) || !ok(lanes_t)) return set_berr(PDHGC_ERR_INVALID_ARG, "lanes must be 0 (auto) or 1..32, a power of two");
+  for (int k = 0; k < B->count; ++k) {
+    LpDesc& d = B->h_desc[k];
+    d.gA = lanes_a ? lanes_a : lanes_for(d.m ? (double)d.nnz / d.m : 1.0);
+    d.gT = lanes_t ? lanes_t : lanes_for(d.n ? (double)d.nnz / d.n : 1.0);
+  }
+  BCK(cudaMemcpyAsync(B->d_desc, B->h_desc.data(), B->count * sizeof(LpDesc), cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_set_layout(pdhgc_batch* B, int32_t sell) {
+  if (!B || (sell != 0 && sell != 1)) return set_berr(PDHGC_ERR_INVALID_ARG, "sell must be 0 or 1");
+  for (int k = 0; k < B->count; ++k) B->h_desc[k].sell = sell;
+  BCK(cudaMemcpyAsync(B->d_desc, B->h_desc.data(), B->count * sizeof(LpDesc), cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return PDHGC_OK;
+}
+
+// The schedule autotuner: times a fixed number of iterations of the whole
+// batch (setup included, no early termination, so every candidate does the
+// same work) for each candidate schedule and keeps the fastest.
+int pdhgc_batch_tune(pdhgc_batch* B, const pdhgc_params* params, int32_t tune_iters, int32_t* chosen,
+                     double* timings_ms) {
+  if (!B || tune_iters < 1) return set_berr(PDHGC_ERR_INVALID_ARG, "bad argument");
+  pdhgc_params p;
+  if (params) p = *params; else pdhgc_default_params(&p);
+  if (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "precision must be PDHGC_FP64 or PDHGC_FP32_BULK");
+  p.max_iters = tune_iters;
+  p.eps_rel = -1.0;
+  B->precision = p.precision;
+  struct Cand {
+    int block, sell, la, lt;
+  };
+  const Cand cands[] = {{1024, 1, 0, 0}, {512, 1, 0, 0}, {1024, 0, 0, 0}, {512, 0, 0, 0},
+                        {1024, 0, 4, 2}, {1024, 0, 1, 1}, {1024, 0, 8, 4}};
+  const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  const BatchParams bp = make_params(p, nullptr);
+  for (int ci = 0; ci < nc; ++ci) {
+    RET(pdhgc_batch_set_block(B, cands[ci].block));
+    RET(pdhgc_batch_set_layout(B, cands[ci].sell));
+    RET(pdhgc_batch_set_lanes(B, cands[ci].la, cands[ci].lt));
+    BCK(cudaEventRecord(e0, B->stream));
+    RET(run_batch(B, bp, 0, B->stream));
+    BCK(cudaEventRecord(e1, B->stream));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BCK(cudaEventElapsedTime(&ms, e0, e1));
+    if (timings_ms) timings_ms[ci] = ms;
+    if (ci == 0 || ms < best_ms) {
+      best = ci;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RET(pdhgc_batch_set_block(B, cands[best].block));
+  RET(pdhgc_batch_set_layout(B, cands[best].sell));
+  RET(pdhgc_batch_set_lanes(B, cands[best].la, cands[best].lt));
+  if (chosen) {
+    chosen[0] = cands[best].block;
+    chosen[1] = cands[best].sell;
+    chosen[2] = cands[best].la;
+    chosen[3] = cands[best].lt;
+  }
+  B->have_phase1 = 0;  // the tuning runs overwrote the phase-1 state
+  B->have_corner = 0;
+  return PDHGC_OK;
+}
+
+void pdhgc_batch_destroy(pdhgc_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  delete B;
+}
+
+}  // extern "C"

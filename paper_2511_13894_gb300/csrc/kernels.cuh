@@ -11,6 +11,7 @@
 
 #include <type_traits>
 
+#include "../../include/pdhgc.h"
 #include "host_prep.h"
 
 namespace pdhgc {
@@ -113,6 +114,100 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// The decision made at a check, from the 22 folded KKT quantities q
+// (rows: 5 per point, cur then avg; columns: 6 per point): the Section 2
+// ratios and the omega-weighted KKT of both points, then termination (the
+// Section 2 test in phase 1, the Section 3.1 rule in the corner phase),
+// limits, and the adaptive restart with its primal-weight update.
+// mode 0 only records KKT_omega of the start point as the restart reference.
+// Runs on one thread; shared by the graph-driven and the batched solvers.
+__device__ inline void decide_step(Scalars* S, const double* q, int mode) {
+
+  double nrp2[2], nrd2[2], gap[2], dx2[2], dy2[2];
+  const double om = S->omega;
+  for (int w = 0; w < 2; ++w) {
+    nrp2[w] = q[5 * w + 0];
+    const double rP2 = sqrt(q[5 * w + 1]);
+    const double by = q[5 * w + 3];
+    dy2[w] = q[5 * w + 4];
+    nrd2[w] = q[10 + 6 * w + 0];
+    const double rD2 = sqrt(q[10 + 6 * w + 1]);
+    const double cx = q[10 + 6 * w + 3];
+    const double bnd = q[10 + 6 * w + 4];
+    dx2[w] = q[10 + 6 * w + 5];
+    const double pobj = cx, dobj = by + bnd;
+    gap[w] = pobj - dobj;
+    S->kkt[w] = sqrt(om * nrp2[w] + nrd2[w] / om + gap[w] * gap[w]);
+    S->rP2[w] = rP2;
+    S->rel_p[w] = rP2 / (1.0 + S->nb);
+    S->rel_d[w] = rD2 / (1.0 + S->nc);
+    S->rel_gap[w] = fabs(gap[w]) / (1.0 + fabs(pobj) + fabs(dobj));
+    S->rel_kkt[w] = fmax(S->rel_p[w], fmax(S->rel_d[w], S->rel_gap[w]));
+  }
+  if (mode == 0) {
+    S->kkt_r = S->kkt[0];
+    S->kkt_prev = INFINITY;
+    return;
+  }
+  S->restart_to = 0;
+  const int pick = S->rel_kkt[1] <= S->rel_kkt[0] ? 1 : 0;
+  const double elapsed = (double)(global_ns() - S->t0_ns) * 1e-9;
+  const bool finite = isfinite(S->kkt[0]) && isfinite(S->kkt[1]);
+  if (S->phase == 0) {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_NUMERICAL; S->chosen = 0;
+    } else if (S->at_check && fmin(S->rel_kkt[0], S->rel_kkt[1]) <= S->eps_rel) {
+      S->done = 1; S->status = PDHGC_STATUS_OPTIMAL; S->chosen = pick;
+    } else if (S->at_limit) {
+      S->done = 1; S->status = PDHGC_STATUS_ITER_LIMIT; S->chosen = pick;
+    } else if (elapsed > S->time_limit_s) {
+      S->done = 1; S->status = PDHGC_STATUS_TIME_LIMIT; S->chosen = pick;
+    }
+  } else {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 0;
+    } else if (S->at_check && S->k >= S->min_iters) {
+      const double tol = S->eps_rel * (1.0 + S->nb);
+      if (S->stop_rule == 1) {
+        if (fmin(S->rel_kkt[0], S->rel_kkt[1]) <= S->eps_rel) {
+          S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = pick;
+        }
+      } else if (S->rP2[0] <= tol) {
+        S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 0;
+      } else if (S->rP2[1] <= tol) {
+        S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 1;
+      }
+    }
+    if (!S->done && (S->at_limit || elapsed > S->time_limit_s)) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 0;
+    }
+  }
+  if (!S->done) {
+    const int c = S->kkt[1] <= S->kkt[0] ? 1 : 0;
+    const double kc = S->kkt[c];
+    const bool restart = kc <= S->beta_suff * S->kkt_r ||
+                         (kc <= S->beta_nec * S->kkt_r && kc > S->kkt_prev) ||
+                         (double)S->t >= S->beta_art * (double)S->k;
+    if (!restart) {
+      S->kkt_prev = kc;
+    } else {
+      const double dx = sqrt(dx2[c]), dy = sqrt(dy2[c]);
+      double omega = S->omega;
+      if (dx > 1e-10 && dy > 1e-10)
+        omega = exp(S->theta * log(dy / dx) + (1.0 - S->theta) * log(omega));
+      S->omega = omega;
+      S->kkt_r = sqrt(omega * nrp2[c] + nrd2[c] / omega + gap[c] * gap[c]);
+      S->kkt_prev = INFINITY;
+      S->t = 0;
+      S->restarts += 1;
+      S->restart_to = c ? 2 : 1;
+      S->tau = S->eta / omega;
+      S->sigma = S->eta * omega;
+    }
+  }
+  S->t1_ns = global_ns();
 }
 
 // ---------------------------------------------------------------------------
@@ -795,7 +890,7 @@ struct CornerColsOp {
 // ---------------------------------------------------------------------------
 
 // deterministic sum (or max) of partials[q * ntiles + 0 .. ntiles-1] by one CTA
-__device__ double block_fold(const double* __restrict__ p, int ntiles, bool is_max, double* s_tmp) {
+__device__ inline double block_fold(const double* __restrict__ p, int ntiles, bool is_max, double* s_tmp) {
   double v = 0.0;
   for (int k = threadIdx.x; k < ntiles; k += blockDim.x) v = is_max ? fmax(v, p[k]) : v + p[k];
   for (int off = 16; off > 0; off >>= 1) {

@@ -93,6 +93,16 @@ _sig = {
     "pdhgc_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_profile_iteration": (C.c_int, [_vp, C.c_int32, _vp]),
     "pdhgc_lp_destroy": (None, [_vp]),
+    "pdhgc_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp]),
+    "pdhgc_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp]),
+    "pdhgc_batch_corner_phase": (C.c_int, [_vp, C.POINTER(CornerParams), _vp]),
+    "pdhgc_batch_get_solution": (C.c_int, [_vp, C.c_int32, C.c_int, _vp, _vp]),
+    "pdhgc_batch_set_block": (C.c_int, [_vp, C.c_int32]),
+    "pdhgc_batch_set_lanes": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "pdhgc_batch_destroy": (None, [_vp]),
+    "pdhgc_batch_set_layout": (C.c_int, [_vp, C.c_int32]),
+    "pdhgc_batch_tune": (C.c_int, [_vp, C.POINTER(Params), C.c_int32, _vp, _vp]),
     "pdhgc_strerror": (C.c_char_p, [C.c_int]),
     "pdhgc_last_error_detail": (C.c_char_p, []),
 }
@@ -273,6 +283,92 @@ def lp_from_dict(lp: dict, stream=None, device=False) -> LP:
         arrs = [None if a is None else torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
                 for a, dt in zip(arrs, dts)]
     return lp_create(lp["m"], lp["n"], *arrs, stream=stream)
+
+
+class Batch:
+    """Many LPs solved by one persistent launch (pdhgc_batch_*).  `lps` is a
+    list of generator dicts (host arrays)."""
+
+    _KEYS = (("row_ptr", np.int64), ("col_idx", np.int32), ("val", np.float64), ("b", np.float64),
+             ("c", np.float64), ("lb", np.float64), ("ub", np.float64), ("sense", np.int8))
+
+    def __init__(self, lps, stream=None):
+        self.count = len(lps)
+        self.m = [int(lp["m"]) for lp in lps]
+        self.n = [int(lp["n"]) for lp in lps]
+        self._keep = []
+        ptrs = {}
+        for key, dt in self._KEYS:
+            arr = (C.c_void_p * self.count)()
+            for k, lp in enumerate(lps):
+                a = lp.get(key)
+                if a is None:
+                    arr[k] = None
+                    continue
+                a = np.ascontiguousarray(a, dtype=dt)
+                self._keep.append(a)
+                arr[k] = a.ctypes.data
+            ptrs[key] = arr
+        m = np.array(self.m, dtype=np.int32)
+        n = np.array(self.n, dtype=np.int32)
+        nnz = np.array([int(lp["row_ptr"][-1]) for lp in lps], dtype=np.int64)
+        self._keep += [m, n, nnz]
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        h = _vp()
+        _check(lib.pdhgc_batch_create(C.byref(h), self.count, m.ctypes.data, n.ctypes.data, nnz.ctypes.data,
+                                      *[C.cast(ptrs[k], _vp) for k, _ in self._KEYS], stream),
+               "pdhgc_batch_create")
+        self._h = h
+        self._keep = None  # create copied everything
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.pdhgc_batch_destroy(h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def solve(self, params: Params | None = None, **kw):
+        p = params if params is not None else default_params(**kw)
+        reps = (Report * self.count)()
+        _check(lib.pdhgc_batch_solve(self._h, C.byref(p), C.cast(reps, _vp)), "pdhgc_batch_solve")
+        return [r.as_dict() for r in reps]
+
+    def corner_phase(self, params: CornerParams | None = None, **kw):
+        p = params if params is not None else default_corner_params(**kw)
+        reps = (Report * self.count)()
+        _check(lib.pdhgc_batch_corner_phase(self._h, C.byref(p), C.cast(reps, _vp)), "pdhgc_batch_corner_phase")
+        return [r.as_dict() for r in reps]
+
+    def get_solution(self, k: int, which: int = PHASE1):
+        x = np.empty(self.n[k])
+        y = np.empty(self.m[k])
+        _check(lib.pdhgc_batch_get_solution(self._h, k, which, x.ctypes.data, y.ctypes.data),
+               "pdhgc_batch_get_solution")
+        return x, y
+
+    def set_block(self, threads: int):
+        _check(lib.pdhgc_batch_set_block(self._h, threads), "pdhgc_batch_set_block")
+
+    def set_lanes(self, lanes_a: int = 0, lanes_t: int = 0):
+        _check(lib.pdhgc_batch_set_lanes(self._h, lanes_a, lanes_t), "pdhgc_batch_set_lanes")
+
+    def set_layout(self, sell: int):
+        _check(lib.pdhgc_batch_set_layout(self._h, int(sell)), "pdhgc_batch_set_layout")
+
+    def tune(self, tune_iters: int = 256, params: Params | None = None, **kw):
+        """pdhgc_batch_tune: returns the chosen schedule and the candidates' times."""
+        p = params if params is not None else default_params(**kw)
+        chosen = np.zeros(4, dtype=np.int32)
+        ms = np.zeros(7)
+        _check(lib.pdhgc_batch_tune(self._h, C.byref(p), int(tune_iters), chosen.ctypes.data, ms.ctypes.data),
+               "pdhgc_batch_tune")
+        return dict(threads=int(chosen[0]), sell=int(chosen[1]), lanes_a=int(chosen[2]), lanes_t=int(chosen[3]),
+                    timings_ms=ms.tolist())
 
 
 def _device_lp_args(lp: dict, x, y):
