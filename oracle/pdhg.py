@@ -190,6 +190,11 @@ def project_dual_cone(lam, l, u):
     return z
 
 
+def reduced_cost_hat(model, y_hat):
+    """z_hat = proj_Lambda(c_hat - A_hat' y_hat): the scaled reduced costs."""
+    return project_dual_cone(model.chat - model.AhatT @ y_hat, model.lhat, model.uhat)
+
+
 def primal_residual(b, Ax, ge):
     """r_P = b - Ax on '=' rows; max(b - Ax, 0) on '>' rows (implicit slack)."""
     r = b - Ax
@@ -269,6 +274,9 @@ class State:
         self.kkt_r = kkt_omega(evaluate(model, self.x, self.y, omega), omega)
         self.kkt_prev = math.inf             # KKT_omega of the previous check's candidate
         self.restarts = 0
+        # restart history: (x, z) at the start point and at every restart,
+        # z = proj_Lambda(c_hat - A_hat' y) in scaled space (guidance features)
+        self.ring = [(self.x.copy(), reduced_cost_hat(model, self.y))]
 
     @property
     def tau(self):
@@ -331,6 +339,8 @@ def restart_check(model: Model, s: State, p, ev_cur, ev_avg):
     s.sum_y = np.zeros_like(s.y)
     s.t = 0
     s.restarts += 1
+    s.ring.append((xc.copy(), reduced_cost_hat(model, yc)))
+    del s.ring[:-8]
     return True
 
 
@@ -488,7 +498,15 @@ def kkt_report(model: Model, x_hat, y_hat, omega=1.0):
 # Algorithm 1: corner push PDHG (Section 3, 3.1)
 # ---------------------------------------------------------------------------
 
-def corner_model(model: Model, x_hat1, y_hat1, cp):
+def nearest_bound(x, l, u):
+    """The bound of [l, u] nearest to x (ties to l); NaN where both are infinite."""
+    dl = np.where(np.isfinite(l), x - l, np.inf)
+    du = np.where(np.isfinite(u), u - x, np.inf)
+    nb = np.where(dl <= du, l, u)
+    return np.where(np.isfinite(dl) | np.isfinite(du), nb, np.nan)
+
+
+def corner_model(model: Model, x_hat1, y_hat1, cp, hold=None):
     """The secondary model M_hat of Algorithm 1 in scaled space.
 
     z from the phase-1 point (unscaled, eps_abs):  ub_j <- x_j if z_j > eps_abs,
@@ -496,7 +514,11 @@ def corner_model(model: Model, x_hat1, y_hat1, cp):
     the start point stays inside the new box); inequality rows whose dual is
     non-trivial (|y_i| > eps_abs) become '=' with the same right-hand side
     (Section 3: slack upper bound fixed to zero); objective Uniform([0,1]^n)
-    times obj_scale, drawn in unscaled space and scaled like c."""
+    times obj_scale, drawn in unscaled space and scaled like c.
+
+    `hold` (guided form, not in the paper): a boolean mask of columns to hold
+    at the bound nearest to x_hat1 (l_hat = u_hat = that bound); columns the
+    rule above already fixed, and columns without a finite bound, are left."""
     _, y1, z1 = unscale(model, x_hat1, y_hat1)
     cm = model.copy()
     fix_up = z1 > cp["eps_abs"]
@@ -505,14 +527,23 @@ def corner_model(model: Model, x_hat1, y_hat1, cp):
     cm.lhat = np.where(fix_lo, x_hat1, model.lhat)
     cm.u = np.where(fix_up, x_hat1 * model.Dc, model.u)
     cm.l = np.where(fix_lo, x_hat1 * model.Dc, model.l)
+    held = np.zeros(model.n, dtype=bool)
+    if hold is not None:
+        nb = nearest_bound(x_hat1, model.lhat, model.uhat)
+        held = np.asarray(hold, dtype=bool) & ~fix_up & ~fix_lo & np.isfinite(nb)
+        cm.lhat = np.where(held, nb, cm.lhat)
+        cm.uhat = np.where(held, nb, cm.uhat)
+        cm.l = np.where(held, nb * model.Dc, cm.l)
+        cm.u = np.where(held, nb * model.Dc, cm.u)
     to_eq = model.ge & (np.abs(y1) > cp["eps_abs"])
     cm.ge = model.ge & ~to_eq
     cm.set_objective(cp["obj_scale"] * splitmix64_uniform(cp["obj_seed"], model.n))
     return cm, dict(fixed_upper=int(fix_up.sum()), fixed_lower=int(fix_lo.sum()),
-                    rows_to_eq=int(to_eq.sum()))
+                    rows_to_eq=int(to_eq.sum()), held=int(held.sum()),
+                    fixed=fix_up | fix_lo, held_mask=held)
 
 
-def corner_phase(phase1, corner_params=None):
+def corner_phase(phase1, corner_params=None, hold=None):
     """Algorithm 1 on the phase-1 result: build M_hat, run PDHG from (x, 0)
     with the same step size, stop once k >= min_iters and the primal residual
     of the current (else the average) point meets eps_rel (1 + ||b||) on M_hat,
@@ -525,8 +556,8 @@ def corner_phase(phase1, corner_params=None):
     p = dict(phase1["params"])
     eta = phase1["eta"]
     x1, y1 = phase1["x_hat"], phase1["y_hat"]
-    cm, info = corner_model(model, x1, y1, cp)
-    s = State(cm, x1.copy(), np.zeros(model.m), eta, initial_omega(cm))
+    cm, info = corner_model(model, x1, y1, cp, hold)
+    s = State(cm, project_box(x1, cm.lhat, cm.uhat), np.zeros(model.m), eta, initial_omega(cm))
     t0 = time.perf_counter()
     nb = float(np.linalg.norm(model.b_user))
     status = None
