@@ -332,6 +332,143 @@ int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tun
 
 void pdhgc_batch_destroy(pdhgc_batch* batch);
 
+/* ---- learned corner guidance (an extension of Algorithm 1; the paper has none) ----
+ *
+ * A per-column network predicts which columns the corner phase may hold at a
+ * bound.  Network: 18 features -> 64 -> 64 -> 1, ReLU hidden layers, sigmoid
+ * output read as P(column ends at a bound after the corner phase); BF16
+ * weights and activations, FP32 accumulation (tensor cores), trained on the
+ * mean binary cross-entropy with Adam (Kingma & Ba 2015: beta1 0.9, beta2
+ * 0.999, eps 1e-8).
+ *
+ * Features of column j (PDHGC_GUIDE_FEATURES = 18), from a phase-1 result and
+ * the corner parameters (the objective seed):
+ *   [0]      c'_j: Algorithm 1's random objective, scaled like c (the
+ *            objective of the LP the corner phase solves);
+ *   [1]      ||A_hat_j||_2, the column norm of the scaled matrix;
+ *   [2..9]   x_hat_j at the last 8 restart points of phase 1, newest first
+ *            (the start point counts as the first; padded with the oldest);
+ *   [10..17] z_hat_j = proj(c_hat - A_hat' y_hat)_j at the same points;
+ * each of the four groups divided by its root mean square over all columns.
+ * Stored as BF16 rows of PDHGC_GUIDE_FEAT_STRIDE (32) values, 64 bytes, the
+ * entries 18..31 zero; row-major, 16-byte aligned, in user column order.
+ *
+ * A column is eligible for holding when Algorithm 1's reduced-cost rule did
+ * not fix it and it has a finite bound; a held column gets l_hat = u_hat =
+ * the bound of [l_hat, u_hat] nearest to its phase-1 value (ties: lower),
+ * and the corner phase starts there.
+ *
+ * Parameter vector (PDHGC_GUIDE_PARAMS = 5441 FP32): W1 [64][18], b1 [64],
+ * W2 [64][64], b2 [64], w3 [64], b3 — row-major, unit-major rows.
+ */
+#define PDHGC_GUIDE_FEATURES    18
+#define PDHGC_GUIDE_FEAT_STRIDE 32
+#define PDHGC_GUIDE_PARAMS      5441
+#define PDHGC_STATUS_GUIDE_FALLBACK 7  /* pdhgc_guide_report.status: the plain corner result was returned */
+
+typedef struct pdhgc_guide pdhgc_guide;
+
+typedef struct {
+    double threshold;   /* hold an eligible column when its probability >= threshold (0.9) */
+    int32_t fallback;   /* 1 (default): run the plain corner phase when the guided one regresses */
+    int32_t reserved;
+} pdhgc_guide_params;
+
+typedef struct {
+    int32_t status;                 /* guided run's status; PDHGC_STATUS_GUIDE_FALLBACK when replaced */
+    int32_t fell_back;              /* 1 when the plain corner phase's result was returned */
+    int64_t eligible, held;         /* eligible columns; columns held at a bound */
+    int64_t guided_iters;           /* iterations of the guided corner run */
+    double guided_seconds;          /* device time of the guided run (features and inference included) */
+    double guided_rel_kkt;          /* its relative KKT error on the original model */
+    int64_t guided_corner_measure;  /* its corner measure */
+    double infer_seconds;           /* features + network inference */
+} pdhgc_guide_report;
+
+/* pdhgc_default_guide_params — threshold 0.9, fallback 1. */
+void pdhgc_default_guide_params(pdhgc_guide_params* p);
+
+/*
+ * pdhgc_guide_create — a network with He-uniform initial weights drawn from
+ * SplitMix64(seed) (biases 0); device memory on the current device, work on
+ * `cuda_stream`.  Errors: INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_guide_create(pdhgc_guide** out, uint64_t seed, void* cuda_stream);
+void pdhgc_guide_destroy(pdhgc_guide* g);
+
+/* set (resets Adam's moments) / read the FP32 parameter vector; host arrays of PDHGC_GUIDE_PARAMS.
+ * Errors: INVALID_ARG, NONFINITE (set). */
+int pdhgc_guide_set_weights(pdhgc_guide* g, const float* w);
+int pdhgc_guide_get_weights(pdhgc_guide* g, float* w);
+
+/*
+ * pdhgc_guide_infer — probabilities p[r] for `rows` feature rows; feat and p
+ * are DEVICE pointers (feat: rows x 32 BF16, 16-byte aligned; p: rows FP32).
+ * Errors: INVALID_ARG (NULL, rows < 1, misaligned), CUDA.
+ */
+int pdhgc_guide_infer(pdhgc_guide* g, const uint16_t* feat, int64_t rows, float* p);
+
+/*
+ * pdhgc_guide_grad — gradient of the mean binary cross-entropy over the
+ * minibatch idx[0..batch-1] (HOST int32 indices into the rows of the DEVICE
+ * arrays feat and labels (uint8 0/1)), without updating the weights; grad
+ * (host, PDHGC_GUIDE_PARAMS floats) in the parameter-vector layout; loss
+ * (host, may be NULL).  Errors: INVALID_ARG (index out of range), CUDA, OOM.
+ */
+int pdhgc_guide_grad(pdhgc_guide* g, const uint16_t* feat, const uint8_t* labels, int64_t rows,
+                     const int32_t* idx, int32_t batch, float* grad, float* loss);
+
+/*
+ * pdhgc_guide_train — `steps` Adam steps at learning rate lr on minibatches
+ * of `batch` rows drawn with replacement: row SplitMix64(seed, step * batch
+ * + s) mod rows for s < batch.  feat and labels are DEVICE arrays as above;
+ * losses (host, `steps` floats, may be NULL) receives each step's minibatch
+ * loss.  Errors: INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_guide_train(pdhgc_guide* g, const uint16_t* feat, const uint8_t* labels, int64_t rows, int32_t batch,
+                      int64_t steps, float lr, uint64_t seed, float* losses);
+
+/*
+ * pdhgc_guide_features — the feature rows of every column of the handle's
+ * phase-1 result for the corner objective of `params` (NULL = defaults):
+ * feat (DEVICE, n rows, layout above), eligible (DEVICE uint8 n, may be
+ * NULL).  Rebuilds the corner model's bounds and objective (the next corner
+ * phase rebuilds them again); the phase-1 and corner results are untouched.
+ * Errors: NO_PHASE1, INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_guide_features(pdhgc_lp* lp, const pdhgc_corner_params* params, uint16_t* feat, uint8_t* eligible);
+
+/*
+ * pdhgc_guide_dataset_append — training rows from the last corner phase:
+ * for every eligible column (in user column order) its feature row (for the
+ * corner objective that phase used) and its label (1 when the returned
+ * corner x_j lies within 1e-6 of l_j or u_j in user space; on a
+ * CORNER_LIMIT status that point is the phase-1 x).  Rows are appended to the
+ * DEVICE arrays feat / labels at row *count, which is advanced.  Errors:
+ * NO_PHASE1, NO_CORNER, BUFFER (capacity - *count too small; *count is left
+ * unchanged and nothing is written), INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_guide_dataset_append(pdhgc_lp* lp, uint16_t* feat, uint8_t* labels, int64_t capacity, int64_t* count);
+
+/*
+ * pdhgc_corner_phase_guided — Algorithm 1 with held columns.  The hold set
+ * comes from the network g (eligible columns with probability >=
+ * gparams->threshold) or, when g is NULL, from `hold` (uint8 per user
+ * column, host or device per hold_on_device; non-eligible entries ignored).
+ * Exactly one of g and hold must be given.  With gparams->fallback = 1, a
+ * guided result that hit a limit, has a relative KKT error above
+ * max(phase-1 rel_kkt, params->eps_rel), or a corner measure above the
+ * phase-1 point's is replaced by the plain corner phase's (out then holds
+ * the plain run's report and gout->status = PDHGC_STATUS_GUIDE_FALLBACK).
+ * out / gout may be NULL.  Errors: as pdhgc_corner_phase, INVALID_ARG.
+ */
+int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, const pdhgc_guide_params* gparams,
+                              pdhgc_guide* g, const uint8_t* hold, int hold_on_device, pdhgc_report* out,
+                              pdhgc_guide_report* gout);
+
+/* pdhgc_guide_kernel_launches — CUDA kernels launched by this network so far. */
+int64_t pdhgc_guide_kernel_launches(const pdhgc_guide* g);
+
 /*
  * pdhgc_kernel_launches — number of CUDA kernels this handle has launched
  * so far (kernels inside the solve graph counted once per execution).

@@ -653,6 +653,10 @@ struct EvalColsOp {
   const double* __restrict__ sum_x;
   const double* __restrict__ x_r;
   DevModel md;
+  // optional: z_hat of the current (z_out0) and average (z_out1) point, for
+  // the restart history of the guidance features (phase 1 only)
+  double* __restrict__ z_out0;
+  double* __restrict__ z_out1;
   __device__ bool skip() const { return S->done; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 2;
@@ -671,6 +675,7 @@ struct EvalColsOp {
       const double aty = wv == 0 ? a.v[0] : a.v[1] * inv_t;
       const double lam = c - aty;
       const double z = proj_dual(lam, l, u);
+      if (z_out0) (wv == 0 ? z_out0 : z_out1)[j] = z;
       const double rd = lam - z;
       const double rdu = rd / dc;
       const double xw = wv == 0 ? x[j] : sum_x[j] * inv_t;
@@ -864,6 +869,7 @@ struct CornerColsOp {
   double* __restrict__ cc;
   double eps_abs, obj_scale;
   unsigned long long seed;
+  int8_t* __restrict__ fixed;  // optional: 1 where the reduced-cost rule fixed a bound
   __device__ bool skip() const { return false; }
   __device__ double row_ctx(int) const { return 0.0; }
   static constexpr int NG = 1;
@@ -877,6 +883,7 @@ struct CornerColsOp {
     const double z = proj_dual(lam, md.lhat[j], md.uhat[j]) / dc;
     lc[j] = z < -eps_abs ? x1[j] : md.lhat[j];
     uc[j] = z > eps_abs ? x1[j] : md.uhat[j];
+    if (fixed) fixed[j] = (z > eps_abs || z < -eps_abs) ? 1 : 0;
     const double cu = obj_scale * splitmix_uniform(seed, (unsigned long long)col_perm[j]);
     const double ch = dc * cu;
     cc[j] = ch;

@@ -3,6 +3,7 @@
 // Algorithm 1, reports and accessors.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -14,6 +15,7 @@
 #include "../../include/pdhgc.h"
 #include "host_prep.h"
 #include "kernels.cuh"
+#include "guide.h"
 #include "kkt_eval.h"
 
 using namespace pdhgc;
@@ -287,8 +289,17 @@ __global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, con
   if (use_handle) cudaGraphSetConditional(h, S->done ? 0u : 1u);
 }
 
+// restart history of phase 1 (guidance features): slot e mod 8 holds
+// (x_hat, z_hat) of restart point e, the start point being e = 0
+struct RingRec {
+  float* rx;
+  float* rz;
+  const double* z_cur;
+  const double* z_avg;
+};
+
 // restart: jump to the candidate, new restart point, sums cleared
-__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter32 w32) {
+__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter32 w32, RingRec rr) {
   const int rt = S->restart_to;
   if (rt == 0 || S->done) return;
   const double inv_t = S->inv_t;
@@ -299,6 +310,11 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.x_r[i] = xn;
     w.sum_x[i] = 0.0;
     if (w32.x && rt == 2) w32.x[i] = (float)xn;
+    if (rr.rx) {
+      const size_t slot = (size_t)(S->restarts % 8) * (size_t)n;
+      rr.rx[slot + i] = (float)xn;
+      rr.rz[slot + i] = (float)(rt == 2 ? rr.z_avg[i] : rr.z_cur[i]);
+    }
   }
   if (i < m) {
     const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
@@ -306,6 +322,14 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.y_r[i] = yn;
     w.sum_y[i] = 0.0;
     if (w32.y && rt == 2) w32.y[i] = (float)yn;
+  }
+}
+
+__global__ void k_ring_init(int n, const double* __restrict__ x, RingRec rr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    rr.rx[i] = (float)x[i];
+    rr.rz[i] = (float)rr.z_cur[i];
   }
 }
 
@@ -466,6 +490,19 @@ struct pdhgc_lp {
   double *x1 = nullptr, *y1 = nullptr, *xc = nullptr;
   double *chat_c = nullptr, *lhat_c = nullptr, *uhat_c = nullptr;
   int8_t* ge_c = nullptr;
+  // phase-1 restart history for the guidance features: 8 slots x n
+  float *ring_x = nullptr, *ring_z = nullptr;
+  double *z_cur = nullptr, *z_avg = nullptr;  // z_hat of the last evaluated points
+  // guidance buffers (allocated on first use)
+  bool have_gbufs = false;
+  uint16_t* gfeat = nullptr;  // n x 32 BF16 feature rows
+  float* gprob = nullptr;
+  uint8_t *ghold = nullptr, *gelig = nullptr, *glabel = nullptr, *gstage = nullptr;
+  int8_t* gfixed = nullptr;
+  double *gnorm = nullptr, *gxs = nullptr, *gpart = nullptr;
+  long long* gcount = nullptr;
+  int* gblk = nullptr;
+  pdhgc_corner_params cp_last{};
   double *pi_v = nullptr, *pi_w = nullptr, *pi_u = nullptr, *tmp_n = nullptr, *tmp_m = nullptr;
   double *pA = nullptr, *pT = nullptr, *scratch = nullptr;
   int* err = nullptr;  // device error word set by a kernel whose bounded wait ran out
@@ -646,10 +683,13 @@ int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
 }
 
 // the KKT evaluation of the current and average points (two matrix passes)
-int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st) {
+int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st, bool record_z) {
   const DevIter& w = lp->it;
   RET(launch_tiles(lp, false, true, EvalRowsOp{lp->S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, lp->pA, st));
-  RET(launch_tiles(lp, true, true, EvalColsOp{lp->S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, lp->pT, st));
+  RET(launch_tiles(lp, true, true,
+                   EvalColsOp{lp->S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md, record_z ? lp->z_cur : nullptr,
+                              record_z ? lp->z_avg : nullptr},
+                   lp->pT, st));
   return PDHGC_OK;
 }
 
@@ -666,10 +706,18 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
   lp->launches += 2;
   CKL();
-  RET(launch_eval(lp, md, st));
+  // phase 1 records its restart history (start point and restart points)
+  const bool ring = pi.phase == 0;
+  const RingRec rr = ring ? RingRec{lp->ring_x, lp->ring_z, lp->z_cur, lp->z_avg} : RingRec{};
+  RET(launch_eval(lp, md, st, ring));
   k_decide<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
   lp->launches++;
   CKL();
+  if (ring) {
+    k_ring_init<<<grid_for(n), 256, 0, st>>>(n, lp->it.x, rr);
+    lp->launches++;
+    CKL();
+  }
 
   // the loop: while (!done) { P iterations; pre-check; eval; decide; restart }
   cudaGraph_t graph = nullptr;
@@ -708,11 +756,11 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   if (rc == PDHGC_OK) {
     k_pre_check<<<1, 32, 0, cs>>>(lp->S);
     lp->launches++;
-    rc = launch_eval(lp, md, cs);
+    rc = launch_eval(lp, md, cs, ring);
   }
   if (rc == PDHGC_OK) {
     k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
-    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32);
+    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr);
     lp->launches += 2;
   }
   cudaGraph_t captured = nullptr;
@@ -842,6 +890,291 @@ int setup_mat(pdhgc_lp* lp, pdhgc_lp::Mat& M, const Csr& C, cudaStream_t st) {
     CKL();
   }
   return PDHGC_OK;
+}
+
+int check_corner_params(const pdhgc_corner_params& cp) {
+  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
+    return set_err(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  return PDHGC_OK;
+}
+
+// Algorithm 1's corner model: new bounds and objective (columns; `fixed`
+// optionally flags the columns the reduced-cost rule fixed), new senses
+// (rows), and the norms of the new objective for the primal weight
+int corner_build(pdhgc_lp* lp, const pdhgc_corner_params& cp, int8_t* fixed) {
+  cudaStream_t st = lp->stream;
+  const DevModel md = model_orig(lp);
+  RET(launch_tiles(lp, true, true,
+                   CornerColsOp{lp->y1, lp->x1, lp->col_perm, md, lp->lhat_c, lp->uhat_c, lp->chat_c, cp.eps_abs,
+                                cp.obj_scale, (unsigned long long)cp.obj_seed, fixed},
+                   lp->pT, st));
+  k_corner_rows<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->ge, lp->Dr, lp->y1, cp.eps_abs, lp->ge_c);
+  lp->launches++;
+  CKL();
+  k_fold2<<<1, 256, 0, st>>>(lp->pT, lp->ntT, lp->scratch + 8);
+  lp->launches++;
+  CKL();
+  return PDHGC_OK;
+}
+
+// the corner iterations from x_start (Section 3.1 stopping rule) and the report
+int corner_run(pdhgc_lp* lp, const pdhgc_corner_params& cp, const double* x_start, pdhgc_report* r) {
+  cudaStream_t st = lp->stream;
+  const pdhgc_params& p = lp->params;
+  PhaseInit pi{};
+  pi.eps_rel = cp.eps_rel;
+  pi.beta_suff = p.beta_suff;
+  pi.beta_nec = p.beta_nec;
+  pi.beta_art = p.beta_art;
+  pi.theta = p.theta;
+  pi.time_limit_s = cp.time_limit_s;
+  pi.nb = lp->b_norm;
+  pi.nc = 0.0;
+  pi.max_iters = cp.max_iters;
+  pi.min_iters = cp.min_iters;
+  pi.check_period = p.check_period;
+  pi.phase = 1;
+  pi.stop_rule = cp.stop_rule;
+  pi.use_cc2 = 1;
+  if (p.precision == PDHGC_FP32_BULK) {
+    RET(to32(lp, lp->chat_c, lp->chat_c32, lp->n, st));
+    RET(to32(lp, lp->lhat_c, lp->lhat_c32, lp->n, st));
+    RET(to32(lp, lp->uhat_c, lp->uhat_c32, lp->n, st));
+  }
+  RET(run_phase(lp, model_corner(lp), model32_corner(lp), pi, x_start, lp->scratch + 8, lp->xc, nullptr, lp->x1));
+  *r = pdhgc_report{};
+  RET(fill_phase_report(lp, r));
+  RET(run_report(lp, lp->xc, lp->y1, r));
+  return PDHGC_OK;
+}
+
+// ---- learned guidance: features, labels, held columns ---------------------
+
+int ensure_gbufs(pdhgc_lp* lp) {
+  if (lp->have_gbufs) return PDHGC_OK;
+  const int n = lp->n, nb = grid_for(n);
+  RET(lp->alloc(&lp->gfeat, (size_t)n * 32));
+  RET(lp->alloc(&lp->gprob, n));
+  RET(lp->alloc(&lp->ghold, n));
+  RET(lp->alloc(&lp->gelig, n));
+  RET(lp->alloc(&lp->glabel, n));
+  RET(lp->alloc(&lp->gstage, n));
+  RET(lp->alloc(&lp->gfixed, n));
+  RET(lp->alloc(&lp->gnorm, n));
+  RET(lp->alloc(&lp->gxs, n));
+  RET(lp->alloc(&lp->gpart, (size_t)4 * nb + 4));
+  RET(lp->alloc(&lp->gcount, 2));
+  RET(lp->alloc(&lp->gblk, (size_t)nb + 1));
+  lp->have_gbufs = true;
+  return PDHGC_OK;
+}
+
+// the 8 ring slots of the history features, newest first: restart point e
+// (e = 0 the start point) sits in slot e mod 8; fewer than 8 points are
+// padded with the oldest
+struct RingIdx {
+  int slot[8];
+};
+RingIdx ring_index(long long restarts) {
+  RingIdx ri{};
+  const long long oldest = restarts > 7 ? restarts - 7 : 0;
+  for (int k = 0; k < 8; ++k) {
+    long long e = restarts - k;
+    if (e < oldest) e = oldest;
+    ri.slot[k] = (int)(e % 8);
+  }
+  return ri;
+}
+
+// ||A_hat_j||_2: one warp per row of A_hat'
+__global__ void k_col_norm(int n, const int* __restrict__ rp, const double* __restrict__ hat, double* __restrict__ out) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= n) return;
+  const int j = (int)wid;
+  double s = 0.0;
+  for (int k = rp[j] + lane; k < rp[j + 1]; k += 32) s = fma(hat[k], hat[k], s);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[j] = sqrt(s);
+}
+
+// per-block sums of squares of the four feature groups (c', ||A_j||, x history, z history)
+__global__ void k_feat_sums(int n, const double* __restrict__ cc, const double* __restrict__ cn,
+                            const float* __restrict__ rx, const float* __restrict__ rz, RingIdx ri,
+                            double* __restrict__ part) {
+  __shared__ double s_w[4][8];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < n) {
+    v[0] = cc[j] * cc[j];
+    v[1] = cn[j] * cn[j];
+    for (int k = 0; k < 8; ++k) {
+      const double a = rx[(size_t)ri.slot[k] * n + j], b = rz[(size_t)ri.slot[k] * n + j];
+      v[2] += a * a;
+      v[3] += b * b;
+    }
+  }
+  for (int q = 0; q < 4; ++q)
+    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) s_w[q][threadIdx.x >> 5] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[threadIdx.x][w];
+    part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// 1 / RMS of each group (1 when the group is all zero)
+__global__ void k_feat_fold(const double* __restrict__ part, int nb, int n, double* __restrict__ inv) {
+  __shared__ double s_tmp[32];
+  for (int q = 0; q < 4; ++q) {
+    const double v = block_fold(part + (size_t)q * nb, nb, false, s_tmp);
+    if (threadIdx.x == 0) {
+      const double cnt = q < 2 ? (double)n : 8.0 * (double)n;
+      const double r = sqrt(v / cnt);
+      inv[q] = r > 0.0 ? 1.0 / r : 1.0;
+    }
+    __syncthreads();
+  }
+}
+
+// feature row of column j (row col_perm[j] when perm is given, else j) and
+// its eligibility: not fixed by the reduced-cost rule, a finite bound
+__global__ void k_feat_write(int n, const double* __restrict__ cc, const double* __restrict__ cn,
+                             const float* __restrict__ rx, const float* __restrict__ rz, RingIdx ri,
+                             const double* __restrict__ inv, const int* __restrict__ perm,
+                             const int8_t* __restrict__ fixed, const double* __restrict__ lhat,
+                             const double* __restrict__ uhat, uint16_t* __restrict__ feat,
+                             uint8_t* __restrict__ elig) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const size_t row = perm ? (size_t)perm[j] : (size_t)j;
+  double f[18];
+  f[0] = cc[j] * inv[0];
+  f[1] = cn[j] * inv[1];
+  for (int k = 0; k < 8; ++k) {
+    f[2 + k] = (double)rx[(size_t)ri.slot[k] * n + j] * inv[2];
+    f[10 + k] = (double)rz[(size_t)ri.slot[k] * n + j] * inv[3];
+  }
+  uint32_t* dst = reinterpret_cast<uint32_t*>(feat + row * 32);
+#pragma unroll
+  for (int w = 0; w < 16; ++w) {
+    const uint32_t lo = 2 * w < 18 ? __bfloat16_as_ushort(__double2bfloat16(f[2 * w])) : 0u;
+    const uint32_t hi = 2 * w + 1 < 18 ? __bfloat16_as_ushort(__double2bfloat16(f[2 * w + 1])) : 0u;
+    dst[w] = lo | (hi << 16);
+  }
+  if (elig) elig[row] = (!fixed[j] && (lhat[j] != -INFINITY || uhat[j] != INFINITY)) ? 1 : 0;
+}
+
+int build_features(pdhgc_lp* lp, const pdhgc_corner_params& cp, bool user_order, uint16_t* feat, uint8_t* elig) {
+  cudaStream_t st = lp->stream;
+  const int n = lp->n, nb = grid_for(n);
+  RET(corner_build(lp, cp, lp->gfixed));
+  k_col_norm<<<grid_for((long long)n * 32), 256, 0, st>>>(n, lp->T.rp, lp->T.hat, lp->gnorm);
+  const RingIdx ri = ring_index(lp->rep1.restarts);
+  double* inv = lp->gpart + (size_t)4 * nb;
+  k_feat_sums<<<nb, 256, 0, st>>>(n, lp->chat_c, lp->gnorm, lp->ring_x, lp->ring_z, ri, lp->gpart);
+  k_feat_fold<<<1, 256, 0, st>>>(lp->gpart, nb, n, inv);
+  k_feat_write<<<nb, 256, 0, st>>>(n, lp->chat_c, lp->gnorm, lp->ring_x, lp->ring_z, ri, inv,
+                                   user_order ? lp->col_perm : nullptr, lp->gfixed, lp->lhat, lp->uhat, feat, elig);
+  lp->launches += 4;
+  CKL();
+  return PDHGC_OK;
+}
+
+__global__ void k_hold_from_p(int n, const float* __restrict__ p, double thr, uint8_t* __restrict__ hold) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) hold[j] = (double)p[j] >= thr ? 1 : 0;
+}
+
+__global__ void k_gather_u8(int n, const int* __restrict__ perm, const uint8_t* __restrict__ src,
+                            uint8_t* __restrict__ dst) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) dst[j] = src[perm[j]] != 0 ? 1 : 0;
+}
+
+// held columns: l_hat' = u_hat' = the bound nearest to x1 (ties: lower), the
+// start point there; count[0] eligible columns, count[1] held columns
+__global__ void k_apply_hold(int n, const uint8_t* __restrict__ hold, const int8_t* __restrict__ fixed,
+                             const double* __restrict__ x1, const double* __restrict__ lhat,
+                             const double* __restrict__ uhat, double* __restrict__ lc, double* __restrict__ uc,
+                             double* __restrict__ xs, long long* __restrict__ count) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = x1[j], l = lhat[j], u = uhat[j];
+  const bool lf = l != -INFINITY, uf = u != INFINITY;
+  double xj = x;
+  if (!fixed[j] && (lf || uf)) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&count[0]), 1ull);
+    if (hold[j]) {
+      const double dl = lf ? x - l : INFINITY, du = uf ? u - x : INFINITY;
+      const double b = dl <= du ? l : u;
+      lc[j] = b;
+      uc[j] = b;
+      xj = b;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&count[1]), 1ull);
+    }
+  }
+  xs[j] = xj;
+}
+
+// training label of column j (user row): the corner x_j within 1e-6 of a bound
+__global__ void k_labels(int n, const double* __restrict__ xc, const double* __restrict__ Dc,
+                         const double* __restrict__ l, const double* __restrict__ u, const int* __restrict__ perm,
+                         uint8_t* __restrict__ lab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = Dc[j] * xc[j];
+  lab[perm[j]] = fmin(x - l[j], u[j] - x) > 1e-6 ? 0 : 1;
+}
+
+// deterministic stream compaction of the flagged rows (256-row blocks)
+__global__ void k_count_flags(int n, const uint8_t* __restrict__ flag, int* __restrict__ blk) {
+  __shared__ int s_w[8];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned b = __ballot_sync(0xffffffffu, j < n && flag[j] != 0);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+    blk[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan_blocks(int nb, int* __restrict__ blk, long long* __restrict__ total) {
+  long long run = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int c = blk[b];
+    blk[b] = (int)run;
+    run += c;
+  }
+  total[0] = run;
+}
+
+__global__ void k_compact(int n, const uint8_t* __restrict__ flag, const int* __restrict__ blk_off,
+                          const uint16_t* __restrict__ feat_in, const uint8_t* __restrict__ lab_in,
+                          uint16_t* __restrict__ feat_out, uint8_t* __restrict__ lab_out) {
+  __shared__ int s_w[8];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool f = j < n && flag[j] != 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_w[warp] = __popc(b);
+  __syncthreads();
+  int off = blk_off[blockIdx.x];
+  for (int w = 0; w < warp; ++w) off += s_w[w];
+  off += __popc(b & ((1u << lane) - 1u));
+  if (f) {
+    const uint4* src = reinterpret_cast<const uint4*>(feat_in + (size_t)j * 32);
+    uint4* dst = reinterpret_cast<uint4*>(feat_out + (size_t)off * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = src[q];
+    lab_out[off] = lab_in[j];
+  }
 }
 
 }  // namespace
@@ -980,6 +1313,10 @@ int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int
   RET(lp->alloc(&lp->y1, m));
   RET(lp->alloc(&lp->xc, n));
   RET(lp->alloc(&lp->chat_c, n));
+  RET(lp->alloc(&lp->ring_x, (size_t)8 * n));
+  RET(lp->alloc(&lp->ring_z, (size_t)8 * n));
+  RET(lp->alloc(&lp->z_cur, n));
+  RET(lp->alloc(&lp->z_avg, n));
   RET(lp->alloc(&lp->lhat_c, n));
   RET(lp->alloc(&lp->uhat_c, n));
   RET(lp->alloc(&lp->pi_v, n));
@@ -1051,51 +1388,136 @@ int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_re
   if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
   pdhgc_corner_params cp;
   if (params) cp = *params; else pdhgc_default_corner_params(&cp);
-  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
-      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
-    return set_err(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  RET(check_corner_params(cp));
   lp->have_corner = false;
-  cudaStream_t st = lp->stream;
-  const DevModel md = model_orig(lp);
-  // Algorithm 1: new bounds and objective (columns), new senses (rows)
-  RET(launch_tiles(lp, true, true,
-                   CornerColsOp{lp->y1, lp->x1, lp->col_perm, md, lp->lhat_c, lp->uhat_c, lp->chat_c, cp.eps_abs,
-                                cp.obj_scale, (unsigned long long)cp.obj_seed},
-                   lp->pT, st));
-  k_corner_rows<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->ge, lp->Dr, lp->y1, cp.eps_abs, lp->ge_c);
-  lp->launches++;
-  CKL();
-  k_fold2<<<1, 256, 0, st>>>(lp->pT, lp->ntT, lp->scratch + 8);
-  lp->launches++;
-  CKL();
-  const pdhgc_params& p = lp->params;
-  PhaseInit pi{};
-  pi.eps_rel = cp.eps_rel;
-  pi.beta_suff = p.beta_suff;
-  pi.beta_nec = p.beta_nec;
-  pi.beta_art = p.beta_art;
-  pi.theta = p.theta;
-  pi.time_limit_s = cp.time_limit_s;
-  pi.nb = lp->b_norm;
-  pi.nc = 0.0;
-  pi.max_iters = cp.max_iters;
-  pi.min_iters = cp.min_iters;
-  pi.check_period = p.check_period;
-  pi.phase = 1;
-  pi.stop_rule = cp.stop_rule;
-  pi.use_cc2 = 1;
-  if (p.precision == PDHGC_FP32_BULK) {
-    RET(to32(lp, lp->chat_c, lp->chat_c32, lp->n, st));
-    RET(to32(lp, lp->lhat_c, lp->lhat_c32, lp->n, st));
-    RET(to32(lp, lp->uhat_c, lp->uhat_c32, lp->n, st));
-  }
-  RET(run_phase(lp, model_corner(lp), model32_corner(lp), pi, lp->x1, lp->scratch + 8, lp->xc, nullptr, lp->x1));
+  RET(corner_build(lp, cp, nullptr));
   pdhgc_report r{};
-  RET(fill_phase_report(lp, &r));
-  RET(run_report(lp, lp->xc, lp->y1, &r));
+  RET(corner_run(lp, cp, lp->x1, &r));
   lp->repc = r;
   lp->have_corner = true;
+  lp->cp_last = cp;
   if (out) *out = r;
+  return PDHGC_OK;
+}
+
+void pdhgc_default_guide_params(pdhgc_guide_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->threshold = 0.9;
+  p->fallback = 1;
+}
+
+int pdhgc_guide_features(pdhgc_lp* lp, const pdhgc_corner_params* params, uint16_t* feat, uint8_t* eligible) {
+  if (!lp || !feat) return set_err(PDHGC_ERR_INVALID_ARG, "lp or feat is NULL");
+  if (((uintptr_t)feat & 15u) != 0u) return set_err(PDHGC_ERR_INVALID_ARG, "feat must be 16-byte aligned");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
+  pdhgc_corner_params cp;
+  if (params) cp = *params; else pdhgc_default_corner_params(&cp);
+  RET(check_corner_params(cp));
+  RET(ensure_gbufs(lp));
+  RET(build_features(lp, cp, true, feat, eligible));
+  CK(cudaStreamSynchronize(lp->stream));
+  return PDHGC_OK;
+}
+
+int pdhgc_guide_dataset_append(pdhgc_lp* lp, uint16_t* feat, uint8_t* labels, int64_t capacity, int64_t* count) {
+  if (!lp || !feat || !labels || !count) return set_err(PDHGC_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)feat & 15u) != 0u) return set_err(PDHGC_ERR_INVALID_ARG, "feat must be 16-byte aligned");
+  if (*count < 0 || *count > capacity) return set_err(PDHGC_ERR_INVALID_ARG, "count outside [0, capacity]");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
+  if (!lp->have_corner) return set_err(PDHGC_ERR_NO_CORNER, "no corner result on this handle");
+  RET(ensure_gbufs(lp));
+  cudaStream_t st = lp->stream;
+  const int n = lp->n, nb = grid_for(n);
+  RET(build_features(lp, lp->cp_last, true, lp->gfeat, lp->gelig));
+  k_labels<<<nb, 256, 0, st>>>(n, lp->xc, lp->Dc, lp->l, lp->u, lp->col_perm, lp->glabel);
+  k_count_flags<<<nb, 256, 0, st>>>(n, lp->gelig, lp->gblk);
+  k_scan_blocks<<<1, 1, 0, st>>>(nb, lp->gblk, lp->gcount);
+  lp->launches += 3;
+  CKL();
+  long long total = 0;
+  CK(cudaMemcpyAsync(&total, lp->gcount, sizeof(total), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (total > capacity - *count)
+    return set_err(PDHGC_ERR_BUFFER, "dataset capacity too small: need " + std::to_string(*count + total) + " rows");
+  k_compact<<<nb, 256, 0, st>>>(n, lp->gelig, lp->gblk, lp->gfeat, lp->glabel, feat + (size_t)(*count) * 32,
+                                labels + *count);
+  lp->launches++;
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  *count += total;
+  return PDHGC_OK;
+}
+
+int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, const pdhgc_guide_params* gparams,
+                              pdhgc_guide* g, const uint8_t* hold, int hold_on_device, pdhgc_report* out,
+                              pdhgc_guide_report* gout) {
+  if (!lp) return set_err(PDHGC_ERR_INVALID_ARG, "lp is NULL");
+  if ((g == nullptr) == (hold == nullptr))
+    return set_err(PDHGC_ERR_INVALID_ARG, "give exactly one of the network and the hold mask");
+  if (hold && hold_on_device != 0 && hold_on_device != 1)
+    return set_err(PDHGC_ERR_INVALID_ARG, "hold_on_device must be 0 or 1");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
+  pdhgc_corner_params cp;
+  if (params) cp = *params; else pdhgc_default_corner_params(&cp);
+  RET(check_corner_params(cp));
+  pdhgc_guide_params gp;
+  if (gparams) gp = *gparams; else pdhgc_default_guide_params(&gp);
+  if (!std::isfinite(gp.threshold) || (gp.fallback != 0 && gp.fallback != 1))
+    return set_err(PDHGC_ERR_INVALID_ARG, "guide parameter out of range");
+  RET(ensure_gbufs(lp));
+  lp->have_corner = false;
+  cudaStream_t st = lp->stream;
+  const int n = lp->n, nb = grid_for(n);
+  const auto t0 = std::chrono::steady_clock::now();
+  RET(corner_build(lp, cp, lp->gfixed));
+  if (g) {
+    RET(build_features(lp, cp, false, lp->gfeat, nullptr));
+    RET(guide_forward(g, reinterpret_cast<const __nv_bfloat16*>(lp->gfeat), n, lp->gprob, st));
+    k_hold_from_p<<<nb, 256, 0, st>>>(n, lp->gprob, gp.threshold, lp->ghold);
+  } else {
+    const uint8_t* src = hold;
+    if (!hold_on_device) {
+      CK(cudaMemcpyAsync(lp->gstage, hold, (size_t)n, cudaMemcpyHostToDevice, st));
+      src = lp->gstage;
+    }
+    k_gather_u8<<<nb, 256, 0, st>>>(n, lp->col_perm, src, lp->ghold);
+  }
+  CK(cudaMemsetAsync(lp->gcount, 0, 2 * sizeof(long long), st));
+  k_apply_hold<<<nb, 256, 0, st>>>(n, lp->ghold, lp->gfixed, lp->x1, lp->lhat, lp->uhat, lp->lhat_c, lp->uhat_c,
+                                   lp->gxs, lp->gcount);
+  lp->launches += 2;
+  CKL();
+  long long counts[2] = {0, 0};
+  CK(cudaMemcpyAsync(counts, lp->gcount, sizeof(counts), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const auto t1 = std::chrono::steady_clock::now();
+  pdhgc_report r{};
+  RET(corner_run(lp, cp, lp->gxs, &r));
+  const auto t2 = std::chrono::steady_clock::now();
+  pdhgc_guide_report gr{};
+  gr.status = r.status;
+  gr.eligible = counts[0];
+  gr.held = counts[1];
+  gr.guided_iters = r.iters;
+  gr.guided_seconds = std::chrono::duration<double>(t2 - t0).count();
+  gr.infer_seconds = std::chrono::duration<double>(t1 - t0).count();
+  gr.guided_rel_kkt = r.rel_kkt;
+  gr.guided_corner_measure = r.corner_measure;
+  const bool regressed = r.status == PDHGC_STATUS_CORNER_LIMIT ||
+                         r.rel_kkt > std::fmax(lp->rep1.rel_kkt, cp.eps_rel) ||
+                         r.corner_measure > lp->rep1.corner_measure;
+  if (gp.fallback && regressed) {
+    RET(corner_build(lp, cp, nullptr));
+    RET(corner_run(lp, cp, lp->x1, &r));
+    gr.fell_back = 1;
+    gr.status = PDHGC_STATUS_GUIDE_FALLBACK;
+  }
+  lp->repc = r;
+  lp->have_corner = true;
+  lp->cp_last = cp;
+  if (out) *out = r;
+  if (gout) *gout = gr;
   return PDHGC_OK;
 }
 

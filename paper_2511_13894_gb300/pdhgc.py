@@ -32,7 +32,8 @@ OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "INVALID_CSR", -3: "NONFINITE", -4: "BOUNDS", -5: "CUDA", -6: "OOM",
              -7: "NO_PHASE1", -8: "NO_CORNER", -9: "TOO_LARGE", -10: "DEVICE", -11: "BUFFER"}
 STATUS_NAMES = {0: "NONE", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "TIME_LIMIT", 4: "NUMERICAL",
-                5: "CORNER_DONE", 6: "CORNER_LIMIT"}
+                5: "CORNER_DONE", 6: "CORNER_LIMIT", 7: "GUIDE_FALLBACK"}
+GUIDE_FEATURES, GUIDE_FEAT_STRIDE, GUIDE_PARAMS = 18, 32, 5441
 FP64, FP32_BULK = 0, 1
 PHASE1, CORNER = 0, 1
 
@@ -75,6 +76,21 @@ class Report(C.Structure):
         return d
 
 
+class GuideParams(C.Structure):
+    _fields_ = [("threshold", C.c_double), ("fallback", C.c_int32), ("reserved", C.c_int32)]
+
+
+class GuideReport(C.Structure):
+    _fields_ = [("status", C.c_int32), ("fell_back", C.c_int32), ("eligible", C.c_int64), ("held", C.c_int64),
+                ("guided_iters", C.c_int64), ("guided_seconds", C.c_double), ("guided_rel_kkt", C.c_double),
+                ("guided_corner_measure", C.c_int64), ("infer_seconds", C.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
 _vp = C.c_void_p
 _sig = {
     "pdhgc_default_params": (None, [C.POINTER(Params)]),
@@ -103,6 +119,19 @@ _sig = {
     "pdhgc_batch_destroy": (None, [_vp]),
     "pdhgc_batch_set_layout": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_batch_tune": (C.c_int, [_vp, C.POINTER(Params), C.c_int32, _vp, _vp]),
+    "pdhgc_default_guide_params": (None, [C.POINTER(GuideParams)]),
+    "pdhgc_guide_create": (C.c_int, [C.POINTER(_vp), C.c_uint64, _vp]),
+    "pdhgc_guide_destroy": (None, [_vp]),
+    "pdhgc_guide_set_weights": (C.c_int, [_vp, _vp]),
+    "pdhgc_guide_get_weights": (C.c_int, [_vp, _vp]),
+    "pdhgc_guide_infer": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
+    "pdhgc_guide_grad": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp, _vp]),
+    "pdhgc_guide_train": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int64, C.c_float, C.c_uint64, _vp]),
+    "pdhgc_guide_features": (C.c_int, [_vp, C.POINTER(CornerParams), _vp, _vp]),
+    "pdhgc_guide_dataset_append": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64)]),
+    "pdhgc_corner_phase_guided": (C.c_int, [_vp, C.POINTER(CornerParams), C.POINTER(GuideParams), _vp, _vp,
+                                            C.c_int, C.POINTER(Report), C.POINTER(GuideReport)]),
+    "pdhgc_guide_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_strerror": (C.c_char_p, [C.c_int]),
     "pdhgc_last_error_detail": (C.c_char_p, []),
 }
@@ -226,6 +255,52 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    # -- learned corner guidance ------------------------------------------------
+    def guide_features(self, params: CornerParams | None = None, **kw):
+        """pdhgc_guide_features: (feat, eligible) as CUDA tensors: feat n x 32
+        bfloat16 (18 features then zeros), eligible n uint8; user column order."""
+        torch = _torch()
+        p = params if params is not None else default_corner_params(**kw)
+        feat = torch.zeros((self.n, GUIDE_FEAT_STRIDE), dtype=torch.bfloat16, device="cuda")
+        elig = torch.zeros(self.n, dtype=torch.uint8, device="cuda")
+        _check(lib.pdhgc_guide_features(self._h, C.byref(p), feat.data_ptr(), elig.data_ptr()),
+               "pdhgc_guide_features")
+        return feat, elig
+
+    def dataset_append(self, feat, labels, count: int) -> int:
+        """pdhgc_guide_dataset_append into CUDA tensors (feat rows x 32
+        bfloat16, labels uint8) at row `count`; returns the new count."""
+        c = C.c_int64(int(count))
+        _check(lib.pdhgc_guide_dataset_append(self._h, feat.data_ptr(), labels.data_ptr(), int(feat.shape[0]),
+                                              C.byref(c)), "pdhgc_guide_dataset_append")
+        return int(c.value)
+
+    def corner_phase_guided(self, guide=None, hold=None, threshold: float = 0.9, fallback: bool = True,
+                            params: CornerParams | None = None, **kw):
+        """pdhgc_corner_phase_guided with a Guide network or a hold mask
+        (numpy bool/uint8 per user column, or a CUDA uint8 tensor).
+        Returns (report, guide_report)."""
+        p = params if params is not None else default_corner_params(**kw)
+        gp = GuideParams()
+        lib.pdhgc_default_guide_params(C.byref(gp))
+        gp.threshold = float(threshold)
+        gp.fallback = int(bool(fallback))
+        r, gr = Report(), GuideReport()
+        keep = None
+        hold_ptr, on_dev = None, 0
+        if hold is not None:
+            if _is_cuda_tensor(hold):
+                hold_ptr, on_dev = hold.data_ptr(), 1
+            else:
+                keep = np.ascontiguousarray(np.asarray(hold).astype(np.uint8))
+                if keep.shape[0] != self.n:
+                    raise ValueError("hold mask must have one entry per column")
+                hold_ptr = keep.ctypes.data
+        _check(lib.pdhgc_corner_phase_guided(self._h, C.byref(p), C.byref(gp), guide._h if guide else None,
+                                             hold_ptr, on_dev, C.byref(r), C.byref(gr)),
+               "pdhgc_corner_phase_guided")
+        return r.as_dict(), gr.as_dict()
 
     def profile_iteration(self, iters: int = 20):
         """Mean ms per launch of the primal (A' pass) and dual (A pass)
@@ -369,6 +444,75 @@ class Batch:
                "pdhgc_batch_tune")
         return dict(threads=int(chosen[0]), sell=int(chosen[1]), lanes_a=int(chosen[2]), lanes_t=int(chosen[3]),
                     timings_ms=ms.tolist())
+
+
+class Guide:
+    """The corner-guidance network (pdhgc_guide_*).  Feature and label arrays
+    are CUDA tensors (rows x 32 bfloat16; uint8)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        h = _vp()
+        _check(lib.pdhgc_guide_create(C.byref(h), C.c_uint64(seed), stream), "pdhgc_guide_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.pdhgc_guide_destroy(h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
+        if w.shape[0] != GUIDE_PARAMS:
+            raise ValueError(f"expected {GUIDE_PARAMS} parameters")
+        _check(lib.pdhgc_guide_set_weights(self._h, w.ctypes.data), "pdhgc_guide_set_weights")
+
+    def get_weights(self) -> np.ndarray:
+        w = np.empty(GUIDE_PARAMS, dtype=np.float32)
+        _check(lib.pdhgc_guide_get_weights(self._h, w.ctypes.data), "pdhgc_guide_get_weights")
+        return w
+
+    def save(self, path):
+        np.save(path, self.get_weights())
+
+    def load(self, path):
+        self.set_weights(np.load(path))
+
+    def infer(self, feat):
+        torch = _torch()
+        p = torch.empty(int(feat.shape[0]), dtype=torch.float32, device="cuda")
+        _check(lib.pdhgc_guide_infer(self._h, feat.data_ptr(), int(feat.shape[0]), p.data_ptr()),
+               "pdhgc_guide_infer")
+        return p
+
+    def grad(self, feat, labels, idx):
+        """Gradient of the mean BCE over the rows idx (no update): (grad, loss)."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+        g = np.empty(GUIDE_PARAMS, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(lib.pdhgc_guide_grad(self._h, feat.data_ptr(), labels.data_ptr(), int(feat.shape[0]),
+                                    idx.ctypes.data, int(idx.shape[0]), g.ctypes.data, C.byref(loss)),
+               "pdhgc_guide_grad")
+        return g, float(loss.value)
+
+    def train(self, feat, labels, rows: int, batch: int = 4096, steps: int = 1000, lr: float = 1e-3,
+              seed: int = 0) -> np.ndarray:
+        """`steps` Adam steps on minibatches drawn from the first `rows` rows;
+        returns the per-step minibatch losses."""
+        losses = np.zeros(int(steps), dtype=np.float32)
+        _check(lib.pdhgc_guide_train(self._h, feat.data_ptr(), labels.data_ptr(), int(rows), int(batch),
+                                     int(steps), float(lr), C.c_uint64(seed), losses.ctypes.data if steps else None),
+               "pdhgc_guide_train")
+        return losses
+
+    def kernel_launches(self) -> int:
+        return int(lib.pdhgc_guide_kernel_launches(self._h))
 
 
 def _device_lp_args(lp: dict, x, y):
