@@ -45,6 +45,8 @@ WORKLOADS = {
     "power_law_m100k_n400k": lambda: lpgen.large_power_law_lp(0),
     "transportation_1000x2000": lambda: lpgen.large_transportation_lp(0),
     "random_face_m200_n500": lambda: lpgen.small_face_lp(0),
+    # 512 uneven LPs solved together (run_batch_workload)
+    "batch_512": None,
 }
 
 
@@ -65,6 +67,9 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=50)
     ap.add_argument("--cpu-iters", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-sample", type=int, default=16,
+                    help="batch_512: LPs solved one by one with the single-LP FP64 path for the "
+                         "sequential reference time (every count/sample-th LP by size)")
     ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
                     help="kernels: short solve, then --profile-iters replays of the two iteration "
                          "kernels as plain launches inside the NVTX range 'pdhg_kernels' (for ncu)")
@@ -197,7 +202,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    lp = WORKLOADS[args.workload]()
+    if args.workload == "batch_512":
+        lp = sorted(lpgen.batch_lps(512), key=lambda d: d["n"])[256]  # the median-size LP of the batch
+    else:
+        lp = WORKLOADS[args.workload]()
     model, p, sigma_max, eta = oracle.setup(lp)
     iters = args.cpu_iters
 
@@ -258,6 +266,153 @@ def cpu_baseline_sample(lp, iters):
                       f"numpy/scipy, single-threaded"}
 
 
+def batch_bytes_per_iter(lp, s_v=4, s_x=4, s_sum=8):
+    m, n, nnz = int(lp["m"]), int(lp["n"]), int(lp["row_ptr"][-1])
+    p, d = algorithmic_bytes(m, n, nnz, s_v, s_x, s_sum)
+    return p + d
+
+
+def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
+    """512 uneven LPs (random-face construction, m ~ U{50..5000}) in one
+    persistent, graph-captured launch per phase with the autotuned schedule,
+    FP32 bulk.  One step = phase 1 of every LP to rel-KKT 1e-6 plus Algorithm
+    1 on every LP.  Ranks split the LPs round-robin (strong scaling: the batch
+    is fixed).  The single-LP FP64 path on a size-stratified sample of the LPs,
+    one after another, gives the sequential reference time."""
+    all_lps = lpgen.batch_lps(512)
+    lps = all_lps[rank::world]
+    stream = torch.cuda.current_stream()
+    B = P.Batch(lps, stream=stream.cuda_stream)
+    params = P.default_params(precision=P.FP32_BULK, max_iters=args.phase1_max_iters)
+    tuned = B.tune(256, params)  # schedule autotuner (untimed setup)
+    cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        r1 = B.solve(params)
+        rc = B.corner_phase(cparams)
+        return r1, rc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    l0 = B.kernel_launches()
+    step_ms, iters, last = [], [], None
+    byte_iters = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r1, rc = step()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(sum(a["iters"] + b["iters"] for a, b in zip(r1, rc)))
+        byte_iters += sum((a["iters"] + b["iters"]) * batch_bytes_per_iter(lp) for a, b, lp in zip(r1, rc, lps))
+        last = (r1, rc)
+    clk = clocks.stop()
+    launches = B.kernel_launches() - l0
+    total_ms = sum(step_ms)
+    total_iters = float(sum(iters))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        total_iters = float(it.item())
+    value = total_iters / (total_ms * 1e-3)
+    r1, rc = last
+    peak, peak_kind = measured_peaks()
+    achieved = byte_iters / (sum(step_ms) * 1e-3) / 1e9
+    # sequential reference: the single-LP FP64 path, LP after LP, on a sample
+    seq = None
+    if rank == 0 and args.batch_sample > 0:
+        order = sorted(range(len(all_lps)), key=lambda k: all_lps[k]["n"] + all_lps[k]["m"])
+        stride = max(1, len(order) // args.batch_sample)
+        sample = [order[k] for k in range(stride // 2, len(order), stride)][:args.batch_sample]
+        t_s = 0.0
+        for k in sample:
+            g = P.lp_from_dict(all_lps[k], stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.solve(max_iters=args.phase1_max_iters)
+            g.corner_phase(cparams)
+            torch.cuda.synchronize()
+            t_s += time.perf_counter() - t0
+            g.close()
+        est = t_s * len(all_lps) / len(sample)
+        seq = {"sample_lps": len(sample), "sample_seconds": t_s, "estimated_seconds_all": est,
+               "speedup_batched_vs_sequential_fp64": est / (total_ms / args.steps * 1e-3),
+               "note": "single-LP FP64 path (graph-driven loop, one LP at a time), size-stratified "
+                       "sample scaled to all LPs"}
+    # end to end: batch created from host arrays, both phases, every x and y back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Be = P.Batch(lps, stream=stream.cuda_stream)
+    Be.set_block(tuned["threads"])
+    Be.set_layout(tuned["sell"])
+    Be.set_lanes(tuned["lanes_a"], tuned["lanes_t"])
+    a1 = Be.solve(params)
+    a2 = Be.corner_phase(cparams)
+    d2h = 0
+    for k in range(len(lps)):
+        x, y = Be.get_solution(k, P.CORNER)
+        d2h += x.nbytes + y.nbytes
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - t0) * 1e3
+    h2d = sum(sum(np.asarray(lp[key]).nbytes for key in ("row_ptr", "col_idx", "val", "b", "c", "lb", "ub", "sense")
+                  if lp.get(key) is not None) for lp in lps)
+    e_it = float(sum(a["iters"] + b["iters"] for a, b in zip(a1, a2)))
+    Be.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mid = sorted(all_lps, key=lambda lp: lp["n"])[len(all_lps) // 2]
+        cpu = cpu_baseline_sample(mid, args.cpu_iters * 8)
+        cpu["sample"] = "median-size LP of the batch (m=%d, n=%d): " % (mid["m"], mid["n"]) + cpu["sample"]
+    if rank == 0:
+        done = sum(r["status_name"] == "OPTIMAL" for r in r1)
+        cdone = sum(r["status_name"] == "CORNER_DONE" for r in rc)
+        out = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32+f32x2acc", "data": "synthetic",
+            "config": {"workload": "batch_512", "lps": len(all_lps), "lps_per_rank": len(lps),
+                       "sum_m": sum(lp["m"] for lp in all_lps), "sum_n": sum(lp["n"] for lp in all_lps),
+                       "sum_nnz": sum(int(lp["row_ptr"][-1]) for lp in all_lps), "precision": "fp32_bulk",
+                       "schedule": tuned, "corner_max_iters": args.corner_max_iters, "eps_rel": 1e-6,
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"lp-split x{world}"},
+            "time_to_corner_s": total_ms / args.steps * 1e-3,
+            "phase1": {"optimal": done, "lps": len(r1), "iters_sum": sum(r["iters"] for r in r1),
+                       "iters_max": max(r["iters"] for r in r1),
+                       "corner_measure_sum": sum(r["corner_measure"] for r in r1)},
+            "corner": {"done": cdone, "lps": len(rc), "iters_sum": sum(r["iters"] for r in rc),
+                       "corner_measure_sum": sum(r["corner_measure"] for r in rc)},
+            "sequential_fp64": seq,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_batch (whole step)",
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "note": "algorithmic bytes of every LP's iterations (FP32 bulk) over the step time"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_it * world / (e_ms * 1e-3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e_ms},
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -276,6 +431,23 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    if args.workload == "batch_512" and args.mode == "kernels":
+        # --profile-iters iterations of every LP in one batched launch (FP32 bulk), for ncu
+        B = P.Batch(lpgen.batch_lps(512), stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("batch_kernel")
+        B.solve(max_iters=args.profile_iters, eps_rel=-1.0, precision=P.FP32_BULK)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"mode": "kernels", "workload": "batch_512", "iters": args.profile_iters}))
+        return
+    if args.workload == "batch_512":
+        run_batch_workload(args, rank, world, local, torch, P, dist, barrier)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     lp_dict = WORKLOADS[args.workload]()
     m, n, nnz = lp_dict["m"], lp_dict["n"], int(lp_dict["row_ptr"][-1])

@@ -292,7 +292,9 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
 
 /*
  * pdhgc_batch_solve — phase 1 (as pdhgc_solve, same parameters) for every
- * LP of the batch in one persistent kernel launch: each CTA takes LPs from
+ * LP of the batch in one persistent kernel launch, captured with the reset of
+ * its work queue in a CUDA graph that is launched on the batch's stream (one
+ * graph launch per call): each CTA takes LPs from
  * a work queue, largest first, and runs the whole method on one LP (scaling,
  * power iteration, the restarted PDHG loop with its per-LP step size, primal
  * weight, restarts and termination, then the report); an LP's x_bar and y
@@ -329,6 +331,9 @@ int pdhgc_batch_set_layout(pdhgc_batch* batch, int32_t sell);
  */
 int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tune_iters, int32_t* chosen,
                      double* timings_ms);
+
+/* pdhgc_batch_kernel_launches — persistent batched kernels launched so far (one per graph launch). */
+int64_t pdhgc_batch_kernel_launches(const pdhgc_batch* batch);
 
 void pdhgc_batch_destroy(pdhgc_batch* batch);
 
@@ -369,8 +374,9 @@ void pdhgc_batch_destroy(pdhgc_batch* batch);
 typedef struct pdhgc_guide pdhgc_guide;
 
 typedef struct {
-    double threshold;   /* hold an eligible column when its probability >= threshold (0.9) */
-    int32_t fallback;   /* 1 (default): run the plain corner phase when the guided one regresses */
+    double threshold;          /* hold an eligible column when its probability >= threshold (0.9) */
+    int64_t guided_max_iters;  /* iteration limit of the guided run; 0 (default) = the corner limit */
+    int32_t fallback;          /* 1 (default): run the plain corner phase when the guided one regresses */
     int32_t reserved;
 } pdhgc_guide_params;
 
@@ -385,7 +391,7 @@ typedef struct {
     double infer_seconds;           /* features + network inference */
 } pdhgc_guide_report;
 
-/* pdhgc_default_guide_params — threshold 0.9, fallback 1. */
+/* pdhgc_default_guide_params — threshold 0.9, guided_max_iters 0, fallback 1. */
 void pdhgc_default_guide_params(pdhgc_guide_params* p);
 
 /*
@@ -442,8 +448,9 @@ int pdhgc_guide_features(pdhgc_lp* lp, const pdhgc_corner_params* params, uint16
  * pdhgc_guide_dataset_append — training rows from the last corner phase:
  * for every eligible column (in user column order) its feature row (for the
  * corner objective that phase used) and its label (1 when the returned
- * corner x_j lies within 1e-6 of l_j or u_j in user space; on a
- * CORNER_LIMIT status that point is the phase-1 x).  Rows are appended to the
+ * corner x_j lies within 1e-6, in user space, of the bound a hold would use:
+ * the one nearest to its phase-1 value; on a CORNER_LIMIT status the corner
+ * point is the phase-1 x).  Rows are appended to the
  * DEVICE arrays feat / labels at row *count, which is advanced.  Errors:
  * NO_PHASE1, NO_CORNER, BUFFER (capacity - *count too small; *count is left
  * unchanged and nothing is written), INVALID_ARG, CUDA, OOM.

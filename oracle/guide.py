@@ -8,7 +8,7 @@ states, in plain numpy, what the CUDA path computes around the network:
 * which columns may be held (`eligible`): not fixed by Algorithm 1's
   reduced-cost rule and with a finite bound;
 * the training labels of a corner result (`labels`): x_j within the metric
-  tolerance of a bound (the complement of the Section 2.1 "off bound" test);
+  tolerance (Section 4.2) of the bound a hold would fix it at;
 * the guided corner phase with its fallback (`guided_corner_phase`).
 
 The network itself is `oracle/mlp.py`.  Only `tests/`, the smoke check and
@@ -24,7 +24,11 @@ Readings (the paper has no such component):
   restart, newest first, the last 8 kept, padded by repeating the oldest;
   z_hat = proj_Lambda(c_hat - A_hat' y_hat) at the same point;
 * each of the four groups (c, ||A_j||, the 8 x values, the 8 z values) is
-  divided by its root mean square over all columns (1 when that is 0).
+  divided by its root mean square over all columns (1 when that is 0);
+* the label is "the corner phase ends with x_j at the bound nearest to its
+  phase-1 value", the bound a hold uses: a column that ends at its other
+  bound would be held at the wrong one, which can make the held corner
+  model infeasible.
 """
 from __future__ import annotations
 
@@ -82,10 +86,15 @@ def eligible(phase1, cp):
     return ~info["fixed"] & np.isfinite(nb)
 
 
-def labels(model, x_hat, tol=LABEL_TOL):
-    """1 where the user-space x_j lies within tol of l_j or u_j."""
+def labels(model, x_hat, x_hat1, tol=LABEL_TOL):
+    """1 where the user-space corner x_j lies within tol of the bound that a
+    hold would use: the bound nearest to the phase-1 value x_hat1_j (in
+    scaled space, then unscaled by D_c).  0 for a column without a finite
+    bound."""
+    nb = pdhg.nearest_bound(x_hat1, model.lhat, model.uhat)
     x = model.Dc * x_hat
-    return ~(np.minimum(x - model.l, model.u - x) > tol)
+    b = model.Dc * nb
+    return np.isfinite(b) & (np.abs(x - b) <= tol)
 
 
 def hold_mask(p, elig, threshold):
@@ -108,15 +117,19 @@ def regressed(guided_report, ref_report, status, eps_rel):
             or guided_report["corner_measure"] > ref_report["corner_measure"])
 
 
-def guided_corner_phase(phase1, hold, corner_params=None, fallback=True):
-    """Algorithm 1 with `hold` columns fixed at their nearest bound; when the
-    result regresses against the phase-1 point, the plain corner phase runs
-    and its result is returned (fell_back = True)."""
+def guided_corner_phase(phase1, hold, corner_params=None, fallback=True, guided_max_iters=0):
+    """Algorithm 1 with `hold` columns fixed at their nearest bound (at most
+    guided_max_iters iterations when > 0); when the result regresses against
+    the phase-1 point, the plain corner phase runs and its result is returned
+    (fell_back = True)."""
     cp = dict(pdhg.CORNER_DEFAULTS)
     if corner_params:
         cp.update(corner_params)
     model = phase1["model"]
-    g = pdhg.corner_phase(phase1, cp, hold=hold)
+    cpg = dict(cp)
+    if guided_max_iters > 0:
+        cpg["max_iters"] = min(cp["max_iters"], guided_max_iters)
+    g = pdhg.corner_phase(phase1, cpg, hold=hold)
     g_rep = pdhg.kkt_report(model, g["x_hat"], g["y_hat"])
     p_rep = pdhg.kkt_report(model, phase1["x_hat"], phase1["y_hat"])
     out = dict(guided=g, guided_report=g_rep, fell_back=False, result=g, report=g_rep)

@@ -671,7 +671,10 @@ struct pdhgc_batch {
   int precision = PDHGC_FP32_BULK;
   pdhgc_params params{};
   double tune_ms[4] = {0, 0, 0, 0};
+  cudaGraphExec_t gexec = nullptr;  // the last launched batch graph
+  int64_t launches = 0;             // persistent kernels launched (one per graph)
   ~pdhgc_batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
     for (void* q : allocs) cudaFree(q);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
@@ -741,9 +744,28 @@ int launch_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t 
   if (per_sm < 1) return set_berr(PDHGC_ERR_CUDA, "batched kernel does not fit on an SM");
   int grid = sms * per_sm;
   if (grid > B->count) grid = B->count;
-  BCK(cudaMemsetAsync(B->d_queue, 0, sizeof(int), st));
-  k_batch<VT, BT><<<grid, BT, smem, st>>>(B->d_desc, B->d_order, B->count, B->d_queue, bp, phase, B->d_rep);
-  BCK(cudaGetLastError());
+  // one CUDA graph: the queue reset and the persistent kernel, captured on the
+  // batch's private stream and launched on the caller's stream
+  cudaGraph_t graph = nullptr;
+  BCK(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t me = cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->cap_stream);
+  k_batch<VT, BT><<<grid, BT, smem, B->cap_stream>>>(B->d_desc, B->d_order, B->count, B->d_queue, bp, phase,
+                                                     B->d_rep);
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t ce = cudaStreamEndCapture(B->cap_stream, &graph);
+  if (me != cudaSuccess || le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    const cudaError_t e = me != cudaSuccess ? me : (le != cudaSuccess ? le : ce);
+    return set_berr(PDHGC_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+  }
+  // the previous executable graph is freed once its launch completes
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  B->gexec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&B->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  BCK(ie);
+  BCK(cudaGraphLaunch(B->gexec, st));
+  B->launches++;
   return PDHGC_OK;
 }
 
@@ -1151,6 +1173,8 @@ int pdhgc_batch_tune(pdhgc_batch* B, const pdhgc_params* params, int32_t tune_it
   B->have_corner = 0;
   return PDHGC_OK;
 }
+
+int64_t pdhgc_batch_kernel_launches(const pdhgc_batch* B) { return B ? B->launches : 0; }
 
 void pdhgc_batch_destroy(pdhgc_batch* B) {
   if (!B) return;

@@ -1121,14 +1121,24 @@ __global__ void k_apply_hold(int n, const uint8_t* __restrict__ hold, const int8
   xs[j] = xj;
 }
 
-// training label of column j (user row): the corner x_j within 1e-6 of a bound
-__global__ void k_labels(int n, const double* __restrict__ xc, const double* __restrict__ Dc,
-                         const double* __restrict__ l, const double* __restrict__ u, const int* __restrict__ perm,
-                         uint8_t* __restrict__ lab) {
+// training label of column j (user row): the corner x_j within 1e-6 (user
+// space) of the bound a hold would use, the one of [l_hat, u_hat] nearest to
+// the phase-1 x1_j; explicit roundings keep the products out of an FMA
+__global__ void k_labels(int n, const double* __restrict__ xc, const double* __restrict__ x1,
+                         const double* __restrict__ Dc, const double* __restrict__ lhat,
+                         const double* __restrict__ uhat, const int* __restrict__ perm, uint8_t* __restrict__ lab) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double x = Dc[j] * xc[j];
-  lab[perm[j]] = fmin(x - l[j], u[j] - x) > 1e-6 ? 0 : 1;
+  const double l = lhat[j], u = uhat[j], v = x1[j];
+  const bool lf = l != -INFINITY, uf = u != INFINITY;
+  uint8_t out = 0;
+  if (lf || uf) {
+    const double dl = lf ? v - l : INFINITY, du = uf ? u - v : INFINITY;
+    const double nb = dl <= du ? l : u;
+    const double x = __dmul_rn(Dc[j], xc[j]), b = __dmul_rn(Dc[j], nb);
+    out = fabs(x - b) <= 1e-6 ? 1 : 0;
+  }
+  lab[perm[j]] = out;
 }
 
 // deterministic stream compaction of the flagged rows (256-row blocks)
@@ -1404,6 +1414,7 @@ void pdhgc_default_guide_params(pdhgc_guide_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
   p->threshold = 0.9;
+  p->guided_max_iters = 0;
   p->fallback = 1;
 }
 
@@ -1430,7 +1441,7 @@ int pdhgc_guide_dataset_append(pdhgc_lp* lp, uint16_t* feat, uint8_t* labels, in
   cudaStream_t st = lp->stream;
   const int n = lp->n, nb = grid_for(n);
   RET(build_features(lp, lp->cp_last, true, lp->gfeat, lp->gelig));
-  k_labels<<<nb, 256, 0, st>>>(n, lp->xc, lp->Dc, lp->l, lp->u, lp->col_perm, lp->glabel);
+  k_labels<<<nb, 256, 0, st>>>(n, lp->xc, lp->x1, lp->Dc, lp->lhat, lp->uhat, lp->col_perm, lp->glabel);
   k_count_flags<<<nb, 256, 0, st>>>(n, lp->gelig, lp->gblk);
   k_scan_blocks<<<1, 1, 0, st>>>(nb, lp->gblk, lp->gcount);
   lp->launches += 3;
@@ -1463,8 +1474,10 @@ int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, c
   RET(check_corner_params(cp));
   pdhgc_guide_params gp;
   if (gparams) gp = *gparams; else pdhgc_default_guide_params(&gp);
-  if (!std::isfinite(gp.threshold) || (gp.fallback != 0 && gp.fallback != 1))
+  if (!std::isfinite(gp.threshold) || (gp.fallback != 0 && gp.fallback != 1) || gp.guided_max_iters < 0)
     return set_err(PDHGC_ERR_INVALID_ARG, "guide parameter out of range");
+  pdhgc_corner_params cpg = cp;
+  if (gp.guided_max_iters > 0 && gp.guided_max_iters < cp.max_iters) cpg.max_iters = gp.guided_max_iters;
   RET(ensure_gbufs(lp));
   lp->have_corner = false;
   cudaStream_t st = lp->stream;
@@ -1493,7 +1506,7 @@ int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, c
   CK(cudaStreamSynchronize(st));
   const auto t1 = std::chrono::steady_clock::now();
   pdhgc_report r{};
-  RET(corner_run(lp, cp, lp->gxs, &r));
+  RET(corner_run(lp, cpg, lp->gxs, &r));
   const auto t2 = std::chrono::steady_clock::now();
   pdhgc_guide_report gr{};
   gr.status = r.status;

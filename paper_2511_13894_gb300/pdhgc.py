@@ -77,7 +77,8 @@ class Report(C.Structure):
 
 
 class GuideParams(C.Structure):
-    _fields_ = [("threshold", C.c_double), ("fallback", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("threshold", C.c_double), ("guided_max_iters", C.c_int64), ("fallback", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class GuideReport(C.Structure):
@@ -119,6 +120,7 @@ _sig = {
     "pdhgc_batch_destroy": (None, [_vp]),
     "pdhgc_batch_set_layout": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_batch_tune": (C.c_int, [_vp, C.POINTER(Params), C.c_int32, _vp, _vp]),
+    "pdhgc_batch_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_default_guide_params": (None, [C.POINTER(GuideParams)]),
     "pdhgc_guide_create": (C.c_int, [C.POINTER(_vp), C.c_uint64, _vp]),
     "pdhgc_guide_destroy": (None, [_vp]),
@@ -277,7 +279,7 @@ class LP:
         return int(c.value)
 
     def corner_phase_guided(self, guide=None, hold=None, threshold: float = 0.9, fallback: bool = True,
-                            params: CornerParams | None = None, **kw):
+                            guided_max_iters: int = 0, params: CornerParams | None = None, **kw):
         """pdhgc_corner_phase_guided with a Guide network or a hold mask
         (numpy bool/uint8 per user column, or a CUDA uint8 tensor).
         Returns (report, guide_report)."""
@@ -286,6 +288,7 @@ class LP:
         lib.pdhgc_default_guide_params(C.byref(gp))
         gp.threshold = float(threshold)
         gp.fallback = int(bool(fallback))
+        gp.guided_max_iters = int(guided_max_iters)
         r, gr = Report(), GuideReport()
         keep = None
         hold_ptr, on_dev = None, 0
@@ -425,6 +428,9 @@ class Batch:
         _check(lib.pdhgc_batch_get_solution(self._h, k, which, x.ctypes.data, y.ctypes.data),
                "pdhgc_batch_get_solution")
         return x, y
+
+    def kernel_launches(self) -> int:
+        return int(lib.pdhgc_batch_kernel_launches(self._h))
 
     def set_block(self, threads: int):
         _check(lib.pdhgc_batch_set_block(self._h, threads), "pdhgc_batch_set_block")

@@ -314,7 +314,7 @@ def test_dataset_rows_and_labels():
     assert count == 2 + int(E.sum())
     rows = fbuf[2:count].view(torch.int16).cpu().numpy()
     assert np.array_equal(rows, feat_all.view(torch.int16).cpu().numpy()[E])
-    lab = oguide.labels(r1["model"], rc["x_hat"])
+    lab = oguide.labels(r1["model"], rc["x_hat"], r1["x_hat"])
     assert np.array_equal(lbuf[2:count].cpu().numpy().astype(bool), lab[E])
     assert int(lbuf[count:].cpu().numpy().max()) == 7  # nothing written past the rows
     # too small a buffer: BUFFER, nothing written, count unchanged

@@ -165,11 +165,30 @@ def test_labels_at_the_constructed_optimum():
     lp = lpgen.small_face_lp(7)
     model = oracle.Model(lp)
     x_hat = lp["x_star"] / model.Dc
-    lab = guide.labels(model, x_hat)
-    # off S the constructed x* is 0 (at bound), on S it lies in [0.1, 1]
+    lab = guide.labels(model, x_hat, x_hat)
+    # off S the constructed x* is 0 (at its nearest bound), on S it lies in
+    # [0.1, 1], away from the only finite bound
+    assert np.array_equal(guide.labels(model, x_hat, np.zeros(lp["n"])), lab)
     on_s = lp["x_star"] > 0
     assert np.array_equal(lab, ~on_s)
     assert int(lab.sum()) == lp["n"] - int(on_s.sum())
+
+
+def test_labels_use_the_bound_nearest_to_the_phase1_point():
+    # a column at its upper bound is labelled 1 only when the phase-1 point
+    # was nearer to that bound
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(7), 7)
+    model = oracle.Model(lp)
+    j = int(np.nonzero(np.isfinite(lp["ub"]))[0][0])
+    x = np.zeros(lp["n"])
+    x[j] = lp["ub"][j]
+    x_hat = x / model.Dc
+    near_u = np.zeros(lp["n"])
+    near_u[j] = 0.9 * lp["ub"][j] / model.Dc[j]
+    near_l = np.zeros(lp["n"])
+    near_l[j] = 0.1 * lp["ub"][j] / model.Dc[j]
+    assert guide.labels(model, x_hat, near_u)[j]
+    assert not guide.labels(model, x_hat, near_l)[j]
 
 
 # --------------------------------------------------------------------------
