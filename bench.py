@@ -76,6 +76,24 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate(dist, total_ms, total_work, device):
+    """Whole-job figures over the ranks: the slowest rank's timed region (max)
+    and the work of all ranks (sum).  Single process: unchanged."""
+    if dist is None:
+        return float(total_ms), float(total_work)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(total_work)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
+def shard(items, rank, world):
+    """The items of one rank when a fixed set is split round-robin."""
+    return items[rank::world]
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -280,7 +298,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     is fixed).  The single-LP FP64 path on a size-stratified sample of the LPs,
     one after another, gives the sequential reference time."""
     all_lps = lpgen.batch_lps(512)
-    lps = all_lps[rank::world]
+    lps = shard(all_lps, rank, world)
     stream = torch.cuda.current_stream()
     B = P.Batch(lps, stream=stream.cuda_stream)
     params = P.default_params(precision=P.FP32_BULK, max_iters=args.phase1_max_iters)
@@ -324,15 +342,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
         last = (r1, rc)
     clk = clocks.stop()
     launches = B.kernel_launches() - l0
-    total_ms = sum(step_ms)
-    total_iters = float(sum(iters))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_iters = float(it.item())
+    total_ms, total_iters = aggregate(dist, sum(step_ms), sum(iters), "cuda")
     value = total_iters / (total_ms * 1e-3)
     r1, rc = last
     peak, peak_kind = measured_peaks()
@@ -504,17 +514,8 @@ def main():
             reps.append((r1, rc))
         launches = g.kernel_launches() - launches0
         clk = clocks.stop()
-        total_ms = sum(step_ms)
         total_iters = sum(iters)
-        if dist is not None:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-            it = torch.tensor([total_iters], dtype=torch.float64, device="cuda")
-            dist.all_reduce(it, op=dist.ReduceOp.SUM)
-            total_iters_all = float(it.item())
-        else:
-            total_iters_all = float(total_iters)
+        total_ms, total_iters_all = aggregate(dist, sum(step_ms), total_iters, "cuda")
         value = total_iters_all / (total_ms * 1e-3)
         # kernel durations: event-bracketed replays of the two iteration kernels
         ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
