@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--corner-seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-iters", type=int, default=50)
-    ap.add_argument("--cpu-iters", type=int, default=128)
+    ap.add_argument("--cpu-iters", type=int, default=640,
+                    help="oracle iterations of the CPU baseline sample (about 10 s on the default LP)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-sample", type=int, default=16,
                     help="batch_512: LPs solved one by one with the single-LP FP64 path for the "
@@ -389,12 +390,23 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     Be.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mid = sorted(all_lps, key=lambda lp: lp["n"])[len(all_lps) // 2]
-        cpu = cpu_baseline_sample(mid, args.cpu_iters * 8)
-        cpu["sample"] = "median-size LP of the batch (m=%d, n=%d): " % (mid["m"], mid["n"]) + cpu["sample"]
+        # 16 LPs spread over the size range, 2048 oracle iterations each
+        by_size = sorted(all_lps, key=lambda lp: lp["n"] + lp["m"])
+        picks = [by_size[k] for k in range(16, len(by_size), len(by_size) // 16)][:16]
+        t_cpu, it_cpu = 0.0, 0
+        for lp in picks:
+            c1 = cpu_baseline_sample(lp, 2048)
+            t_cpu += 2048 / c1["value"]
+            it_cpu += 2048
+        cpu = {"value": it_cpu / t_cpu, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"2048 phase-1 PDHG iterations with restart checks on each of 16 LPs of the batch "
+                         f"spread over its size range ({t_cpu:.1f} s; setup not counted); numpy/scipy, "
+                         f"single-threaded"}
     if rank == 0:
         done = sum(r["status_name"] == "OPTIMAL" for r in r1)
         cdone = sum(r["status_name"] == "CORNER_DONE" for r in rc)
+        h1 = sum(B.handed_off(k, P.PHASE1) for k in range(len(lps)))
+        hc = sum(B.handed_off(k, P.CORNER) for k in range(len(lps)))
         out = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -405,6 +417,9 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "schedule": tuned, "corner_max_iters": args.corner_max_iters, "eps_rel": 1e-6,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"lp-split x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
+            "tail_handoff": {"phase1_lps": h1, "corner_lps": hc,
+                             "rule": "once the queue is empty and <= 16 LPs run, an LP past 4096 iterations "
+                                     "of its phase finishes on the single-LP path, concurrently"},
             "phase1": {"optimal": done, "lps": len(r1), "iters_sum": sum(r["iters"] for r in r1),
                        "iters_max": max(r["iters"] for r in r1),
                        "corner_measure_sum": sum(r["corner_measure"] for r in r1)},

@@ -332,7 +332,24 @@ int pdhgc_batch_set_layout(pdhgc_batch* batch, int32_t sell);
 int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tune_iters, int32_t* chosen,
                      double* timings_ms);
 
-/* pdhgc_batch_kernel_launches — persistent batched kernels launched so far (one per graph launch). */
+/*
+ * pdhgc_batch_set_handoff — the tail handoff.  Once every LP of the queue has
+ * been taken and at most `max_running` LPs are still running, an LP that has
+ * done at least `min_iters` iterations of the current phase stops at its next
+ * check, and the batch finishes it on the single-LP path (the graph-driven
+ * whole-GPU loop of pdhgc_solve / pdhgc_corner_phase), several such LPs
+ * concurrently on their own streams.  A handed-off LP restarts its phase from
+ * the phase's start point on that path; a corner phase handed off there
+ * starts from that path's own phase 1 of the LP.  Its report and result are
+ * the single-LP path's.  Defaults: 16, 4096; max_running = 0 disables.
+ */
+int pdhgc_batch_set_handoff(pdhgc_batch* batch, int32_t max_running, int64_t min_iters);
+
+/* pdhgc_batch_handed_off — 1 when LP `lp`'s result of phase `which` came from the single-LP path. */
+int32_t pdhgc_batch_handed_off(const pdhgc_batch* batch, int32_t lp, int which);
+
+/* pdhgc_batch_kernel_launches — kernels launched so far: one persistent kernel per graph launch, plus the
+ * single-LP kernels of handed-off LPs. */
 int64_t pdhgc_batch_kernel_launches(const pdhgc_batch* batch);
 
 void pdhgc_batch_destroy(pdhgc_batch* batch);

@@ -18,6 +18,7 @@
 #include <memory>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pdhgc.h"
@@ -205,7 +206,15 @@ struct BatchParams {
   long long c_min_iters, c_max_iters;
   unsigned long long obj_seed;
   int stop_rule;
+  // tail handoff: once the queue is empty and at most handoff_running LPs are
+  // still running, an LP past handoff_min_iters iterations of its phase stops
+  // at its next check and is finished on the single-LP path (0: never)
+  int handoff_running;
+  long long handoff_min_iters;
 };
+
+// BatchReport.status of an LP handed to the single-LP path
+constexpr int kStatusHandoff = 100;
 
 // ---- one LP, one CTA ------------------------------------------------------
 
@@ -219,6 +228,8 @@ struct LpSolver {
   double* q;    // [32] folded quantities
   VT* s_y;      // gathered y (shared or global)
   VT* s_xbar;   // gathered x_bar (shared or global)
+  const int* queue;  // [0] next LP of the queue, [1] LPs running
+  int count;
 
   __device__ void fill(double* a, int n, double v) const {
     for (int i = threadIdx.x; i < n; i += BT) a[i] = v;
@@ -492,7 +503,15 @@ struct LpSolver {
       }
       __syncthreads();
       evaluate(corner);
-      if (threadIdx.x == 0) decide_step(S, q, 1);
+      if (threadIdx.x == 0) {
+        decide_step(S, q, 1);
+        // tail handoff (reads of the queue counters, no wait)
+        if (!S->done && bp.handoff_running > 0 && S->k >= bp.handoff_min_iters &&
+            *(volatile const int*)&queue[0] >= count && *(volatile const int*)&queue[1] <= bp.handoff_running) {
+          S->done = 1;
+          S->status = kStatusHandoff;
+        }
+      }
       __syncthreads();
       if (S->done) break;
       const int rt = S->restart_to;
@@ -567,10 +586,23 @@ struct LpSolver {
     __syncthreads();
   }
 
+  __device__ bool handed_off(BatchReport* out) {
+    if (S->status != kStatusHandoff) return false;
+    if (threadIdx.x == 0) {
+      BatchReport r{};
+      r.status = kStatusHandoff;
+      r.iters = S->k;
+      *out = r;
+    }
+    __syncthreads();
+    return true;
+  }
+
   __device__ void phase1(BatchReport* out) {
     setup();
     init_phase(0, nullptr, S->nc_hat, d.c_norm);
     loop(false);
+    if (handed_off(out)) return;
     finalize(d.x1, d.y1, nullptr, false);
     report(d.x1, d.y1, out);
   }
@@ -602,6 +634,7 @@ struct LpSolver {
     __syncthreads();
     init_phase(1, d.x1, sqrt(cc2), sqrt(cu2));
     loop(true);
+    if (handed_off(out)) return;
     finalize(d.xc, nullptr, d.x1, true);
     report(d.xc, d.y1, out);
   }
@@ -617,7 +650,10 @@ __global__ void __launch_bounds__(BT) k_batch(const LpDesc* __restrict__ descs, 
   __shared__ double q[32];
   __shared__ int job;
   while (true) {
-    if (threadIdx.x == 0) job = atomicAdd(queue, 1);
+    if (threadIdx.x == 0) {
+      job = atomicAdd(&queue[0], 1);
+      if (job < count) atomicAdd(&queue[1], 1);
+    }
     __syncthreads();
     const int jj = job;
     __syncthreads();
@@ -627,11 +663,12 @@ __global__ void __launch_bounds__(BT) k_batch(const LpDesc* __restrict__ descs, 
     VT* sy = d.smem ? reinterpret_cast<VT*>(s_vec) : (std::is_same<VT, float>::value ? (VT*)d.y32 : (VT*)d.y);
     VT* sxb = d.smem ? reinterpret_cast<VT*>(s_vec) + d.m
                      : (std::is_same<VT, float>::value ? (VT*)d.xbar32 : (VT*)d.xbar);
-    LpSolver<VT, BT> sol{d, bp, &S, red, q, sy, sxb};
+    LpSolver<VT, BT> sol{d, bp, &S, red, q, sy, sxb, queue, count};
     if (phase == 0)
       sol.phase1(&reps[lp]);
     else
       sol.corner(&reps[lp]);
+    if (threadIdx.x == 0) atomicSub(&queue[1], 1);
   }
 }
 
@@ -672,7 +709,21 @@ struct pdhgc_batch {
   pdhgc_params params{};
   double tune_ms[4] = {0, 0, 0, 0};
   cudaGraphExec_t gexec = nullptr;  // the last launched batch graph
-  int64_t launches = 0;             // persistent kernels launched (one per graph)
+  int64_t launches = 0;             // kernels launched (batched, and single-LP ones of handed-off LPs)
+  int device = 0;
+  // the caller's inputs, kept for the single-LP path of handed-off LPs
+  struct HostLp {
+    int32_t m = 0, n = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col;
+    std::vector<double> val, b, c, lb, ub;
+    std::vector<int8_t> sense;
+  };
+  std::vector<HostLp> host;
+  int handoff_running = 16;
+  long long handoff_min_iters = 4096;
+  std::vector<pdhgc_report> ext_rep1, ext_repc;  // reports of handed-off LPs
+  std::vector<char> ext1, extc;                  // 1: that phase's result came from the single-LP path
   ~pdhgc_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     for (void* q : allocs) cudaFree(q);
@@ -748,7 +799,7 @@ int launch_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t 
   // batch's private stream and launched on the caller's stream
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
-  const cudaError_t me = cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->cap_stream);
+  const cudaError_t me = cudaMemsetAsync(B->d_queue, 0, 2 * sizeof(int), B->cap_stream);
   k_batch<VT, BT><<<grid, BT, smem, B->cap_stream>>>(B->d_desc, B->d_order, B->count, B->d_queue, bp, phase,
                                                      B->d_rep);
   const cudaError_t le = cudaGetLastError();
@@ -807,6 +858,80 @@ void to_report(const BatchReport& r, int64_t m, double nb, double nc, int precis
   out->sigma_max = r.sigma_max;
 }
 
+// One handed-off LP on the single-LP path (its own stream and handle, run
+// from a host thread so that several run concurrently): phase 1, and for
+// phase 1 the corner phase too (from that handle's own phase-1 result); the
+// result goes back into the batch's scaled internal buffers.
+int finish_on_single_path(pdhgc_batch* B, int k, int phase, const pdhgc_params& p, const pdhgc_corner_params* cp,
+                          std::string& err, int64_t& launches) {
+  BCK(cudaSetDevice(B->device));
+  cudaStream_t st = nullptr;
+  BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  const auto& h = B->host[k];
+  pdhgc_lp* lp = nullptr;
+  int rc = pdhgc_lp_create(&lp, h.m, h.n, (int64_t)h.col.size(), h.rp.data(), h.col.data(), h.val.data(),
+                           h.b.data(), h.c.data(), h.lb.empty() ? nullptr : h.lb.data(),
+                           h.ub.empty() ? nullptr : h.ub.data(), h.sense.empty() ? nullptr : h.sense.data(), 0, st);
+  pdhgc_report r1{}, rc_rep{};
+  if (rc == PDHGC_OK) rc = pdhgc_solve(lp, &p, &r1);
+  if (rc == PDHGC_OK && phase == 1) rc = pdhgc_corner_phase(lp, cp, &rc_rep);
+  std::vector<double> x(h.n), y(h.m);
+  if (rc == PDHGC_OK) rc = pdhgc_get_solution(lp, phase ? PDHGC_CORNER : PDHGC_PHASE1, x.data(), y.data(), nullptr, 0);
+  if (rc != PDHGC_OK) err = std::string("handoff of LP ") + std::to_string(k) + ": " + pdhgc_last_error_detail();
+  if (lp) {
+    launches = pdhgc_kernel_launches(lp);
+    pdhgc_lp_destroy(lp);
+  }
+  if (rc == PDHGC_OK) {
+    const LpDesc& d = B->h_desc[k];
+    std::vector<double> Dc(d.n), Dr(d.m), xh(d.n), yh(d.m);
+    cudaError_t e = cudaMemcpyAsync(Dc.data(), d.Dc, (size_t)d.n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Dr.data(), d.Dr, (size_t)d.m * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      for (int j = 0; j < d.n; ++j) xh[j] = x[B->col_perm[k][j]] / Dc[j];
+      for (int i = 0; i < d.m; ++i) yh[i] = B->sign[k][i] * y[B->row_perm[k][i]] / Dr[i];
+      e = cudaMemcpyAsync(phase ? d.xc : d.x1, xh.data(), (size_t)d.n * 8, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && phase == 0)
+        e = cudaMemcpyAsync(d.y1, yh.data(), (size_t)d.m * 8, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) {
+      rc = PDHGC_ERR_CUDA;
+      err = std::string("handoff copy-back: ") + cudaGetErrorString(e);
+    } else if (phase == 0) {
+      B->ext_rep1[k] = r1;
+      B->ext1[k] = 1;
+    } else {
+      B->ext_repc[k] = rc_rep;
+      B->extc[k] = 1;
+    }
+  }
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+// the LPs a batched phase handed off, finished concurrently
+int run_handoffs(pdhgc_batch* B, int phase, const pdhgc_params& p, const pdhgc_corner_params* cp) {
+  const std::vector<BatchReport>& reps = phase ? B->h_repc : B->h_rep1;
+  std::vector<int> ks;
+  for (int k = 0; k < B->count; ++k)
+    if (reps[k].status == kStatusHandoff) ks.push_back(k);
+  if (ks.empty()) return PDHGC_OK;
+  // each worker writes only its LP's slots (result buffers, report, flag)
+  std::vector<int> rcs(ks.size(), PDHGC_OK);
+  std::vector<std::string> errs(ks.size());
+  std::vector<int64_t> lcount(ks.size(), 0);
+  std::vector<std::thread> th;
+  for (size_t i = 0; i < ks.size(); ++i)
+    th.emplace_back([&, i] { rcs[i] = finish_on_single_path(B, ks[i], phase, p, cp, errs[i], lcount[i]); });
+  for (auto& t : th) t.join();
+  for (size_t i = 0; i < ks.size(); ++i) B->launches += lcount[i];
+  for (size_t i = 0; i < ks.size(); ++i)
+    if (rcs[i] != PDHGC_OK) return set_berr(rcs[i], errs[i]);
+  return PDHGC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -823,11 +948,24 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   B->stream = static_cast<cudaStream_t>(cuda_stream);
   std::vector<Prepared> P(count);
   int64_t sm = 0, sn = 0, snz = 0;
+  BCK(cudaGetDevice(&B->device));
+  B->host.resize(count);
   for (int k = 0; k < count; ++k) {
     std::string detail;
     const int rc = prepare_lp(P[k], m[k], n[k], nnz[k], row_ptr[k], col_idx[k], val[k], b[k], c[k],
                               lb ? lb[k] : nullptr, ub ? ub[k] : nullptr, sense ? sense[k] : nullptr, detail);
     if (rc != PDHGC_OK) return set_berr(rc, "LP " + std::to_string(k) + ": " + detail);
+    auto& h = B->host[k];
+    h.m = m[k];
+    h.n = n[k];
+    h.rp.assign(row_ptr[k], row_ptr[k] + m[k] + 1);
+    h.col.assign(col_idx[k], col_idx[k] + nnz[k]);
+    h.val.assign(val[k], val[k] + nnz[k]);
+    h.b.assign(b[k], b[k] + m[k]);
+    h.c.assign(c[k], c[k] + n[k]);
+    if (lb && lb[k]) h.lb.assign(lb[k], lb[k] + n[k]);
+    if (ub && ub[k]) h.ub.assign(ub[k], ub[k] + n[k]);
+    if (sense && sense[k]) h.sense.assign(sense[k], sense[k] + m[k]);
     sm += m[k];
     sn += n[k];
     snz += nnz[k];
@@ -886,7 +1024,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   BAL(ge, M); BAL(ge_c, M);
   BAL(B->d_desc, K);
   BAL(B->d_order, K);
-  BAL(B->d_queue, 1);
+  BAL(B->d_queue, 2);
   BAL(B->d_rep, K);
 #undef BAL
   cudaStream_t st = B->stream;
@@ -1021,6 +1159,10 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   BCK(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
   B->h_rep1.resize(count);
   B->h_repc.resize(count);
+  B->ext_rep1.resize(count);
+  B->ext_repc.resize(count);
+  B->ext1.assign(count, 0);
+  B->extc.assign(count, 0);
   pdhgc_default_params(&B->params);
   *out = B.release();
   return PDHGC_OK;
@@ -1038,13 +1180,23 @@ int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* 
   B->precision = p.precision;
   B->have_phase1 = 0;
   B->have_corner = 0;
+  std::fill(B->ext1.begin(), B->ext1.end(), 0);
+  std::fill(B->extc.begin(), B->extc.end(), 0);
   cudaStream_t st = B->stream;
-  RET(run_batch(B, make_params(p, nullptr), 0, st));
+  BatchParams bp = make_params(p, nullptr);
+  bp.handoff_running = B->handoff_running;
+  bp.handoff_min_iters = B->handoff_min_iters;
+  RET(run_batch(B, bp, 0, st));
   BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
+  RET(run_handoffs(B, 0, p, nullptr));
   for (int k = 0; k < B->count; ++k)
-    if (reports)
-      to_report(B->h_rep1[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, p.precision, &reports[k]);
+    if (reports) {
+      if (B->ext1[k])
+        reports[k] = B->ext_rep1[k];
+      else
+        to_report(B->h_rep1[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, p.precision, &reports[k]);
+    }
   B->have_phase1 = 1;
   return PDHGC_OK;
 }
@@ -1058,13 +1210,22 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
       !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
     return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
   cudaStream_t st = B->stream;
-  RET(run_batch(B, make_params(B->params, &cp), 1, st));
+  std::fill(B->extc.begin(), B->extc.end(), 0);
+  BatchParams bp = make_params(B->params, &cp);
+  bp.handoff_running = B->handoff_running;
+  bp.handoff_min_iters = B->handoff_min_iters;
+  RET(run_batch(B, bp, 1, st));
   BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
+  RET(run_handoffs(B, 1, B->params, &cp));
   for (int k = 0; k < B->count; ++k)
-    if (reports)
-      to_report(B->h_repc[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, B->precision,
-                &reports[k]);
+    if (reports) {
+      if (B->extc[k])
+        reports[k] = B->ext_repc[k];
+      else
+        to_report(B->h_repc[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, B->precision,
+                  &reports[k]);
+    }
   B->have_corner = 1;
   return PDHGC_OK;
 }
@@ -1175,6 +1336,18 @@ int pdhgc_batch_tune(pdhgc_batch* B, const pdhgc_params* params, int32_t tune_it
 }
 
 int64_t pdhgc_batch_kernel_launches(const pdhgc_batch* B) { return B ? B->launches : 0; }
+
+int pdhgc_batch_set_handoff(pdhgc_batch* B, int32_t max_running, int64_t min_iters) {
+  if (!B || max_running < 0 || min_iters < 0) return set_berr(PDHGC_ERR_INVALID_ARG, "bad argument");
+  B->handoff_running = max_running;
+  B->handoff_min_iters = min_iters;
+  return PDHGC_OK;
+}
+
+int32_t pdhgc_batch_handed_off(const pdhgc_batch* B, int32_t lp, int which) {
+  if (!B || lp < 0 || lp >= B->count) return 0;
+  return which == PDHGC_CORNER ? B->extc[lp] : B->ext1[lp];
+}
 
 void pdhgc_batch_destroy(pdhgc_batch* B) {
   if (!B) return;

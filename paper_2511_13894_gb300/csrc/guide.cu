@@ -13,6 +13,11 @@
 // cores from shared-memory copies of the chunk, one 16-row slice of the
 // gradient per warp, accumulated in registers across chunks; per-CTA
 // partials are then folded in a fixed order, so a step is deterministic.
+//
+// Inference (k_guide_forward_tc) runs on the 5th-generation tensor cores:
+// tcgen05.mma from shared-memory operands into tensor-memory accumulators,
+// 128 rows per tile, one CTA per SM.  k_guide_forward is the mma.sync form
+// of the same pass (built with PDHGC_GUIDE_TC=0).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -203,6 +208,231 @@ __global__ void __launch_bounds__(kGThreads) k_guide_forward(const GuideBf16* __
       if (r0 < rows) p[r0] = sigmoid(o0 + b3);
       if (r1 < rows) p[r1] = sigmoid(o1 + b3);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor cores: tcgen05.mma with operands in
+// shared memory and FP32 accumulators in tensor memory.  One CTA per SM
+// (persistent over 128-row tiles), 4 warps; thread t owns row t of a tile.
+// Layer 1: D1[128 x 64] = X[128 x 32] W1'; layer 2: D2[128 x 64] = A1[128 x 64]
+// W2'.  Operands use the K-major layout without swizzle: core matrices of
+// 8 rows x 16 bytes (8 BF16) stored contiguously, the K-adjacent cores 128
+// bytes apart (leading byte offset) and the 8-row groups KC x 128 bytes apart
+// (stride byte offset), KC = K / 8.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcCols = 128;          // TMEM columns: [0, 64) layer 1, [64, 128) layer 2
+constexpr long long kTcWaitLimit = 1ll << 24;  // bounded mbarrier wait (iterations)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading / stride byte offsets,
+// the fixed version field (bits 46-47 = 1), base offset 0, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// bounded wait for phase `parity` of the mbarrier; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long i = 0; i < kTcWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive TMEM columns of this thread's lane (warp w reads lanes 32w..32w+31)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row r, k) in the K-major core-matrix layout with KC cores per row group
+__device__ __forceinline__ uint32_t core_off(int r, int k, int KC) {
+  return (uint32_t)((((r >> 3) * KC + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+struct TcSmem {
+  __nv_bfloat16 x[kTcRows * kGFeat];   // 8 KB, KC = 4
+  __nv_bfloat16 a1[kTcRows * kGHid];   // 16 KB, KC = 8
+  __nv_bfloat16 w1[kGHid * kGFeat];    // 4 KB, KC = 4
+  __nv_bfloat16 w2[kGHid * kGHid];     // 8 KB, KC = 8
+  float b1[kGHid], b2[kGHid], w3[kGHid];
+  unsigned long long mbar;
+  uint32_t tmem_base;
+};
+
+__global__ void __launch_bounds__(kTcRows, 1) k_guide_forward_tc(const GuideBf16* __restrict__ wb,
+                                                                 const float* __restrict__ w,
+                                                                 const __nv_bfloat16* __restrict__ feat,
+                                                                 long long rows, float* __restrict__ p,
+                                                                 int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(tc_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights in the core-matrix layout: one 16-byte chunk (8 inputs of one unit) per copy
+  for (int e = tid; e < kGHid * (kGFeat / 8); e += blockDim.x) {
+    const int j = e / (kGFeat / 8), kc = e % (kGFeat / 8);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.w1) + core_off(j, kc * 8, kGFeat / 8)) =
+        *reinterpret_cast<const uint4*>(wb->w1 + j * kGFeat + kc * 8);
+  }
+  for (int e = tid; e < kGHid * (kGHid / 8); e += blockDim.x) {
+    const int j = e / (kGHid / 8), kc = e % (kGHid / 8);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.w2) + core_off(j, kc * 8, kGHid / 8)) =
+        *reinterpret_cast<const uint4*>(wb->w2 + j * kGHid + kc * 8);
+  }
+  for (int j = tid; j < kGHid; j += blockDim.x) {
+    s.b1[j] = w[kOffB1 + j];
+    s.b2[j] = w[kOffB2 + j];
+    s.w3[j] = __bfloat162float(wb->w3[j]);
+  }
+  const float b3 = w[kOffB3];
+  const uint32_t mbar = smem_addr(&s.mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s.tmem_base)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  async_proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s.tmem_base;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t x_addr = smem_addr(s.x), a1_addr = smem_addr(s.a1);
+  const uint32_t w1_addr = smem_addr(s.w1), w2_addr = smem_addr(s.w2);
+  constexpr uint32_t kIdesc = umma_idesc(kTcRows, kGHid);
+  uint32_t parity = 0;
+  bool ok = true;
+  const long long ntiles = (rows + kTcRows - 1) / kTcRows;
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // ---- this thread's input row into the core layout (zeros past the end)
+    const long long r = tile * kTcRows + tid;
+    const uint4* src = reinterpret_cast<const uint4*>(feat + r * kGFeat);
+#pragma unroll
+    for (int kc = 0; kc < kGFeat / 8; ++kc) {
+      const uint4 v = r < rows ? src[kc] : make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.x) + core_off(tid, kc * 8, kGFeat / 8)) = v;
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    // ---- layer 1: two K = 16 steps into TMEM columns [0, 64)
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < kGFeat / 16; ++ks)
+        umma_bf16(tmem, umma_desc(x_addr + ks * 256, 128, (kGFeat / 8) * 128),
+                  umma_desc(w1_addr + ks * 256, 128, (kGFeat / 8) * 128), kIdesc, ks > 0 ? 1u : 0u);
+      umma_commit(mbar);
+    }
+    ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;  // the same decision in every thread
+    if (!ok) break;
+    parity ^= 1u;
+    tc_fence_after();
+    // ---- epilogue 1: bias, ReLU, BF16, into the layer-2 operand
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + half * 32, v);
+#pragma unroll
+      for (int c8 = 0; c8 < 4; ++c8) {
+        uint32_t q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = half * 32 + c8 * 8 + 2 * u;
+          q[u] = pack2(relu(v[c8 * 8 + 2 * u] + s.b1[j]), relu(v[c8 * 8 + 2 * u + 1] + s.b1[j + 1]));
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.a1) +
+                                  core_off(tid, half * 32 + c8 * 8, kGHid / 8)) = make_uint4(q[0], q[1], q[2], q[3]);
+      }
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    // ---- layer 2: four K = 16 steps into TMEM columns [64, 128)
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < kGHid / 16; ++ks)
+        umma_bf16(tmem + 64, umma_desc(a1_addr + ks * 256, 128, (kGHid / 8) * 128),
+                  umma_desc(w2_addr + ks * 256, 128, (kGHid / 8) * 128), kIdesc, ks > 0 ? 1u : 0u);
+      umma_commit(mbar);
+    }
+    ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;
+    if (!ok) break;
+    parity ^= 1u;
+    tc_fence_after();
+    // ---- epilogue 2: bias, ReLU, BF16 activations, the output unit, sigmoid
+    float o = b3;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + 64 + half * 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int j = half * 32 + i;
+        o = fmaf(bf_round(relu(v[i] + s.b2[j])), s.w3[j], o);
+      }
+    }
+    if (r < rows) p[r] = sigmoid(o);
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // the pending MMA may still be in flight: give it the same bounded time to land
+    mbar_wait(mbar, parity);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
   }
 }
 
@@ -537,14 +767,36 @@ int guide_sync_bf16(pdhgc_guide* g, cudaStream_t st) {
   return PDHGC_OK;
 }
 
+#ifndef PDHGC_GUIDE_TC
+#define PDHGC_GUIDE_TC 1
+#endif
+
 int guide_forward(pdhgc_guide* g, const __nv_bfloat16* feat, int64_t rows, float* p, cudaStream_t st) {
   if (rows <= 0) return PDHGC_OK;
+#if PDHGC_GUIDE_TC
+  // tcgen05: one CTA per SM at most, persistent over 128-row tiles
+  const long long tiles = (rows + kTcRows - 1) / kTcRows;
+  const long long grid = tiles < g->max_ctas ? tiles : g->max_ctas;
+  k_guide_forward_tc<<<(unsigned)grid, kTcRows, sizeof(TcSmem), st>>>(g->wb, g->w, feat, (long long)rows, p, g->err);
+#else
   const long long tiles = (rows + 15) / 16;
   long long grid = (tiles + kGWarps - 1) / kGWarps;
   if (grid > 152 * 8) grid = 152 * 8;
   k_guide_forward<<<(unsigned)grid, kGThreads, 0, st>>>(g->wb, g->w, feat, (long long)rows, p);
+#endif
   g->launches++;
   GKL();
+  return PDHGC_OK;
+}
+
+int guide_check_error(pdhgc_guide* g, cudaStream_t st) {
+  int e = 0;
+  GK(cudaMemcpyAsync(&e, g->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GK(cudaStreamSynchronize(st));
+  if (e != 0) {
+    GK(cudaMemsetAsync(g->err, 0, sizeof(int), st));
+    return set_error_detail(PDHGC_ERR_DEVICE, "a bounded tensor-core wait of the network ran out");
+  }
   return PDHGC_OK;
 }
 
@@ -635,6 +887,8 @@ int pdhgc_guide_create(pdhgc_guide** out, uint64_t seed, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&g->grad, sizeof(float) * kGPartial);
   if (e == cudaSuccess) e = cudaMalloc(&g->wb, sizeof(GuideBf16));
   if (e == cudaSuccess) e = cudaMalloc(&g->partials, sizeof(float) * kGPartial * (size_t)g->max_ctas);
+  if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->wb, 0, sizeof(GuideBf16), g->stream);
   if (e != cudaSuccess) {
     pdhgc_guide_destroy(g);
@@ -661,6 +915,7 @@ void pdhgc_guide_destroy(pdhgc_guide* g) {
   cudaFree(g->wb);
   cudaFree(g->partials);
   cudaFree(g->idx);
+  cudaFree(g->err);
   delete g;
 }
 
@@ -684,8 +939,7 @@ int pdhgc_guide_infer(pdhgc_guide* g, const uint16_t* feat, int64_t rows, float*
   if (rc != PDHGC_OK) return rc;
   rc = guide_forward(g, reinterpret_cast<const __nv_bfloat16*>(feat), rows, p, g->stream);
   if (rc != PDHGC_OK) return rc;
-  GK(cudaStreamSynchronize(g->stream));
-  return PDHGC_OK;
+  return guide_check_error(g, g->stream);
 }
 
 int pdhgc_guide_grad(pdhgc_guide* g, const uint16_t* feat, const uint8_t* labels, int64_t rows, const int32_t* idx,

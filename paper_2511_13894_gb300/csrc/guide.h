@@ -42,6 +42,7 @@ struct pdhgc_guide {
   float* partials = nullptr;  // per-CTA partial gradients
   int max_ctas = 0;
   int32_t* idx = nullptr;     // explicit minibatch indices (gradient check)
+  int* err = nullptr;         // set by a kernel whose bounded wait ran out
   int idx_cap = 0;
   int64_t adam_t = 0;         // Adam steps taken
   int64_t launches = 0;
@@ -52,6 +53,9 @@ namespace pdhgc {
 // forward pass: p[r] = sigmoid(network(feat row r)) for r < rows; feat is
 // rows x kGFeat BF16 on the device; p FP32 on the device
 int guide_forward(pdhgc_guide* g, const __nv_bfloat16* feat, int64_t rows, float* p, cudaStream_t st);
+
+// the error word of the network's kernels (synchronises st); DEVICE when set
+int guide_check_error(pdhgc_guide* g, cudaStream_t st);
 
 // one minibatch gradient (idx != nullptr: explicit device indices; else drawn
 // from SplitMix64(seed, step * batch + s) mod rows) folded into g->grad;

@@ -1487,6 +1487,7 @@ int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, c
   if (g) {
     RET(build_features(lp, cp, false, lp->gfeat, nullptr));
     RET(guide_forward(g, reinterpret_cast<const __nv_bfloat16*>(lp->gfeat), n, lp->gprob, st));
+    RET(guide_check_error(g, st));
     k_hold_from_p<<<nb, 256, 0, st>>>(n, lp->gprob, gp.threshold, lp->ghold);
   } else {
     const uint8_t* src = hold;

@@ -121,6 +121,8 @@ _sig = {
     "pdhgc_batch_set_layout": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_batch_tune": (C.c_int, [_vp, C.POINTER(Params), C.c_int32, _vp, _vp]),
     "pdhgc_batch_kernel_launches": (C.c_int64, [_vp]),
+    "pdhgc_batch_set_handoff": (C.c_int, [_vp, C.c_int32, C.c_int64]),
+    "pdhgc_batch_handed_off": (C.c_int32, [_vp, C.c_int32, C.c_int]),
     "pdhgc_default_guide_params": (None, [C.POINTER(GuideParams)]),
     "pdhgc_guide_create": (C.c_int, [C.POINTER(_vp), C.c_uint64, _vp]),
     "pdhgc_guide_destroy": (None, [_vp]),
@@ -431,6 +433,13 @@ class Batch:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_batch_kernel_launches(self._h))
+
+    def set_handoff(self, max_running: int = 16, min_iters: int = 4096):
+        """pdhgc_batch_set_handoff (max_running = 0 disables the tail handoff)."""
+        _check(lib.pdhgc_batch_set_handoff(self._h, int(max_running), int(min_iters)), "pdhgc_batch_set_handoff")
+
+    def handed_off(self, k: int, which: int = PHASE1) -> bool:
+        return bool(lib.pdhgc_batch_handed_off(self._h, int(k), int(which)))
 
     def set_block(self, threads: int):
         _check(lib.pdhgc_batch_set_block(self._h, threads), "pdhgc_batch_set_block")

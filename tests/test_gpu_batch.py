@@ -48,6 +48,7 @@ def test_batch_fp64_iterates_after_100_match_oracle():
 def test_batch_fp64_full_solves_match_oracle():
     lps = _mixed_lps()
     B = P.Batch(lps)
+    B.set_handoff(0)  # every LP to the end inside the batched kernel
     reps = B.solve()
     for k, lp in enumerate(lps):
         ref = oracle.solve(lp)
@@ -81,3 +82,29 @@ def test_batch_fp32_reaches_tolerance_and_schedules_agree():
     for r, r2 in zip(reps, reps2):
         assert r2["status_name"] == "OPTIMAL" and r2["rel_kkt"] <= 1e-6
         assert abs(r2["pobj"] - r["pobj"]) <= 1e-5 * (1 + abs(r["pobj"]))
+
+
+def test_batch_tail_handoff_matches_oracle():
+    # with few LPs left every LP past 128 iterations is handed to the single-LP
+    # path: same results as the oracle, flagged as handed off
+    lps = _mixed_lps()
+    B = P.Batch(lps)
+    B.set_handoff(16, 128)
+    reps = B.solve()
+    handed = [B.handed_off(k) for k in range(len(lps))]
+    assert sum(handed) >= 3
+    for k, lp in enumerate(lps):
+        ref = oracle.solve(lp)
+        assert reps[k]["status_name"] == "OPTIMAL", k
+        assert reps[k]["iters"] == ref["iters"] and reps[k]["restarts"] == ref["restarts"], k
+        xo, yo, _ = oracle.unscale(ref["model"], ref["x_hat"], ref["y_hat"])
+        x, y = B.get_solution(k)
+        assert rel_err(x, xo) <= 1e-8 and rel_err(y, yo) <= 1e-8, k
+    creps = B.corner_phase(obj_seed=11)
+    for k, lp in enumerate(lps[:3]):
+        ref1 = oracle.solve(lp)
+        refc = oracle.corner_phase(ref1, dict(obj_seed=11))
+        assert creps[k]["status"] == refc["status"] and creps[k]["iters"] == refc["iters"], k
+        x, _ = B.get_solution(k, P.CORNER)
+        xo, _, _ = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+        assert rel_err(x, xo) <= 1e-7, k
