@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--phase1-max-iters", type=int, default=1_000_000)
     ap.add_argument("--corner-max-iters", type=int, default=200_000)
     ap.add_argument("--corner-seed", type=int, default=1)
+    ap.add_argument("--no-row-option", action="store_true",
+                    help="skip the extra arms that time the corner phase with the row_rule = 1 option")
+    ap.add_argument("--corner-rows", choices=["paper", "active"], default="paper",
+                    help="paper: Section 3's row rule; active: the option that keeps rows inactive at the "
+                         "phase-1 point as inequalities (row_rule = 1)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-iters", type=int, default=50)
     ap.add_argument("--cpu-iters", type=int, default=640,
@@ -194,16 +199,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8, s_sum=8):
+def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8, s_sum=8, s_lo=0):
     """Bytes one PDHG iteration must move (gathers counted once per element):
     primal (A' pass): values + indices, row pointers, reads of c, l, u, x and
     the running sum, writes of x, x_bar and the running sum, y gathered once;
     dual (A pass): values + indices, row pointers, reads of b, y, the running
     sum and the sense byte, writes of y and the running sum, x_bar gathered once.
     s_v, s_x, s_sum: bytes of a matrix value, an iterate / model entry and a
-    running-sum entry (8, 8, 8 in FP64; 4, 4, 8 in FP32 bulk)."""
-    primal = nnz * (s_v + 4) + n * 4 + n * (6 * s_x + 2 * s_sum) + m * s_x
-    dual = nnz * (s_v + 4) + m * 4 + m * (3 * s_x + 2 * s_sum + 1) + n * s_x
+    running-sum entry (8, 8, 8 in FP64; 4, 4, 8 in FP32 bulk); s_lo: bytes of
+    the low part of a float-float iterate, read and written (0; 4 in FP32 bulk)."""
+    primal = nnz * (s_v + 4) + n * 4 + n * (6 * s_x + 2 * s_sum + 2 * s_lo) + m * s_x
+    dual = nnz * (s_v + 4) + m * 4 + m * (3 * s_x + 2 * s_sum + 2 * s_lo + 1) + n * s_x
     return primal, dual
 
 
@@ -285,9 +291,9 @@ def cpu_baseline_sample(lp, iters):
                       f"numpy/scipy, single-threaded"}
 
 
-def batch_bytes_per_iter(lp, s_v=4, s_x=4, s_sum=8):
+def batch_bytes_per_iter(lp, s_v=4, s_x=4, s_sum=8, s_lo=4):
     m, n, nnz = int(lp["m"]), int(lp["n"]), int(lp["row_ptr"][-1])
-    p, d = algorithmic_bytes(m, n, nnz, s_v, s_x, s_sum)
+    p, d = algorithmic_bytes(m, n, nnz, s_v, s_x, s_sum, s_lo)
     return p + d
 
 
@@ -487,7 +493,8 @@ def main():
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"mode": "kernels", "workload": args.workload, "primal_ms": ms[0], "dual_ms": ms[1]}))
         return
-    cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
+    cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
+                                      row_rule=1 if args.corner_rows == "active" else 0)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     uuid = None
     try:
@@ -496,7 +503,7 @@ def main():
         uuid = None
     peak, peak_kind = measured_peaks()
 
-    def run_arm(precision):
+    def run_arm(precision, cparams=cparams):
         params = P.default_params(max_iters=args.phase1_max_iters, precision=precision)
 
         def step():
@@ -538,7 +545,7 @@ def main():
             b_primal, b_dual = algorithmic_bytes(m, n, nnz)
             f_primal, f_dual = fp64_ops(m, n, nnz)
         else:
-            b_primal, b_dual = algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8)
+            b_primal, b_dual = algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
             f_primal, f_dual = n, m  # FP64 ops left per launch: the running-sum adds
         dom = "primal" if ms_primal >= ms_dual else "dual"
         ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
@@ -583,6 +590,12 @@ def main():
         arms["fp64"] = run_arm(P.FP64)
     if args.precision in ("fp32", "both"):
         arms["fp32"] = run_arm(P.FP32_BULK)
+    # the corner row option (not the paper's rule): the same step with rows
+    # inactive at the phase-1 point kept as inequalities, FP64 and FP32 bulk
+    if args.corner_rows == "paper" and not args.no_row_option and args.precision == "both":
+        cp_opt = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed, row_rule=1)
+        arms["fp64_rows"] = run_arm(P.FP64, cp_opt)
+        arms["fp32_rows"] = run_arm(P.FP32_BULK, cp_opt)
     head = arms["fp64"] if "fp64" in arms else arms["fp32"]
     params = head["params"]
     value = head["value"]
@@ -640,7 +653,7 @@ def main():
             "config": {"workload": args.workload, "m": m, "n": n, "nnz": nnz,
                        "precision": "fp64" if head_is_fp64 else "fp32_bulk",
                        "phase1_max_iters": args.phase1_max_iters, "corner_max_iters": args.corner_max_iters,
-                       "corner_seed": args.corner_seed, "eps_rel": 1e-6,
+                       "corner_seed": args.corner_seed, "corner_rows": args.corner_rows, "eps_rel": 1e-6,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
         }
@@ -656,6 +669,18 @@ def main():
                    "roofline": f["roofline"], "gpu_launches": f["launches"], "clocks": f["clocks"]}
             blk.update(summary(f))
             out["fp32_bulk"] = blk
+        if "fp64_rows" in arms:
+            a64, a32 = arms["fp64_rows"], arms["fp32_rows"]
+            blk = {"note": "corner phase with row_rule = 1 (an option, not the paper's rule): a row becomes '=' "
+                           "only when its dual is non-trivial and it is active at the phase-1 point",
+                   "fp64": {"value": a64["value"], "unit": "iters/s",
+                            "time_to_corner_s": a64["total_ms"] / args.steps * 1e-3, "clocks": a64["clocks"]},
+                   "fp32_bulk": {"value": a32["value"], "unit": "iters/s",
+                                 "time_to_corner_s": a32["total_ms"] / args.steps * 1e-3, "clocks": a32["clocks"]},
+                   "speedup_fp32_vs_fp64_time_to_corner": a64["total_ms"] / a32["total_ms"] if a32["total_ms"] else None}
+            blk["fp64"].update(summary(a64))
+            blk["fp32_bulk"].update(summary(a32))
+            out["corner_row_option"] = blk
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

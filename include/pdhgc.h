@@ -102,7 +102,10 @@ typedef struct pdhgc_corner_params {
     uint64_t obj_seed;     /* seed of the Uniform([0,1]^n) objective (SplitMix64 stream) */
     double   obj_scale;    /* objective = obj_scale * U[0,1) (1.0; Section 5 studies small scales) */
     int32_t  stop_rule;    /* 0: Section 3.1 primal rule; 1: full relative KKT (a testing aid) */
-    int32_t  reserved;
+    int32_t  row_rule;     /* 0 (default): Section 3's rule, an inequality row whose dual is non-trivial
+                              (|y_i| > eps_abs) becomes '='; 1 (an option, not the paper's): only when the
+                              row is also active at the phase-1 point (slack a_i x - b_i <= eps_abs in the
+                              '>' form), so that the start point stays primal feasible */
 } pdhgc_corner_params;
 
 /*

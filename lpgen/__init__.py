@@ -277,19 +277,22 @@ def large_transportation_lp(seed: int = 0, base_seed: int = 0):
                              name="transportation_1000x2000")
 
 
+def batch_lp(i: int, base_seed: int = 0, m_range=(50, 5000)):
+    """LP i of the batch workload: the random-face construction with
+    m ~ U{m_range}, n = round(r m), r ~ U(2, 4), column nnz ~ U{3..12},
+    |S| = m + ceil(m / 4)."""
+    seed = workload_seed(base_seed, 3, i)
+    rng = _rng(seed)
+    m = int(rng.integers(m_range[0], m_range[1] + 1))
+    n = int(round(rng.uniform(2.0, 4.0) * m))
+    support = m + int(math.ceil(0.25 * m))
+    return random_face_lp(m, n, support, seed + 7919 * WORKLOAD_SEED_STRIDE,
+                          col_nnz_range=(3, 12), name=f"batch_{i}")
+
+
 def batch_lps(count: int = 512, base_seed: int = 0, m_range=(50, 5000)):
-    """`count` LPs of the random-face construction: m ~ U{m_range}, n = round(r m)
-    with r ~ U(2, 4), column nnz ~ U{3..12} per column, |S| = m + ceil(m / 4)."""
-    lps = []
-    for i in range(count):
-        seed = workload_seed(base_seed, 3, i)
-        rng = _rng(seed)
-        m = int(rng.integers(m_range[0], m_range[1] + 1))
-        n = int(round(rng.uniform(2.0, 4.0) * m))
-        support = m + int(math.ceil(0.25 * m))
-        lps.append(random_face_lp(m, n, support, seed + 7919 * WORKLOAD_SEED_STRIDE,
-                                  col_nnz_range=(3, 12), name=f"batch_{i}"))
-    return lps
+    """`count` LPs of the batch workload (batch_lp 0 .. count-1)."""
+    return [batch_lp(i, base_seed, m_range) for i in range(count)]
 
 
 def tiny_face_lp(m: int, n: int, support: int, seed: int, col_nnz=3):

@@ -68,6 +68,7 @@ CORNER_DEFAULTS = dict(
     obj_seed=0,
     obj_scale=1.0,       # Algorithm 1: obj = Uniform([0,1]^n); Section 5 studies smaller scales
     stop_rule="primal",  # Section 3.1 rule; "kkt" (full convergence) exists for tests only
+    row_rule=0,          # 0: Section 3's row rule; 1: an option, only rows active at the phase-1 point
 )
 
 METRIC_TOL = 1e-6        # Section 4.2: both tolerances 1e-6
@@ -536,6 +537,11 @@ def corner_model(model: Model, x_hat1, y_hat1, cp, hold=None):
         cm.l = np.where(held, nb * model.Dc, cm.l)
         cm.u = np.where(held, nb * model.Dc, cm.u)
     to_eq = model.ge & (np.abs(y1) > cp["eps_abs"])
+    if cp.get("row_rule", 0) == 1:
+        # option (not the paper's): keep a row '>' when the phase-1 point is
+        # off it, so that the start point stays primal feasible
+        x1 = model.Dc * x_hat1
+        to_eq &= (model.A_int @ x1 - model.b_int) <= cp["eps_abs"]
     cm.ge = model.ge & ~to_eq
     cm.set_objective(cp["obj_scale"] * splitmix64_uniform(cp["obj_seed"], model.n))
     return cm, dict(fixed_upper=int(fix_up.sum()), fixed_lower=int(fix_lo.sum()),

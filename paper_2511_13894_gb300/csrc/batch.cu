@@ -57,6 +57,7 @@ struct LpDesc {
   float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32;
   double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r;  // FP64 iterates (x_bar, y: global fallback)
   float *x32, *xbar32, *y32;                          // FP32 iterates (global fallback)
+  float *x32lo, *y32lo;                               // low parts of the float-float FP32 iterates
   double *x1, *y1, *xc;
   double *pi_v, *pi_w, *pi_u;
   double* keep;  // eta, sigma_max, ||b_hat||, ||c_hat|| from phase 1 (read by the corner phase)
@@ -206,6 +207,7 @@ struct BatchParams {
   long long c_min_iters, c_max_iters;
   unsigned long long obj_seed;
   int stop_rule;
+  int row_rule;
   // tail handoff: once the queue is empty and at most handoff_running LPs are
   // still running, an LP past handoff_min_iters iterations of its phase stops
   // at its next check and is finished on the single-LP path (0: never)
@@ -390,15 +392,20 @@ struct LpSolver {
       d.x_r[j] = x0;
       d.sum_x[j] = 0.0;
       if (kF32) {
-        d.x32[j] = (float)x0;
-        s_xbar[j] = (VT)x0;
+        const float h = (float)x0;
+        d.x32[j] = h;
+        d.x32lo[j] = (float)(x0 - (double)h);
+        s_xbar[j] = (VT)h;
       } else {
         ((double*)s_xbar)[j] = x0;
       }
     }
     for (int i = threadIdx.x; i < m; i += BT) {
       s_y[i] = (VT)0;
-      if (kF32) d.y[i] = 0.0;
+      if (kF32) {
+        d.y[i] = 0.0;
+        d.y32lo[i] = 0.0f;
+      }
       d.y_r[i] = 0.0;
       d.sum_y[i] = 0.0;
     }
@@ -455,7 +462,7 @@ struct LpSolver {
     double part[1] = {0.0};
     if constexpr (kF32) {
       const DevModel32 md = model32(corner);
-      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sum_x, d.sum_y};
+      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sum_x, d.sum_y, d.x32lo, d.y32lo};
       passT(matT32(), PrimalOp32{S, it, (float*)s_y, md, w}, part);
       __syncthreads();
       passA(matA32(), DualOp32{S, it, (float*)s_xbar, md, w}, part);
@@ -475,7 +482,7 @@ struct LpSolver {
     const int m = d.m, n = d.n;
     const DevModel md = model(corner);
     if (kF32) {
-      for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i];
+      for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
     }
     __syncthreads();
     evaluate(corner);
@@ -498,8 +505,9 @@ struct LpSolver {
         if (S->chunks > S->max_chunks) S->at_limit = 1;
       }
       if (kF32) {
-        for (int j = threadIdx.x; j < n; j += BT) d.x[j] = fmin(fmax((double)d.x32[j], md.lhat[j]), md.uhat[j]);
-        for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i];
+        for (int j = threadIdx.x; j < n; j += BT)
+          d.x[j] = fmin(fmax((double)d.x32[j] + (double)d.x32lo[j], md.lhat[j]), md.uhat[j]);
+        for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
       }
       __syncthreads();
       evaluate(corner);
@@ -523,14 +531,22 @@ struct LpSolver {
           w.x[j] = xn;
           w.x_r[j] = xn;
           w.sum_x[j] = 0.0;
-          if (kF32 && rt == 2) d.x32[j] = (float)xn;
+          if (kF32 && rt == 2) {
+            const float h = (float)xn;
+            d.x32[j] = h;
+            d.x32lo[j] = (float)(xn - (double)h);
+          }
         }
         for (int i = threadIdx.x; i < m; i += BT) {
           const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
           w.y[i] = yn;
           w.y_r[i] = yn;
           w.sum_y[i] = 0.0;
-          if (kF32 && rt == 2) ((float*)s_y)[i] = (float)yn;
+          if (kF32 && rt == 2) {
+            const float h = (float)yn;
+            ((float*)s_y)[i] = h;
+            d.y32lo[i] = (float)(yn - (double)h);
+          }
         }
       }
       __syncthreads();
@@ -623,8 +639,19 @@ struct LpSolver {
                  pc);
     cta_fold<BT>(pc, 2, 0u, q, red);
     const double cc2 = q[0], cu2 = q[1];
-    for (int i = threadIdx.x; i < d.m; i += BT)
-      d.ge_c[i] = (d.ge[i] && !(fabs(d.Dr[i] * d.y1[i]) > bp.eps_abs)) ? 1 : 0;
+    if (bp.row_rule == 1) {  // the option: A_hat x1 for the row slacks
+      if (threadIdx.x == 0) S->pi_zero = 0;
+      fill(d.pi_u, d.m, 0.0);
+      __syncthreads();
+      double pu[1] = {0.0};
+      passA(matA(1), SpmvOp<false>{S, d.x1, d.pi_u}, pu);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < d.m; i += BT) {
+      bool to_eq = d.ge[i] && fabs(d.Dr[i] * d.y1[i]) > bp.eps_abs;
+      if (to_eq && bp.row_rule == 1) to_eq = d.pi_u[i] / d.Dr[i] - d.b_int[i] <= bp.eps_abs;
+      d.ge_c[i] = (d.ge[i] && !to_eq) ? 1 : 0;
+    }
     if (kF32)
       for (int j = threadIdx.x; j < d.n; j += BT) {
         d.chat_c32[j] = (float)d.chat_c[j];
@@ -780,6 +807,7 @@ BatchParams make_params(const pdhgc_params& p, const pdhgc_corner_params* cp) {
     b.c_max_iters = cp->max_iters;
     b.obj_seed = cp->obj_seed;
     b.stop_rule = cp->stop_rule;
+    b.row_rule = cp->row_rule;
   }
   return b;
 }
@@ -1011,7 +1039,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   BAL(shatA32, SA + kPad); BAL(shatT32, ST + kPad);
   double *b_int, *cc, *l, *u, *Dr, *Dc, *rfac, *cfac, *bhat, *chat, *lhat, *uhat, *chat_c, *lhat_c, *uhat_c;
   double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r, *x1, *y1, *xc, *pi_v, *pi_w, *pi_u;
-  float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32, *x32, *xbar32, *y32;
+  float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32, *x32, *xbar32, *y32, *x32lo, *y32lo;
   int8_t *ge, *ge_c;
   BAL(b_int, M); BAL(cc, N); BAL(l, N); BAL(u, N); BAL(Dr, M); BAL(Dc, N); BAL(rfac, M); BAL(cfac, N);
   BAL(bhat, M); BAL(chat, N); BAL(lhat, N); BAL(uhat, N); BAL(chat_c, N); BAL(lhat_c, N); BAL(uhat_c, N);
@@ -1020,7 +1048,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   double* keep;
   BAL(keep, 4 * K);
   BAL(bhat32, M); BAL(chat32, N); BAL(lhat32, N); BAL(uhat32, N); BAL(chat_c32, N); BAL(lhat_c32, N);
-  BAL(uhat_c32, N); BAL(x32, N); BAL(xbar32, N); BAL(y32, M);
+  BAL(uhat_c32, N); BAL(x32, N); BAL(xbar32, N); BAL(y32, M); BAL(x32lo, N); BAL(y32lo, M);
   BAL(ge, M); BAL(ge_c, M);
   BAL(B->d_desc, K);
   BAL(B->d_order, K);
@@ -1077,6 +1105,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
     d.x = x + on; d.xbar = xbar + on; d.sum_x = sum_x + on; d.x_r = x_r + on;
     d.y = y + om; d.sum_y = sum_y + om; d.y_r = y_r + om;
     d.x32 = x32 + on; d.xbar32 = xbar32 + on; d.y32 = y32 + om;
+    d.x32lo = x32lo + on; d.y32lo = y32lo + om;
     d.x1 = x1 + on; d.y1 = y1 + om; d.xc = xc + on;
     d.pi_v = pi_v + on; d.pi_w = pi_w + on; d.pi_u = pi_u + om;
     d.keep = keep + 4 * (size_t)k;
@@ -1207,7 +1236,8 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
   pdhgc_corner_params cp;
   if (params) cp = *params; else pdhgc_default_corner_params(&cp);
   if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
-      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
+      (cp.row_rule != 0 && cp.row_rule != 1))
     return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
   cudaStream_t st = B->stream;
   std::fill(B->extc.begin(), B->extc.end(), 0);

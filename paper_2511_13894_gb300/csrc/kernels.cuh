@@ -973,13 +973,35 @@ struct DevModel32 {
   const int8_t* ge;
 };
 
+// FP32-bulk iterates.  x and y are carried as float-float pairs (x + xlo):
+// the gathers and the matrix products read the high parts only, while the
+// updates x - tau g and y + sigma r are added exactly into the pair, so that
+// steps far below an FP32 unit of the iterate (tiny tau or sigma) still move
+// it.  xbar is FP32 (it is only gathered).
 struct DevIter32 {
   float* x;
   float* y;
   float* xbar;
   double* sum_x;
   double* sum_y;
+  float* xlo;
+  float* ylo;
 };
+
+// (hi, lo) + a * b, with a * b formed exactly (fma) and both sums TwoSum:
+// the pair keeps about 48 bits
+__device__ __forceinline__ void ff_axpy(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  const float l = lo + (err + e);
+  const float h2 = s + l;
+  const float b2 = h2 - s;
+  lo = (s - (h2 - b2)) + (l - b2);
+  hi = h2;
+}
 
 // x' = proj_[l,u](x - tau (c - A'y)),  x_bar = 2x' - x,  sum_x += x'  (FP32 bulk)
 struct PrimalOp32 {
@@ -999,18 +1021,26 @@ struct PrimalOp32 {
   __device__ const float* gsrc(int) const { return y; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
-    float c, l, u, x, tau;
+    float c, l, u, x, xl, tau;
     double sx;
   };
   __device__ Pre prefetch(int j) const {
-    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], (float)S->tau, w.sum_x[j]};
+    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.xlo[j], (float)S->tau, w.sum_x[j]};
   }
   __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
     const float g = (float)((double)p.c - a.value());
-    const float xn = clamp_f(fmaf(-p.tau, g, p.x), p.l, p.u);
-    w.xbar[j] = 2.0f * xn - p.x;
-    w.sum_x[j] = p.sx + (double)xn;
-    w.x[j] = xn;
+    float xh = p.x, xl = p.xl;
+    ff_axpy(xh, xl, -p.tau, g);
+    // projection onto [l, u] of the pair (a clamped value carries no low part)
+    const float xc = clamp_f(xh, p.l, p.u);
+    if (xc != xh || (xh == p.l && xl < 0.0f) || (xh == p.u && xl > 0.0f)) {
+      xh = xc;
+      xl = 0.0f;
+    }
+    w.xbar[j] = 2.0f * xh - p.x;
+    w.sum_x[j] = p.sx + ((double)xh + (double)xl);
+    w.x[j] = xh;
+    w.xlo[j] = xl;
   }
 };
 
@@ -1032,19 +1062,25 @@ struct DualOp32 {
   __device__ const float* gsrc(int) const { return xbar; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
-    float b, y, sigma;
+    float b, y, yl, sigma;
     bool ge;
     double sy;
   };
   __device__ Pre prefetch(int i) const {
-    return Pre{md.bhat[i], w.y[i], (float)S->sigma, md.ge[i] != 0, w.sum_y[i]};
+    return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, md.ge[i] != 0, w.sum_y[i]};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     const float r = (float)((double)p.b - a.value());
-    float yn = fmaf(p.sigma, r, p.y);
-    if (p.ge && __float_as_int(yn) < 0) yn = 0.0f;  // y >= 0 on '>' rows (sign bit test)
-    w.sum_y[i] = p.sy + (double)yn;
-    w.y[i] = yn;
+    float yh = p.y, yl = p.yl;
+    ff_axpy(yh, yl, p.sigma, r);
+    // y >= 0 on '>' rows: a negative pair projects to (0, 0)
+    if (p.ge && (yh < 0.0f || (yh == 0.0f && yl < 0.0f))) {
+      yh = 0.0f;
+      yl = 0.0f;
+    }
+    w.sum_y[i] = p.sy + ((double)yh + (double)yl);
+    w.y[i] = yh;
+    w.ylo[i] = yl;
   }
 };
 

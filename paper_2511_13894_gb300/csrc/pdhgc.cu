@@ -160,6 +160,8 @@ struct Iter32 {
   float* x;
   float* xbar;
   float* y;
+  float* xlo;  // low parts of the float-float iterates
+  float* ylo;
 };
 
 __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
@@ -171,27 +173,33 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
     w.x_r[i] = x0;
     w.sum_x[i] = 0.0;
     if (w32.x) {
-      w32.x[i] = (float)x0;
-      w32.xbar[i] = (float)x0;
+      const float h = (float)x0;
+      w32.x[i] = h;
+      w32.xlo[i] = (float)(x0 - (double)h);
+      w32.xbar[i] = h;
     }
   }
   if (i < m) {
     w.y[i] = 0.0;
     w.y_r[i] = 0.0;
     w.sum_y[i] = 0.0;
-    if (w32.y) w32.y[i] = 0.0f;
+    if (w32.y) {
+      w32.y[i] = 0.0f;
+      w32.ylo[i] = 0.0f;
+    }
   }
 }
 
 // FP32 bulk: FP64 copies of the current iterates for the FP64 evaluation; x is
 // clamped to the FP64 bounds (an FP32-rounded bound may lie an ulp outside)
 __global__ void k_to64(const Scalars* S, int n, int m, const float* __restrict__ x32, const float* __restrict__ y32,
+                       const float* __restrict__ xlo, const float* __restrict__ ylo,
                        const double* __restrict__ lhat, const double* __restrict__ uhat, double* __restrict__ x,
                        double* __restrict__ y) {
   if (S->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = fmin(fmax((double)x32[i], lhat[i]), uhat[i]);
-  if (i < m) y[i] = (double)y32[i];
+  if (i < n) x[i] = fmin(fmax((double)x32[i] + (double)xlo[i], lhat[i]), uhat[i]);
+  if (i < m) y[i] = (double)y32[i] + (double)ylo[i];
 }
 
 // FP64 -> FP32 copy
@@ -309,7 +317,11 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.x[i] = xn;
     w.x_r[i] = xn;
     w.sum_x[i] = 0.0;
-    if (w32.x && rt == 2) w32.x[i] = (float)xn;
+    if (w32.x && rt == 2) {
+      const float h = (float)xn;
+      w32.x[i] = h;
+      w32.xlo[i] = (float)(xn - (double)h);
+    }
     if (rr.rx) {
       const size_t slot = (size_t)(S->restarts % 8) * (size_t)n;
       rr.rx[slot + i] = (float)xn;
@@ -321,7 +333,11 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.y[i] = yn;
     w.y_r[i] = yn;
     w.sum_y[i] = 0.0;
-    if (w32.y && rt == 2) w32.y[i] = (float)yn;
+    if (w32.y && rt == 2) {
+      const float h = (float)yn;
+      w32.y[i] = h;
+      w32.ylo[i] = (float)(yn - (double)h);
+    }
   }
 }
 
@@ -349,10 +365,16 @@ __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo
   if (yo && i < m) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
 }
 
+// Section 3: a '>' row whose dual is non-trivial becomes '='.  ax (optional,
+// the row_rule = 1 option): A_hat x1; such a row then stays '>' unless it is
+// active at x1 (slack (A_hat x1)_i / D_r,i - b_i <= eps_abs)
 __global__ void k_corner_rows(int m, const int8_t* ge, const double* Dr, const double* y1, double eps_abs,
-                              int8_t* ge_c) {
+                              const double* ax, const double* b_int, int8_t* ge_c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) ge_c[i] = (ge[i] && !(fabs(Dr[i] * y1[i]) > eps_abs)) ? 1 : 0;
+  if (i >= m) return;
+  bool to_eq = ge[i] && fabs(Dr[i] * y1[i]) > eps_abs;
+  if (to_eq && ax) to_eq = ax[i] / Dr[i] - b_int[i] <= eps_abs;
+  ge_c[i] = (ge[i] && !to_eq) ? 1 : 0;
 }
 
 __global__ void k_report_final(const double* __restrict__ pR, int ntA, const double* __restrict__ pC, int ntT,
@@ -604,6 +626,8 @@ int ensure_fp32(pdhgc_lp* lp) {
   RET(lp->alloc(&lp->it32.x, n));
   RET(lp->alloc(&lp->it32.xbar, n));
   RET(lp->alloc(&lp->it32.y, m));
+  RET(lp->alloc(&lp->it32.xlo, n));
+  RET(lp->alloc(&lp->it32.ylo, m));
   RET(lp->alloc(&lp->chat32, n));
   RET(lp->alloc(&lp->lhat32, n));
   RET(lp->alloc(&lp->uhat32, n));
@@ -700,8 +724,9 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
-  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr};
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y};
+  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr, nullptr, nullptr};
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y, lp->it32.xlo,
+                       lp->it32.ylo};
   k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
   lp->launches += 2;
@@ -750,7 +775,8 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
     }
   }
   if (rc == PDHGC_OK && fp32) {
-    k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, md.lhat, md.uhat, lp->it.x, lp->it.y);
+    k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, lp->it32.xlo, lp->it32.ylo, md.lhat, md.uhat,
+                                lp->it.x, lp->it.y);
     lp->launches++;
   }
   if (rc == PDHGC_OK) {
@@ -894,7 +920,8 @@ int setup_mat(pdhgc_lp* lp, pdhgc_lp::Mat& M, const Csr& C, cudaStream_t st) {
 
 int check_corner_params(const pdhgc_corner_params& cp) {
   if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
-      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1))
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
+      (cp.row_rule != 0 && cp.row_rule != 1))
     return set_err(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
   return PDHGC_OK;
 }
@@ -909,7 +936,16 @@ int corner_build(pdhgc_lp* lp, const pdhgc_corner_params& cp, int8_t* fixed) {
                    CornerColsOp{lp->y1, lp->x1, lp->col_perm, md, lp->lhat_c, lp->uhat_c, lp->chat_c, cp.eps_abs,
                                 cp.obj_scale, (unsigned long long)cp.obj_seed, fixed},
                    lp->pT, st));
-  k_corner_rows<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->ge, lp->Dr, lp->y1, cp.eps_abs, lp->ge_c);
+  const double* ax = nullptr;
+  if (cp.row_rule == 1) {
+    k_fill<<<grid_for(lp->m), 256, 0, st>>>(lp->tmp_m, lp->m, 0.0);  // A = 0 leaves the pass empty
+    lp->launches++;
+    CKL();
+    RET(launch_tiles(lp, false, true, SpmvOp<false>{lp->S, lp->x1, lp->tmp_m}, nullptr, st));
+    ax = lp->tmp_m;
+  }
+  k_corner_rows<<<grid_for(lp->m), 256, 0, st>>>(lp->m, lp->ge, lp->Dr, lp->y1, cp.eps_abs, ax, lp->b_int,
+                                                 lp->ge_c);
   lp->launches++;
   CKL();
   k_fold2<<<1, 256, 0, st>>>(lp->pT, lp->ntT, lp->scratch + 8);
@@ -1674,7 +1710,8 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
   const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y};
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y, lp->it32.xlo,
+                       lp->it32.ylo};
   // the replay must not stop on the phase's done flag or iteration limit
   Scalars S;
   CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));

@@ -236,3 +236,30 @@ def test_fp32_bulk_corner_phase():
     rep = g.corner_phase(obj_seed=11)
     assert rep["status_name"] == "CORNER_DONE"
     assert rep["rel_p"] <= 1e-6 * (1 + 1e-9)
+
+
+def test_fp32_bulk_converges_where_small_steps_underflow():
+    # LP 199 of the 512-LP batch: its primal weight falls to ~1e-3, so the dual
+    # step sigma * r drops below an FP32 unit of y; the float-float iterates
+    # keep those steps (plain FP32 iterates stalled at rel-KKT 1e-1 here)
+    lp = lpgen.batch_lp(199)
+    g = P.lp_from_dict(lp)
+    r64 = g.solve()
+    r32 = g.solve(precision=P.FP32_BULK, max_iters=200_000)
+    assert r64["status_name"] == "OPTIMAL"
+    assert r32["status_name"] == "OPTIMAL" and r32["rel_kkt"] <= 1e-6, (r32["status_name"], r32["rel_kkt"])
+    assert abs(r32["pobj"] - r64["pobj"]) <= 1e-5 * (1 + abs(r64["pobj"]))
+
+
+def test_corner_row_rule_option_matches_oracle():
+    # the option that keeps rows inactive at the phase-1 point as inequalities
+    lp = _lp_cases()["bounded_ineq"]()
+    ref1 = oracle.solve(lp)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=11, row_rule=1))
+    g = P.lp_from_dict(lp)
+    g.solve()
+    rep = g.corner_phase(obj_seed=11, row_rule=1)
+    assert rep["status"] == refc["status"] and rep["iters"] == refc["iters"]
+    x, _, _ = g.get_solution(P.CORNER)
+    xo, _, _ = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+    assert rel_err(x, xo) <= 1e-7

@@ -436,3 +436,22 @@ def test_corner_reaches_the_random_objective_vertex(seed):
     assert np.max(np.abs(xc - v_best)) <= 1e-4
     met = oracle.corner_metrics(r1["model"], xc, *oracle.unscale(r1["model"], r1["x_hat"], r1["y_hat"])[1:])
     assert met["primal_push_est"] == 0
+
+
+def test_corner_row_rule_option_keeps_inactive_rows():
+    # row_rule = 1 (an option, not the paper's rule): of the rows Section 3
+    # turns into equalities, those with a positive slack at the phase-1 point
+    # stay inequalities, and the corner phase still regains the tolerance
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(6), 6)
+    r1 = oracle.solve(lp)
+    model = r1["model"]
+    x1, y1, _ = oracle.unscale(model, r1["x_hat"], r1["y_hat"])
+    cm0, _ = oracle.corner_model(model, r1["x_hat"], r1["y_hat"], dict(oracle.CORNER_DEFAULTS))
+    cm1, _ = oracle.corner_model(model, r1["x_hat"], r1["y_hat"], dict(oracle.CORNER_DEFAULTS, row_rule=1))
+    eq0 = model.ge & ~cm0.ge
+    eq1 = model.ge & ~cm1.ge
+    assert np.all(eq1 <= eq0)
+    slack = model.A_int @ x1 - model.b_int
+    assert np.array_equal(eq1, eq0 & (slack <= 1e-6))
+    rc = oracle.corner_phase(r1, dict(obj_seed=3, row_rule=1))
+    assert rc["status"] == oracle.CORNER_DONE
