@@ -497,6 +497,23 @@ int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, c
 int64_t pdhgc_guide_kernel_launches(const pdhgc_guide* g);
 
 /*
+ * pdhgc_get_state / pdhgc_set_state — checkpoint and restore of a handle's
+ * results (the paper has no counterpart; a service needs it to resume).  The
+ * state is a host byte buffer holding the parameters, the phase-1 and corner
+ * reports, the scaling factors, the phase-1 point (x1, y1), the corner x and
+ * the phase-1 restart history.  get_state with buf = NULL writes the size to
+ * *bytes; with a buffer smaller than that it returns BUFFER (size written
+ * back).  set_state restores into a handle created from the same LP: it
+ * recomputes the scaling and step size (deterministic) and returns INVALID_ARG
+ * when the shape, the format or the recomputed scaling factors differ from the
+ * saved ones.  Afterwards get_solution, kkt_report, corner_phase and the
+ * guidance calls behave as on the original handle.  The state is not portable
+ * across builds that change the scaling arithmetic.
+ */
+int pdhgc_get_state(pdhgc_lp* lp, void* buf, size_t* bytes);
+int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes);
+
+/*
  * pdhgc_kernel_launches — number of CUDA kernels this handle has launched
  * so far (kernels inside the solve graph counted once per execution).
  */

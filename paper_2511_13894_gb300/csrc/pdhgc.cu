@@ -1571,6 +1571,117 @@ int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, c
   return PDHGC_OK;
 }
 
+// ---- checkpoint / restore of a handle's results ----------------------------
+
+namespace {
+struct StateHeader {
+  char magic[8];  // "PDHGCST1"
+  int32_t version, m, n, pad;
+  int64_t nnz;
+  int32_t have_phase1, have_corner;
+  pdhgc_params params;
+  pdhgc_corner_params cp_last;
+  pdhgc_report rep1, repc;
+};
+constexpr char kStateMagic[8] = {'P', 'D', 'H', 'G', 'C', 'S', 'T', '1'};
+size_t state_bytes(int m, int n) {
+  return sizeof(StateHeader) + 8 * (2 * (size_t)m + 3 * (size_t)n) + 4 * 16 * (size_t)n;
+}
+}  // namespace
+
+int pdhgc_get_state(pdhgc_lp* lp, void* buf, size_t* bytes) {
+  if (!lp || !bytes) return set_err(PDHGC_ERR_INVALID_ARG, "lp or bytes is NULL");
+  const int m = lp->m, n = lp->n;
+  const size_t need = state_bytes(m, n);
+  if (!buf) {
+    *bytes = need;
+    return PDHGC_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return set_err(PDHGC_ERR_BUFFER, "state buffer too small: need " + std::to_string(need) + " bytes");
+  }
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.m = m;
+  h.n = n;
+  h.nnz = lp->nnz;
+  h.have_phase1 = lp->have_phase1 ? 1 : 0;
+  h.have_corner = lp->have_corner ? 1 : 0;
+  h.params = lp->params;
+  h.cp_last = lp->cp_last;
+  h.rep1 = lp->rep1;
+  h.repc = lp->repc;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  cudaStream_t st = lp->stream;
+  struct Part {
+    const void* src;
+    size_t bytes;
+  } parts[] = {{lp->Dr, 8 * (size_t)m},      {lp->Dc, 8 * (size_t)n},         {lp->x1, 8 * (size_t)n},
+               {lp->y1, 8 * (size_t)m},      {lp->xc, 8 * (size_t)n},         {lp->ring_x, 32 * (size_t)n},
+               {lp->ring_z, 32 * (size_t)n}};
+  for (const Part& q : parts) {
+    CK(cudaMemcpyAsync(o, q.src, q.bytes, cudaMemcpyDeviceToHost, st));
+    o += q.bytes;
+  }
+  CK(cudaStreamSynchronize(st));
+  *bytes = need;
+  return PDHGC_OK;
+}
+
+int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes) {
+  if (!lp || !buf) return set_err(PDHGC_ERR_INVALID_ARG, "lp or buf is NULL");
+  const int m = lp->m, n = lp->n;
+  if (bytes < sizeof(StateHeader)) return set_err(PDHGC_ERR_INVALID_ARG, "state buffer too short");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    return set_err(PDHGC_ERR_INVALID_ARG, "not a pdhgc state (magic or version)");
+  if (h.m != m || h.n != n || h.nnz != lp->nnz || bytes != state_bytes(m, n))
+    return set_err(PDHGC_ERR_INVALID_ARG, "state was taken from an LP of another shape");
+  RET(check_params(&h.params));
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(StateHeader);
+  const double* Dr_s = reinterpret_cast<const double*>(in);
+  const double* Dc_s = Dr_s + m;
+  cudaStream_t st = lp->stream;
+  lp->have_phase1 = false;
+  lp->have_corner = false;
+  // the scaling, step size and FP32 copies are recomputed (deterministic) and
+  // must reproduce the saved factors bit for bit
+  RET(setup_scaling(lp, h.params));
+  if (h.params.precision == PDHGC_FP32_BULK) {
+    RET(ensure_fp32(lp));
+    RET(convert_fp32(lp, st));
+  }
+  std::vector<double> Dr(m), Dc(n);
+  CK(cudaMemcpyAsync(Dr.data(), lp->Dr, 8 * (size_t)m, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(Dc.data(), lp->Dc, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (std::memcmp(Dr.data(), Dr_s, 8 * (size_t)m) != 0 || std::memcmp(Dc.data(), Dc_s, 8 * (size_t)n) != 0)
+    return set_err(PDHGC_ERR_INVALID_ARG, "state was taken from another LP (scaling factors differ)");
+  const unsigned char* o = in + 8 * ((size_t)m + n);
+  struct Part {
+    void* dst;
+    size_t bytes;
+  } parts[] = {{lp->x1, 8 * (size_t)n}, {lp->y1, 8 * (size_t)m}, {lp->xc, 8 * (size_t)n},
+               {lp->ring_x, 32 * (size_t)n}, {lp->ring_z, 32 * (size_t)n}};
+  for (const Part& q : parts) {
+    CK(cudaMemcpyAsync(q.dst, o, q.bytes, cudaMemcpyHostToDevice, st));
+    o += q.bytes;
+  }
+  CK(cudaStreamSynchronize(st));
+  lp->params = h.params;
+  lp->cp_last = h.cp_last;
+  lp->rep1 = h.rep1;
+  lp->repc = h.repc;
+  lp->have_phase1 = h.have_phase1 != 0;
+  lp->have_corner = h.have_corner != 0 && lp->have_phase1;
+  return PDHGC_OK;
+}
+
 int pdhgc_kkt_report(pdhgc_lp* lp, int which, pdhgc_report* out) {
   if (!lp || !out || (which != PDHGC_PHASE1 && which != PDHGC_CORNER))
     return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");

@@ -123,6 +123,8 @@ _sig = {
     "pdhgc_batch_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_batch_set_handoff": (C.c_int, [_vp, C.c_int32, C.c_int64]),
     "pdhgc_batch_handed_off": (C.c_int32, [_vp, C.c_int32, C.c_int]),
+    "pdhgc_get_state": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t)]),
+    "pdhgc_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "pdhgc_default_guide_params": (None, [C.POINTER(GuideParams)]),
     "pdhgc_guide_create": (C.c_int, [C.POINTER(_vp), C.c_uint64, _vp]),
     "pdhgc_guide_destroy": (None, [_vp]),
@@ -259,6 +261,20 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    # -- checkpoint ----------------------------------------------------------------
+    def get_state(self) -> bytes:
+        """pdhgc_get_state: the handle's results as a byte string."""
+        n = C.c_size_t(0)
+        _check(lib.pdhgc_get_state(self._h, None, C.byref(n)), "pdhgc_get_state")
+        buf = C.create_string_buffer(n.value)
+        _check(lib.pdhgc_get_state(self._h, buf, C.byref(n)), "pdhgc_get_state")
+        return buf.raw[:n.value]
+
+    def set_state(self, state: bytes):
+        """pdhgc_set_state: restore results taken from a handle of the same LP."""
+        buf = C.create_string_buffer(state, len(state))
+        _check(lib.pdhgc_set_state(self._h, buf, len(state)), "pdhgc_set_state")
 
     # -- learned corner guidance ------------------------------------------------
     def guide_features(self, params: CornerParams | None = None, **kw):

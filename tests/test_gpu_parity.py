@@ -263,3 +263,27 @@ def test_corner_row_rule_option_matches_oracle():
     x, _, _ = g.get_solution(P.CORNER)
     xo, _, _ = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
     assert rel_err(x, xo) <= 1e-7
+
+
+def test_checkpoint_restore_resumes_at_the_corner_phase():
+    lp = _lp_cases()["bounded_ineq"]()
+    g = P.lp_from_dict(lp)
+    r1 = g.solve()
+    state = g.get_state()
+    c_orig = g.corner_phase(obj_seed=5)
+    x_orig, _, _ = g.get_solution(P.CORNER)
+    h = P.lp_from_dict(lp)
+    h.set_state(state)
+    assert h.kkt_report(P.PHASE1)["rel_kkt"] == r1["rel_kkt"]
+    x1a, y1a, _ = g.get_solution(P.PHASE1)
+    x1b, y1b, _ = h.get_solution(P.PHASE1)
+    assert np.array_equal(x1a, x1b) and np.array_equal(y1a, y1b)
+    c_rest = h.corner_phase(obj_seed=5)
+    assert c_rest["iters"] == c_orig["iters"]
+    x_rest, _, _ = h.get_solution(P.CORNER)
+    assert np.array_equal(x_rest, x_orig)
+    # a state of another LP is refused
+    other = P.lp_from_dict(lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(4), 4))
+    with pytest.raises(P.PdhgcError) as e:
+        other.set_state(state)
+    assert e.value.code == -1
