@@ -104,8 +104,9 @@ typedef struct pdhgc_corner_params {
     int32_t  stop_rule;    /* 0: Section 3.1 primal rule; 1: full relative KKT (a testing aid) */
     int32_t  row_rule;     /* 0 (default): Section 3's rule, an inequality row whose dual is non-trivial
                               (|y_i| > eps_abs) becomes '='; 1 (an option, not the paper's): only when the
-                              row is also active at the phase-1 point (slack a_i x - b_i <= eps_abs in the
-                              '>' form), so that the start point stays primal feasible */
+                              row also looks active at the phase-1 point, its slack (a_i x - b_i in the '>'
+                              form) no larger than |y_i|, so that rows the phase-1 point is clearly off
+                              keep their sense */
 } pdhgc_corner_params;
 
 /*

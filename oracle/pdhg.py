@@ -538,10 +538,11 @@ def corner_model(model: Model, x_hat1, y_hat1, cp, hold=None):
         cm.u = np.where(held, nb * model.Dc, cm.u)
     to_eq = model.ge & (np.abs(y1) > cp["eps_abs"])
     if cp.get("row_rule", 0) == 1:
-        # option (not the paper's): keep a row '>' when the phase-1 point is
-        # off it, so that the start point stays primal feasible
+        # option (not the paper's): a row turns '=' only when it also looks
+        # active at the phase-1 point, its slack no larger than its dual
+        # (complementarity: an inactive row has slack >> |y_i|)
         x1 = model.Dc * x_hat1
-        to_eq &= (model.A_int @ x1 - model.b_int) <= cp["eps_abs"]
+        to_eq &= (model.A_int @ x1 - model.b_int) <= np.abs(y1)
     cm.ge = model.ge & ~to_eq
     cm.set_objective(cp["obj_scale"] * splitmix64_uniform(cp["obj_seed"], model.n))
     return cm, dict(fixed_upper=int(fix_up.sum()), fixed_lower=int(fix_lo.sum()),

@@ -648,8 +648,9 @@ struct LpSolver {
       __syncthreads();
     }
     for (int i = threadIdx.x; i < d.m; i += BT) {
-      bool to_eq = d.ge[i] && fabs(d.Dr[i] * d.y1[i]) > bp.eps_abs;
-      if (to_eq && bp.row_rule == 1) to_eq = d.pi_u[i] / d.Dr[i] - d.b_int[i] <= bp.eps_abs;
+      const double yu = fabs(d.Dr[i] * d.y1[i]);
+      bool to_eq = d.ge[i] && yu > bp.eps_abs;
+      if (to_eq && bp.row_rule == 1) to_eq = d.pi_u[i] / d.Dr[i] - d.b_int[i] <= yu;
       d.ge_c[i] = (d.ge[i] && !to_eq) ? 1 : 0;
     }
     if (kF32)

@@ -366,14 +366,15 @@ __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo
 }
 
 // Section 3: a '>' row whose dual is non-trivial becomes '='.  ax (optional,
-// the row_rule = 1 option): A_hat x1; such a row then stays '>' unless it is
-// active at x1 (slack (A_hat x1)_i / D_r,i - b_i <= eps_abs)
+// the row_rule = 1 option): A_hat x1; such a row then stays '>' unless it also
+// looks active at x1, its slack (A_hat x1)_i / D_r,i - b_i no larger than |y_i|
 __global__ void k_corner_rows(int m, const int8_t* ge, const double* Dr, const double* y1, double eps_abs,
                               const double* ax, const double* b_int, int8_t* ge_c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  bool to_eq = ge[i] && fabs(Dr[i] * y1[i]) > eps_abs;
-  if (to_eq && ax) to_eq = ax[i] / Dr[i] - b_int[i] <= eps_abs;
+  const double yu = fabs(Dr[i] * y1[i]);
+  bool to_eq = ge[i] && yu > eps_abs;
+  if (to_eq && ax) to_eq = ax[i] / Dr[i] - b_int[i] <= yu;
   ge_c[i] = (ge[i] && !to_eq) ? 1 : 0;
 }
 

@@ -46,6 +46,45 @@ def test_default_params_match_the_paper_and_readings(lib):
     assert (p.beta_suff, p.beta_nec, p.beta_art, p.theta, p.eta_factor) == (0.2, 0.8, 0.36, 0.5, 0.998)
     cp = P.default_corner_params()
     assert cp.eps_abs == 1e-6 and cp.min_iters == 100 and cp.obj_scale == 1.0
+    assert cp.stop_rule == 0 and cp.row_rule == 0  # the Section 3.1 stop and Section 3 row rules
+    gp = P.GuideParams()
+    P.lib.pdhgc_default_guide_params(P.C.byref(gp))
+    assert gp.threshold == 0.9 and gp.fallback == 1 and gp.guided_max_iters == 0
+
+
+def test_ctypes_mirrors_match_the_c_structs(tmp_path):
+    # sizes and field offsets of every struct the binding mirrors, taken from
+    # the header by a C compiler
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2511_13894_gb300 import pdhgc as P
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pdhgc_params": P.Params, "pdhgc_corner_params": P.CornerParams, "pdhgc_report": P.Report,
+               "pdhgc_guide_params": P.GuideParams, "pdhgc_guide_report": P.GuideReport}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhgc.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-I", include, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        parts = line.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def _expect(code, **override):

@@ -108,3 +108,20 @@ def test_batch_tail_handoff_matches_oracle():
         x, _ = B.get_solution(k, P.CORNER)
         xo, _, _ = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
         assert rel_err(x, xo) <= 1e-7, k
+
+
+def test_batch_corner_row_rule_matches_the_single_lp_path():
+    # the row_rule = 1 option inside the batched kernel equals the single-LP path's
+    lps = _mixed_lps()[:3]
+    B = P.Batch(lps)
+    B.set_handoff(0)
+    B.solve()
+    creps = B.corner_phase(obj_seed=7, row_rule=1)
+    for k, lp in enumerate(lps):
+        g = P.lp_from_dict(lp)
+        g.solve()
+        rc = g.corner_phase(obj_seed=7, row_rule=1)
+        assert creps[k]["status"] == rc["status"] and creps[k]["iters"] == rc["iters"], k
+        xb, _ = B.get_solution(k, P.CORNER)
+        xs, _, _ = g.get_solution(P.CORNER)
+        assert rel_err(xb, xs) <= 1e-8, k

@@ -322,3 +322,25 @@ def test_dataset_rows_and_labels():
     with pytest.raises(P.PdhgcError) as e:
         g.dataset_append(small, torch.zeros(3, dtype=torch.uint8, device="cuda"), 0)
     assert e.value.code == -11
+
+
+def test_guided_corner_in_fp32_bulk_holds_exactly():
+    # FP32-bulk phase 1 and a held corner phase: held columns end exactly at
+    # their bound and the Section 3.1 rule is met
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(9), 9)
+    g = P.lp_from_dict(lp)
+    g.solve(precision=P.FP32_BULK)
+    _, elig = g.guide_features(obj_seed=4)
+    E = elig.cpu().numpy().astype(bool)
+    x1, _, _ = g.get_solution(P.PHASE1)
+    lb, ub = lp["lb"], lp["ub"]
+    dl = np.where(np.isfinite(lb), x1 - lb, np.inf)
+    du = np.where(np.isfinite(ub), ub - x1, np.inf)
+    nb = np.where(dl <= du, lb, ub)
+    hold = np.zeros(lp["n"], dtype=bool)
+    hold[np.argsort(np.where(E, np.minimum(dl, du), np.inf), kind="stable")[:12]] = True
+    rep, grep = g.corner_phase_guided(hold=hold, fallback=False, obj_seed=4)
+    assert grep["held"] == 12
+    assert rep["status_name"] == "CORNER_DONE" and rep["rel_p"] <= 1e-6 * (1 + 1e-9)
+    x, _, _ = g.get_solution(P.CORNER)
+    assert np.max(np.abs(x[hold] - nb[hold])) <= 1e-12 * (1 + np.max(np.abs(nb[hold])))

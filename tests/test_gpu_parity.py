@@ -287,3 +287,18 @@ def test_checkpoint_restore_resumes_at_the_corner_phase():
     with pytest.raises(P.PdhgcError) as e:
         other.set_state(state)
     assert e.value.code == -1
+
+
+def test_checkpoint_restore_fp32_bulk():
+    lp = _lp_cases()["power_law_skewed"]()
+    g = P.lp_from_dict(lp)
+    g.solve(precision=P.FP32_BULK)
+    state = g.get_state()
+    c_orig = g.corner_phase(obj_seed=2, max_iters=20000)
+    h = P.lp_from_dict(lp)
+    h.set_state(state)
+    c_rest = h.corner_phase(obj_seed=2, max_iters=20000)
+    assert c_rest["iters"] == c_orig["iters"] and c_rest["status"] == c_orig["status"]
+    xa, _, _ = g.get_solution(P.CORNER)
+    xb, _, _ = h.get_solution(P.CORNER)
+    assert np.array_equal(xa, xb)

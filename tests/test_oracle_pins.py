@@ -440,8 +440,9 @@ def test_corner_reaches_the_random_objective_vertex(seed):
 
 def test_corner_row_rule_option_keeps_inactive_rows():
     # row_rule = 1 (an option, not the paper's rule): of the rows Section 3
-    # turns into equalities, those with a positive slack at the phase-1 point
-    # stay inequalities, and the corner phase still regains the tolerance
+    # turns into equalities, those whose slack at the phase-1 point exceeds
+    # their dual stay inequalities, and the corner phase still regains the
+    # tolerance
     lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(6), 6)
     r1 = oracle.solve(lp)
     model = r1["model"]
@@ -452,6 +453,6 @@ def test_corner_row_rule_option_keeps_inactive_rows():
     eq1 = model.ge & ~cm1.ge
     assert np.all(eq1 <= eq0)
     slack = model.A_int @ x1 - model.b_int
-    assert np.array_equal(eq1, eq0 & (slack <= 1e-6))
+    assert np.array_equal(eq1, eq0 & (slack <= np.abs(y1)))
     rc = oracle.corner_phase(r1, dict(obj_seed=3, row_rule=1))
     assert rc["status"] == oracle.CORNER_DONE
