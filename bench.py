@@ -424,7 +424,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"lp-split x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
             "tail_handoff": {"phase1_lps": h1, "corner_lps": hc,
-                             "rule": "once the queue is empty and <= 16 LPs run, an LP past 4096 iterations "
+                             "rule": "once the queue is empty and <= 8 LPs run, an LP past 8192 iterations "
                                      "of its phase finishes on the single-LP path, concurrently"},
             "phase1": {"optimal": done, "lps": len(r1), "iters_sum": sum(r["iters"] for r in r1),
                        "iters_max": max(r["iters"] for r in r1),

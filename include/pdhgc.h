@@ -345,7 +345,7 @@ int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tun
  * concurrently on their own streams.  A handed-off LP restarts its phase from
  * the phase's start point on that path; a corner phase handed off there
  * starts from that path's own phase 1 of the LP.  Its report and result are
- * the single-LP path's.  Defaults: 16, 4096; max_running = 0 disables.
+ * the single-LP path's.  Defaults: 8, 8192; max_running = 0 disables.
  */
 int pdhgc_batch_set_handoff(pdhgc_batch* batch, int32_t max_running, int64_t min_iters);
 
@@ -493,6 +493,15 @@ int pdhgc_guide_dataset_append(pdhgc_lp* lp, uint16_t* feat, uint8_t* labels, in
 int pdhgc_corner_phase_guided(pdhgc_lp* lp, const pdhgc_corner_params* params, const pdhgc_guide_params* gparams,
                               pdhgc_guide* g, const uint8_t* hold, int hold_on_device, pdhgc_report* out,
                               pdhgc_guide_report* gout);
+
+/*
+ * pdhgc_guide_set_wait_limit — polls each tensor-core completion wait of the
+ * inference kernel makes before it gives up (default 2^24; 0: give up at
+ * once).  A wait that gives up makes the call return DEVICE; the kernel
+ * still lets the pending product land (full limit) and frees its tensor
+ * memory, so the context stays usable.  For failure-path tests.
+ */
+int pdhgc_guide_set_wait_limit(pdhgc_guide* g, int64_t polls);
 
 /* pdhgc_guide_kernel_launches — CUDA kernels launched by this network so far. */
 int64_t pdhgc_guide_kernel_launches(const pdhgc_guide* g);

@@ -251,9 +251,9 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// bounded wait for phase `parity` of the mbarrier; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long i = 0; i < kTcWaitLimit; ++i) {
+// bounded wait for phase `parity` of the mbarrier; false when `limit` polls ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kTcRows, 1) k_guide_forward_tc(const GuideBf16
                                                                  const float* __restrict__ w,
                                                                  const __nv_bfloat16* __restrict__ feat,
                                                                  long long rows, float* __restrict__ p,
-                                                                 int* __restrict__ err) {
+                                                                 int* __restrict__ err, long long wait_limit) {
   extern __shared__ __align__(128) unsigned char tc_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(tc_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kTcRows, 1) k_guide_forward_tc(const GuideBf16
                   umma_desc(w1_addr + ks * 256, 128, (kGFeat / 8) * 128), kIdesc, ks > 0 ? 1u : 0u);
       umma_commit(mbar);
     }
-    ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;  // the same decision in every thread
+    ok = __syncthreads_and(mbar_wait(mbar, parity, wait_limit)) != 0;  // the same decision in every thread
     if (!ok) break;
     parity ^= 1u;
     tc_fence_after();
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kTcRows, 1) k_guide_forward_tc(const GuideBf16
                   umma_desc(w2_addr + ks * 256, 128, (kGHid / 8) * 128), kIdesc, ks > 0 ? 1u : 0u);
       umma_commit(mbar);
     }
-    ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;
+    ok = __syncthreads_and(mbar_wait(mbar, parity, wait_limit)) != 0;
     if (!ok) break;
     parity ^= 1u;
     tc_fence_after();
@@ -425,8 +425,9 @@ __global__ void __launch_bounds__(kTcRows, 1) k_guide_forward_tc(const GuideBf16
   }
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
-    // the pending MMA may still be in flight: give it the same bounded time to land
-    mbar_wait(mbar, parity);
+    // the pending MMA may still be in flight: give it the full bounded time to
+    // land before the tensor memory is freed
+    mbar_wait(mbar, parity, kTcWaitLimit);
   }
   tc_fence_before();
   __syncthreads();
@@ -777,7 +778,8 @@ int guide_forward(pdhgc_guide* g, const __nv_bfloat16* feat, int64_t rows, float
   // tcgen05: one CTA per SM at most, persistent over 128-row tiles
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
   const long long grid = tiles < g->max_ctas ? tiles : g->max_ctas;
-  k_guide_forward_tc<<<(unsigned)grid, kTcRows, sizeof(TcSmem), st>>>(g->wb, g->w, feat, (long long)rows, p, g->err);
+  k_guide_forward_tc<<<(unsigned)grid, kTcRows, sizeof(TcSmem), st>>>(g->wb, g->w, feat, (long long)rows, p, g->err,
+                                                                      g->tc_wait_limit);
 #else
   const long long tiles = (rows + 15) / 16;
   long long grid = (tiles + kGWarps - 1) / kGWarps;
@@ -1004,5 +1006,11 @@ int pdhgc_guide_train(pdhgc_guide* g, const uint16_t* feat, const uint8_t* label
 }
 
 int64_t pdhgc_guide_kernel_launches(const pdhgc_guide* g) { return g ? g->launches : 0; }
+
+int pdhgc_guide_set_wait_limit(pdhgc_guide* g, int64_t polls) {
+  if (!g || polls < 0) return set_error_detail(PDHGC_ERR_INVALID_ARG, "g is NULL or polls < 0");
+  g->tc_wait_limit = polls > 0 ? polls : 0;
+  return PDHGC_OK;
+}
 
 }  // extern "C"

@@ -43,6 +43,7 @@ struct pdhgc_guide {
   int max_ctas = 0;
   int32_t* idx = nullptr;     // explicit minibatch indices (gradient check)
   int* err = nullptr;         // set by a kernel whose bounded wait ran out
+  long long tc_wait_limit = 1ll << 24;  // polls of a tensor-core completion wait before it gives up
   int idx_cap = 0;
   int64_t adam_t = 0;         // Adam steps taken
   int64_t launches = 0;

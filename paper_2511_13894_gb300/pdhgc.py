@@ -138,6 +138,7 @@ _sig = {
     "pdhgc_corner_phase_guided": (C.c_int, [_vp, C.POINTER(CornerParams), C.POINTER(GuideParams), _vp, _vp,
                                             C.c_int, C.POINTER(Report), C.POINTER(GuideReport)]),
     "pdhgc_guide_kernel_launches": (C.c_int64, [_vp]),
+    "pdhgc_guide_set_wait_limit": (C.c_int, [_vp, C.c_int64]),
     "pdhgc_strerror": (C.c_char_p, [C.c_int]),
     "pdhgc_last_error_detail": (C.c_char_p, []),
 }
@@ -450,7 +451,7 @@ class Batch:
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_batch_kernel_launches(self._h))
 
-    def set_handoff(self, max_running: int = 16, min_iters: int = 4096):
+    def set_handoff(self, max_running: int = 8, min_iters: int = 8192):
         """pdhgc_batch_set_handoff (max_running = 0 disables the tail handoff)."""
         _check(lib.pdhgc_batch_set_handoff(self._h, int(max_running), int(min_iters)), "pdhgc_batch_set_handoff")
 
@@ -544,6 +545,10 @@ class Guide:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_guide_kernel_launches(self._h))
+
+    def set_wait_limit(self, polls: int):
+        """pdhgc_guide_set_wait_limit (failure-path tests)."""
+        _check(lib.pdhgc_guide_set_wait_limit(self._h, int(polls)), "pdhgc_guide_set_wait_limit")
 
 
 def _device_lp_args(lp: dict, x, y):

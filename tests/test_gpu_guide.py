@@ -344,3 +344,52 @@ def test_guided_corner_in_fp32_bulk_holds_exactly():
     assert rep["status_name"] == "CORNER_DONE" and rep["rel_p"] <= 1e-6 * (1 + 1e-9)
     x, _, _ = g.get_solution(P.CORNER)
     assert np.max(np.abs(x[hold] - nb[hold])) <= 1e-12 * (1 + np.max(np.abs(nb[hold])))
+
+
+def test_tensor_core_wait_that_gives_up_reports_device_error():
+    # failure detection without a fault: the completion waits of the tcgen05
+    # inference kernel give up at once, the call returns DEVICE, and the
+    # context stays usable
+    F, _ = _random_inputs(1000, 7)
+    feat, _ = feat_tensor(F)
+    g = P.Guide(seed=0)
+    g.set_weights(pack(rounded_weights(2)))
+    p_ok = g.infer(feat).cpu().numpy()
+    g.set_wait_limit(0)
+    with pytest.raises(P.PdhgcError) as e:
+        g.infer(feat)
+    assert e.value.code == -10
+    g.set_wait_limit(1 << 24)
+    assert np.array_equal(g.infer(feat).cpu().numpy(), p_ok)
+    assert float(torch.ones(4, device="cuda").sum().item()) == 4.0
+
+
+def test_empty_hold_is_the_plain_corner_phase():
+    lp = lpgen.small_face_lp(13)
+    g = P.lp_from_dict(lp)
+    g.solve()
+    plain = g.corner_phase(obj_seed=6)
+    x_plain, _, _ = g.get_solution(P.CORNER)
+    rep, grep = g.corner_phase_guided(hold=np.zeros(lp["n"], dtype=bool), fallback=False, obj_seed=6)
+    assert grep["held"] == 0 and rep["iters"] == plain["iters"]
+    x, _, _ = g.get_solution(P.CORNER)
+    assert np.array_equal(x, x_plain)
+
+
+def test_free_columns_are_never_eligible():
+    # columns of S made free (l = -inf, u = +inf) keep the constructed optimum
+    # (their reduced cost is 0) and must not be offered for holding
+    lp = lpgen.small_face_lp(14)
+    free = np.nonzero(lp["x_star"] > 0)[0][:6]
+    lp["lb"] = lp["lb"].copy()
+    lp["lb"][free] = -np.inf
+    r1 = oracle.solve(lp)
+    g = P.lp_from_dict(lp)
+    rep = g.solve()
+    assert rep["iters"] == r1["iters"]
+    feat, elig = g.guide_features(obj_seed=2)
+    F, E = oguide.features(r1, dict(obj_seed=2))
+    got = feat_values(feat)[:, :18]
+    assert np.all(np.abs(got - F) <= BF16_REL * np.abs(F) + 1e-30)
+    assert np.array_equal(elig.cpu().numpy().astype(bool), E)
+    assert not E[free].any()
