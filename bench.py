@@ -567,6 +567,15 @@ def main():
         }
         if roofline["fp64"]["frac"] > roofline["frac"]:
             roofline["bound"] = "alu"
+        # the random-gather ceiling: the same number of random loads from a
+        # vector of the gathered length, warm in L2 (pdhgc_probe_gather)
+        g_len = m if dom == "primal" else n
+        g_bytes = 8 if precision == P.FP64 else 4
+        ms_g = P.probe_gather(g_len, nnz, g_bytes, reps=20)
+        roofline["gather"] = {"gathers_per_launch": nnz, "vector_elems": g_len, "elem_bytes": g_bytes,
+                              "ceiling_ms": ms_g, "ceiling_gathers_per_s": nnz / (ms_g * 1e-3),
+                              "achieved_gathers_per_s": nnz / (ms_dom * 1e-3), "frac": ms_g / ms_dom,
+                              "note": "pdhgc_probe_gather: the same count of random loads alone"}
         r1, rc = reps[-1]
         return dict(value=value, total_ms=total_ms, total_iters=total_iters, launches=launches, clocks=clk,
                     roofline=roofline, r1=r1, rc=rc, params=params)

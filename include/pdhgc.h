@@ -530,6 +530,18 @@ int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes);
 int64_t pdhgc_kernel_launches(const pdhgc_lp* lp);
 
 /*
+ * pdhgc_probe_gather — the random-gather ceiling the SpMV passes run against
+ * (a measurement utility; the paper has no counterpart).  Times `reps`
+ * launches of a kernel that makes `count` loads of elem_bytes (4 or 8) at
+ * hashed uniform positions of a device vector of n_vec elements (resident in
+ * L2 after a warm launch), 8 independent loads in flight per thread, and
+ * writes the mean milliseconds per launch.  Allocates and frees the vector.
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t reps, double* ms_out,
+                       void* cuda_stream);
+
+/*
  * pdhgc_profile_iteration — replays `iters` PDHG iterations of the last
  * phase's model as plain launches on the handle's stream, each kernel
  * bracketed by CUDA events, and writes the mean duration in milliseconds of

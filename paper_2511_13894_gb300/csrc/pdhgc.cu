@@ -442,6 +442,29 @@ __global__ void k_unpermute(int len, const int* perm, const double* a, const dou
   out[perm[i]] = v;
 }
 
+// random-gather ceiling: count loads of v[h(i)] with h a multiplicative
+// hash onto [0, n_vec), kGatherProbeBatch independent loads in flight per
+// thread (as the SpMV keeps them); the sum is kept live through `sink`
+constexpr int kGatherProbeBatch = 8;
+template <class T>
+__global__ void k_gather_probe(const T* __restrict__ v, long long n_vec, long long count, double* sink) {
+  const long long stride = (long long)gridDim.x * blockDim.x * kGatherProbeBatch;
+  T acc = T(0);  // summed in the element type: no FP64 work for 4-byte loads
+  for (long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kGatherProbeBatch; i0 < count;
+       i0 += stride) {
+    T g[kGatherProbeBatch];
+#pragma unroll
+    for (int u = 0; u < kGatherProbeBatch; ++u) {
+      const unsigned long long h = (unsigned long long)(i0 + u + 1) * 0x9E3779B97F4A7C15ull;
+      const long long idx = (long long)__umul64hi(h, (unsigned long long)n_vec);
+      g[u] = i0 + u < count ? __ldg(v + idx) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherProbeBatch; ++u) acc += g[u];
+  }
+  if (acc == T(1.0e30)) *sink = (double)acc;
+}
+
 __global__ void k_uniform(unsigned long long seed, long long n, double scale, double* out) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[j] = scale * splitmix_uniform(seed, (unsigned long long)j);
@@ -1810,6 +1833,48 @@ int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void*
   k_uniform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((unsigned long long)seed, (long long)n, obj_scale, out);
   CKL();
   CK(cudaStreamSynchronize(st));
+  return PDHGC_OK;
+}
+
+int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t reps, double* ms_out,
+                       void* cuda_stream) {
+  if (n_vec < 1 || count < 1 || (elem_bytes != 4 && elem_bytes != 8) || reps < 1 || !ms_out)
+    return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  void* vec = nullptr;
+  double* sink = nullptr;
+  CK(cudaMalloc(&vec, (size_t)n_vec * elem_bytes));
+  std::unique_ptr<void, void (*)(void*)> vg(vec, [](void* q) { cudaFree(q); });
+  CK(cudaMalloc(&sink, sizeof(double)));
+  std::unique_ptr<double, void (*)(double*)> sg(sink, [](double* q) { cudaFree(q); });
+  CK(cudaMemsetAsync(vec, 0, (size_t)n_vec * elem_bytes, st));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long per_block = 256LL * kGatherProbeBatch;
+  long long grid = (count + per_block - 1) / per_block;
+  if (grid > (long long)sms * 8) grid = (long long)sms * 8;
+  auto launch = [&]() {
+    if (elem_bytes == 8)
+      k_gather_probe<double><<<(unsigned)grid, 256, 0, st>>>(static_cast<const double*>(vec), n_vec, count, sink);
+    else
+      k_gather_probe<float><<<(unsigned)grid, 256, 0, st>>>(static_cast<const float*>(vec), n_vec, count, sink);
+  };
+  launch();  // warm: the vector into L2
+  CKL();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; ++r) launch();
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CKL();
+  *ms_out = (double)ms / reps;
   return PDHGC_OK;
 }
 

@@ -123,6 +123,7 @@ _sig = {
     "pdhgc_batch_kernel_launches": (C.c_int64, [_vp]),
     "pdhgc_batch_set_handoff": (C.c_int, [_vp, C.c_int32, C.c_int64]),
     "pdhgc_batch_handed_off": (C.c_int32, [_vp, C.c_int32, C.c_int]),
+    "pdhgc_probe_gather": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32, _vp, _vp]),
     "pdhgc_get_state": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "pdhgc_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "pdhgc_default_guide_params": (None, [C.POINTER(GuideParams)]),
@@ -588,6 +589,15 @@ def uniform(seed: int, n: int, obj_scale: float = 1.0):
     _check(lib.pdhgc_uniform(C.c_uint64(seed), n, obj_scale, out.data_ptr(), _current_stream()),
            "pdhgc_uniform")
     return out
+
+
+def probe_gather(n_vec: int, count: int, elem_bytes: int = 8, reps: int = 20) -> float:
+    """pdhgc_probe_gather: mean ms per launch of `count` random loads from an
+    L2-resident vector of n_vec elements."""
+    out = np.zeros(1)
+    _check(lib.pdhgc_probe_gather(int(n_vec), int(count), int(elem_bytes), int(reps), out.ctypes.data,
+                                  _current_stream()), "pdhgc_probe_gather")
+    return float(out[0])
 
 
 def _cuda_available():

@@ -302,3 +302,11 @@ def test_checkpoint_restore_fp32_bulk():
     xa, _, _ = g.get_solution(P.CORNER)
     xb, _, _ = h.get_solution(P.CORNER)
     assert np.array_equal(xa, xb)
+
+
+def test_gather_probe_reports_a_plausible_rate():
+    ms = P.probe_gather(100_000, 3_206_827, 8, reps=5)
+    rate = 3_206_827 / (ms * 1e-3)
+    assert 1e9 < rate < 1e13
+    with pytest.raises(P.PdhgcError):
+        P.probe_gather(0, 10, 8)
