@@ -58,6 +58,7 @@ struct LpDesc {
   double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r;  // FP64 iterates (x_bar, y: global fallback)
   float *x32, *xbar32, *y32;                          // FP32 iterates (global fallback)
   float *x32lo, *y32lo;                               // low parts of the float-float FP32 iterates
+  float2 *sx32, *sy32;                                // float-float FP32 running sums
   double *x1, *y1, *xc;
   double *pi_v, *pi_w, *pi_u;
   double* keep;  // eta, sigma_max, ||b_hat||, ||c_hat|| from phase 1 (read by the corner phase)
@@ -395,6 +396,7 @@ struct LpSolver {
         const float h = (float)x0;
         d.x32[j] = h;
         d.x32lo[j] = (float)(x0 - (double)h);
+        d.sx32[j] = make_float2(0.f, 0.f);
         s_xbar[j] = (VT)h;
       } else {
         ((double*)s_xbar)[j] = x0;
@@ -405,6 +407,7 @@ struct LpSolver {
       if (kF32) {
         d.y[i] = 0.0;
         d.y32lo[i] = 0.0f;
+        d.sy32[i] = make_float2(0.f, 0.f);
       }
       d.y_r[i] = 0.0;
       d.sum_y[i] = 0.0;
@@ -462,7 +465,7 @@ struct LpSolver {
     double part[1] = {0.0};
     if constexpr (kF32) {
       const DevModel32 md = model32(corner);
-      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sum_x, d.sum_y, d.x32lo, d.y32lo};
+      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sx32, d.sy32, d.x32lo, d.y32lo};
       passT(matT32(), PrimalOp32{S, it, (float*)s_y, md, w}, part);
       __syncthreads();
       passA(matA32(), DualOp32{S, it, (float*)s_xbar, md, w}, part);
@@ -505,9 +508,14 @@ struct LpSolver {
         if (S->chunks > S->max_chunks) S->at_limit = 1;
       }
       if (kF32) {
-        for (int j = threadIdx.x; j < n; j += BT)
+        for (int j = threadIdx.x; j < n; j += BT) {
           d.x[j] = fmin(fmax((double)d.x32[j] + (double)d.x32lo[j], md.lhat[j]), md.uhat[j]);
-        for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
+          d.sum_x[j] = (double)d.sx32[j].x + (double)d.sx32[j].y;
+        }
+        for (int i = threadIdx.x; i < m; i += BT) {
+          d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
+          d.sum_y[i] = (double)d.sy32[i].x + (double)d.sy32[i].y;
+        }
       }
       __syncthreads();
       evaluate(corner);
@@ -531,10 +539,13 @@ struct LpSolver {
           w.x[j] = xn;
           w.x_r[j] = xn;
           w.sum_x[j] = 0.0;
-          if (kF32 && rt == 2) {
-            const float h = (float)xn;
-            d.x32[j] = h;
-            d.x32lo[j] = (float)(xn - (double)h);
+          if (kF32) {
+            d.sx32[j] = make_float2(0.f, 0.f);
+            if (rt == 2) {
+              const float h = (float)xn;
+              d.x32[j] = h;
+              d.x32lo[j] = (float)(xn - (double)h);
+            }
           }
         }
         for (int i = threadIdx.x; i < m; i += BT) {
@@ -542,10 +553,13 @@ struct LpSolver {
           w.y[i] = yn;
           w.y_r[i] = yn;
           w.sum_y[i] = 0.0;
-          if (kF32 && rt == 2) {
-            const float h = (float)yn;
-            ((float*)s_y)[i] = h;
-            d.y32lo[i] = (float)(yn - (double)h);
+          if (kF32) {
+            d.sy32[i] = make_float2(0.f, 0.f);
+            if (rt == 2) {
+              const float h = (float)yn;
+              ((float*)s_y)[i] = h;
+              d.y32lo[i] = (float)(yn - (double)h);
+            }
           }
         }
       }
@@ -1041,6 +1055,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   double *b_int, *cc, *l, *u, *Dr, *Dc, *rfac, *cfac, *bhat, *chat, *lhat, *uhat, *chat_c, *lhat_c, *uhat_c;
   double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r, *x1, *y1, *xc, *pi_v, *pi_w, *pi_u;
   float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32, *x32, *xbar32, *y32, *x32lo, *y32lo;
+  float2 *sx32, *sy32;
   int8_t *ge, *ge_c;
   BAL(b_int, M); BAL(cc, N); BAL(l, N); BAL(u, N); BAL(Dr, M); BAL(Dc, N); BAL(rfac, M); BAL(cfac, N);
   BAL(bhat, M); BAL(chat, N); BAL(lhat, N); BAL(uhat, N); BAL(chat_c, N); BAL(lhat_c, N); BAL(uhat_c, N);
@@ -1050,6 +1065,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   BAL(keep, 4 * K);
   BAL(bhat32, M); BAL(chat32, N); BAL(lhat32, N); BAL(uhat32, N); BAL(chat_c32, N); BAL(lhat_c32, N);
   BAL(uhat_c32, N); BAL(x32, N); BAL(xbar32, N); BAL(y32, M); BAL(x32lo, N); BAL(y32lo, M);
+  BAL(sx32, N); BAL(sy32, M);
   BAL(ge, M); BAL(ge_c, M);
   BAL(B->d_desc, K);
   BAL(B->d_order, K);
@@ -1107,6 +1123,7 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
     d.y = y + om; d.sum_y = sum_y + om; d.y_r = y_r + om;
     d.x32 = x32 + on; d.xbar32 = xbar32 + on; d.y32 = y32 + om;
     d.x32lo = x32lo + on; d.y32lo = y32lo + om;
+    d.sx32 = sx32 + on; d.sy32 = sy32 + om;
     d.x1 = x1 + on; d.y1 = y1 + om; d.xc = xc + on;
     d.pi_v = pi_v + on; d.pi_w = pi_w + on; d.pi_u = pi_u + om;
     d.keep = keep + 4 * (size_t)k;

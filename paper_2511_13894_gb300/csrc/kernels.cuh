@@ -977,16 +977,29 @@ struct DevModel32 {
 // the gathers and the matrix products read the high parts only, while the
 // updates x - tau g and y + sigma r are added exactly into the pair, so that
 // steps far below an FP32 unit of the iterate (tiny tau or sigma) still move
-// it.  xbar is FP32 (it is only gathered).
+// it.  xbar is FP32 (it is only gathered).  The running sums are float-float
+// pairs too (8 bytes, like a double), so the iteration does no FP64 work;
+// they are widened to FP64 at each check.
 struct DevIter32 {
   float* x;
   float* y;
   float* xbar;
-  double* sum_x;
-  double* sum_y;
+  float2* sum_x;
+  float2* sum_y;
   float* xlo;
   float* ylo;
 };
+
+// (hi, lo) += (a, b) for float-float pairs, TwoSum of the high parts
+__device__ __forceinline__ void ff_add(float2& s, float a, float b) {
+  const float t = s.x + a;
+  const float bb = t - s.x;
+  const float err = (s.x - (t - bb)) + (a - bb);
+  const float l = s.y + (err + b);
+  const float h = t + l;
+  s.y = l - (h - t);
+  s.x = h;
+}
 
 // (hi, lo) + a * b, with a * b formed exactly (fma) and both sums TwoSum:
 // the pair keeps about 48 bits
@@ -1022,13 +1035,15 @@ struct PrimalOp32 {
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
     float c, l, u, x, xl, tau;
-    double sx;
+    float2 sx;
   };
   __device__ Pre prefetch(int j) const {
     return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.xlo[j], (float)S->tau, w.sum_x[j]};
   }
   __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
-    const float g = (float)((double)p.c - a.value());
+    // g = c - (A'y) from the float-float row sum: c - hi is exact when the two
+    // are close (Sterbenz), so g keeps its relative precision near optimality
+    const float g = (p.c - a.hi[0]) - a.lo[0];
     float xh = p.x, xl = p.xl;
     ff_axpy(xh, xl, -p.tau, g);
     // projection onto [l, u] of the pair (a clamped value carries no low part)
@@ -1038,7 +1053,9 @@ struct PrimalOp32 {
       xl = 0.0f;
     }
     w.xbar[j] = 2.0f * xh - p.x;
-    w.sum_x[j] = p.sx + ((double)xh + (double)xl);
+    float2 sx = p.sx;
+    ff_add(sx, xh, xl);
+    w.sum_x[j] = sx;
     w.x[j] = xh;
     w.xlo[j] = xl;
   }
@@ -1064,13 +1081,13 @@ struct DualOp32 {
   struct Pre {
     float b, y, yl, sigma;
     bool ge;
-    double sy;
+    float2 sy;
   };
   __device__ Pre prefetch(int i) const {
     return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, md.ge[i] != 0, w.sum_y[i]};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
-    const float r = (float)((double)p.b - a.value());
+    const float r = (p.b - a.hi[0]) - a.lo[0];
     float yh = p.y, yl = p.yl;
     ff_axpy(yh, yl, p.sigma, r);
     // y >= 0 on '>' rows: a negative pair projects to (0, 0)
@@ -1078,7 +1095,9 @@ struct DualOp32 {
       yh = 0.0f;
       yl = 0.0f;
     }
-    w.sum_y[i] = p.sy + ((double)yh + (double)yl);
+    float2 sy = p.sy;
+    ff_add(sy, yh, yl);
+    w.sum_y[i] = sy;
     w.y[i] = yh;
     w.ylo[i] = yl;
   }

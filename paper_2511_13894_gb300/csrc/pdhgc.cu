@@ -162,6 +162,8 @@ struct Iter32 {
   float* y;
   float* xlo;  // low parts of the float-float iterates
   float* ylo;
+  float2* sx;  // float-float running sums
+  float2* sy;
 };
 
 __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
@@ -177,6 +179,7 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
       w32.x[i] = h;
       w32.xlo[i] = (float)(x0 - (double)h);
       w32.xbar[i] = h;
+      w32.sx[i] = make_float2(0.f, 0.f);
     }
   }
   if (i < m) {
@@ -186,6 +189,7 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
     if (w32.y) {
       w32.y[i] = 0.0f;
       w32.ylo[i] = 0.0f;
+      w32.sy[i] = make_float2(0.f, 0.f);
     }
   }
 }
@@ -193,13 +197,20 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
 // FP32 bulk: FP64 copies of the current iterates for the FP64 evaluation; x is
 // clamped to the FP64 bounds (an FP32-rounded bound may lie an ulp outside)
 __global__ void k_to64(const Scalars* S, int n, int m, const float* __restrict__ x32, const float* __restrict__ y32,
-                       const float* __restrict__ xlo, const float* __restrict__ ylo,
-                       const double* __restrict__ lhat, const double* __restrict__ uhat, double* __restrict__ x,
-                       double* __restrict__ y) {
+                       const float* __restrict__ xlo, const float* __restrict__ ylo, const float2* __restrict__ sx,
+                       const float2* __restrict__ sy, const double* __restrict__ lhat,
+                       const double* __restrict__ uhat, double* __restrict__ x, double* __restrict__ y,
+                       double* __restrict__ sum_x, double* __restrict__ sum_y) {
   if (S->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = fmin(fmax((double)x32[i] + (double)xlo[i], lhat[i]), uhat[i]);
-  if (i < m) y[i] = (double)y32[i] + (double)ylo[i];
+  if (i < n) {
+    x[i] = fmin(fmax((double)x32[i] + (double)xlo[i], lhat[i]), uhat[i]);
+    sum_x[i] = (double)sx[i].x + (double)sx[i].y;
+  }
+  if (i < m) {
+    y[i] = (double)y32[i] + (double)ylo[i];
+    sum_y[i] = (double)sy[i].x + (double)sy[i].y;
+  }
 }
 
 // FP64 -> FP32 copy
@@ -317,10 +328,13 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.x[i] = xn;
     w.x_r[i] = xn;
     w.sum_x[i] = 0.0;
-    if (w32.x && rt == 2) {
-      const float h = (float)xn;
-      w32.x[i] = h;
-      w32.xlo[i] = (float)(xn - (double)h);
+    if (w32.x) {
+      w32.sx[i] = make_float2(0.f, 0.f);
+      if (rt == 2) {
+        const float h = (float)xn;
+        w32.x[i] = h;
+        w32.xlo[i] = (float)(xn - (double)h);
+      }
     }
     if (rr.rx) {
       const size_t slot = (size_t)(S->restarts % 8) * (size_t)n;
@@ -333,10 +347,13 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
     w.y[i] = yn;
     w.y_r[i] = yn;
     w.sum_y[i] = 0.0;
-    if (w32.y && rt == 2) {
-      const float h = (float)yn;
-      w32.y[i] = h;
-      w32.ylo[i] = (float)(yn - (double)h);
+    if (w32.y) {
+      w32.sy[i] = make_float2(0.f, 0.f);
+      if (rt == 2) {
+        const float h = (float)yn;
+        w32.y[i] = h;
+        w32.ylo[i] = (float)(yn - (double)h);
+      }
     }
   }
 }
@@ -652,6 +669,8 @@ int ensure_fp32(pdhgc_lp* lp) {
   RET(lp->alloc(&lp->it32.y, m));
   RET(lp->alloc(&lp->it32.xlo, n));
   RET(lp->alloc(&lp->it32.ylo, m));
+  RET(lp->alloc(&lp->it32.sx, n));
+  RET(lp->alloc(&lp->it32.sy, m));
   RET(lp->alloc(&lp->chat32, n));
   RET(lp->alloc(&lp->lhat32, n));
   RET(lp->alloc(&lp->uhat32, n));
@@ -748,8 +767,8 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
-  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr, nullptr, nullptr};
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y, lp->it32.xlo,
+  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
                        lp->it32.ylo};
   k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
@@ -799,8 +818,8 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
     }
   }
   if (rc == PDHGC_OK && fp32) {
-    k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, lp->it32.xlo, lp->it32.ylo, md.lhat, md.uhat,
-                                lp->it.x, lp->it.y);
+    k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, lp->it32.xlo, lp->it32.ylo, lp->it32.sx,
+                                lp->it32.sy, md.lhat, md.uhat, lp->it.x, lp->it.y, lp->it.sum_x, lp->it.sum_y);
     lp->launches++;
   }
   if (rc == PDHGC_OK) {
@@ -1887,7 +1906,7 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
   const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it.sum_x, lp->it.sum_y, lp->it32.xlo,
+  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
                        lp->it32.ylo};
   // the replay must not stop on the phase's done flag or iteration limit
   Scalars S;
