@@ -966,8 +966,16 @@ int run_handoffs(pdhgc_batch* B, int phase, const pdhgc_params& p, const pdhgc_c
   std::vector<std::string> errs(ks.size());
   std::vector<int64_t> lcount(ks.size(), 0);
   std::vector<std::thread> th;
-  for (size_t i = 0; i < ks.size(); ++i)
-    th.emplace_back([&, i] { rcs[i] = finish_on_single_path(B, ks[i], phase, p, cp, errs[i], lcount[i]); });
+  size_t started = 0;
+  try {
+    for (; started < ks.size(); ++started)
+      th.emplace_back([&, started] {
+        rcs[started] = finish_on_single_path(B, ks[started], phase, p, cp, errs[started], lcount[started]);
+      });
+  } catch (...) {
+    // no more threads: finish the rest on this one
+  }
+  for (size_t i = started; i < ks.size(); ++i) rcs[i] = finish_on_single_path(B, ks[i], phase, p, cp, errs[i], lcount[i]);
   for (auto& t : th) t.join();
   for (size_t i = 0; i < ks.size(); ++i) B->launches += lcount[i];
   for (size_t i = 0; i < ks.size(); ++i)
