@@ -396,16 +396,16 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     Be.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # 16 LPs spread over the size range, 2048 oracle iterations each
+        # 16 LPs spread over the size range, 4096 oracle iterations each (~10 s)
         by_size = sorted(all_lps, key=lambda lp: lp["n"] + lp["m"])
         picks = [by_size[k] for k in range(16, len(by_size), len(by_size) // 16)][:16]
         t_cpu, it_cpu = 0.0, 0
         for lp in picks:
-            c1 = cpu_baseline_sample(lp, 2048)
-            t_cpu += 2048 / c1["value"]
-            it_cpu += 2048
+            c1 = cpu_baseline_sample(lp, 4096)
+            t_cpu += 4096 / c1["value"]
+            it_cpu += 4096
         cpu = {"value": it_cpu / t_cpu, "unit": "iters/s", "cores": 1, "kind": "oracle",
-               "sample": f"2048 phase-1 PDHG iterations with restart checks on each of 16 LPs of the batch "
+               "sample": f"4096 phase-1 PDHG iterations with restart checks on each of 16 LPs of the batch "
                          f"spread over its size range ({t_cpu:.1f} s; setup not counted); numpy/scipy, "
                          f"single-threaded"}
     if rank == 0:
