@@ -8,7 +8,11 @@
 // live in the CTA's shared memory, so the random gathers of the SpMV are
 // shared-memory loads.  A finished LP drops out: its CTA pulls the next one.
 // The arithmetic of every step is the same operator code as the single-LP
-// path (kernels.cuh); only the scheduling differs.
+// path (kernels.cuh); only the scheduling differs.  Each phase is one CUDA
+// graph (queue reset + the persistent kernel).  Tail handoff: once the queue
+// is empty and only a few LPs still run, a long-running LP stops at its next
+// check and the host finishes it on the single-LP path (whole-GPU graph
+// loop), several concurrently on their own streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>

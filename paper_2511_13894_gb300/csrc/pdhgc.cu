@@ -1,6 +1,8 @@
 // C-ABI of the PDHG + corner-push library (include/pdhgc.h): handle,
 // device memory, setup kernels, the graph-driven restarted PDHG loop,
-// Algorithm 1, reports and accessors.
+// Algorithm 1, reports and accessors; the phase-1 restart history, features,
+// labels and held corner phase of the learned guidance; checkpoint/restore;
+// the random-gather probe.
 #include <cuda_runtime.h>
 
 #include <chrono>
