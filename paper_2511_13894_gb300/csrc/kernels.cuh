@@ -292,7 +292,7 @@ using SpmvMat = SpmvMatT<double>;
 // gathers in flight per lane, and the minimum resident blocks per SM the
 // register allocation must allow (tuning knobs, overridable at build time)
 #ifndef PDHGC_GATHER_BATCH
-#define PDHGC_GATHER_BATCH 8
+#define PDHGC_GATHER_BATCH 4
 #endif
 #ifndef PDHGC_MIN_BLOCKS
 #define PDHGC_MIN_BLOCKS 4
