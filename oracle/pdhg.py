@@ -57,6 +57,7 @@ DEFAULTS = dict(
     eta_factor=0.998,    # reading: eta = 0.998 / sigma_max
     ruiz_iters=10,       # reading
     power_iters=100,     # reading
+    algorithm="averaged",  # inner loop: "averaged" (this module) or "halpern" (oracle.halpern)
 )
 
 CORNER_DEFAULTS = dict(
@@ -369,7 +370,11 @@ def _pick(ev_cur, ev_avg):
 
 def solve(lp, params=None, model=None):
     """Phase 1: restarted PDHG until max(rel_p, rel_d, rel_gap) <= eps_rel
-    (Section 2, eps_rel = 1e-6 per Section 4.1) at a check, or a limit."""
+    (Section 2, eps_rel = 1e-6 per Section 4.1) at a check, or a limit.
+    params["algorithm"] == "halpern" runs the Halpern loop of oracle.halpern."""
+    if params and params.get("algorithm", "averaged") == "halpern":
+        from . import halpern
+        return halpern.solve(lp, params, model)
     if model is None:
         model, p, sigma_max, eta = setup(lp, params)
     else:
@@ -555,7 +560,11 @@ def corner_phase(phase1, corner_params=None, hold=None):
     with the same step size, stop once k >= min_iters and the primal residual
     of the current (else the average) point meets eps_rel (1 + ||b||) on M_hat,
     checked every check period (Section 3.1); return (x_hat, y, z) with the
-    phase-1 y and z (Algorithm 1, last step)."""
+    phase-1 y and z (Algorithm 1, last step).  A phase 1 run with the Halpern
+    loop continues with it (oracle.halpern.corner_phase)."""
+    if phase1["params"].get("algorithm", "averaged") == "halpern":
+        from . import halpern
+        return halpern.corner_phase(phase1, corner_params, hold)
     cp = dict(CORNER_DEFAULTS)
     if corner_params:
         cp.update(corner_params)
