@@ -3,7 +3,9 @@
 of "Backing PDHG into a Corner" on one synthetic LP per GPU.
 
 One step = pdhgc_solve (Ruiz + Pock-Chambolle scaling, power iteration,
-restarted PDHG until the Section 2 relative test holds at 1e-6) followed by
+restarted PDHG until the Section 2 relative test holds at 1e-6; the headline
+runs the Halpern loop, the cuPDLP+ form Section 4.1 names, and the averaged
+loop's arms follow as blocks) followed by
 pdhgc_corner_phase (Algorithm 1, Section 3.1 stopping rule, capped at
 --corner-max-iters), on the LP already resident in HBM.  The reported value is
 PDHG iterations per second over the whole step (phase-1 plus corner
@@ -30,6 +32,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+# the CPU oracle legs report one core: keep numpy's BLAS single-threaded
+# (set before numpy loads; an explicit setting in the environment wins)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
@@ -68,6 +75,9 @@ def parse():
     ap.add_argument("--corner-rows", choices=["paper", "active"], default="paper",
                     help="paper: Section 3's row rule; active: the option that keeps rows inactive at the "
                          "phase-1 point as inequalities (row_rule = 1)")
+    ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="both",
+                    help="inner loop of the headline (averaged) and of an extra block (halpern); 'both' "
+                         "adds the Halpern loop (FP64, the paper's row rule) beside the averaged arms")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-iters", type=int, default=50)
     ap.add_argument("--cpu-iters", type=int, default=640,
@@ -213,10 +223,70 @@ def algorithmic_bytes(m, n, nnz, s_v=8, s_x=8, s_sum=8, s_lo=0):
     return primal, dual
 
 
+def algorithmic_bytes_halpern(m, n, nnz):
+    """Bytes per launch of the Halpern loop's kernels (FP64), a step inside a
+    chunk: primal reads values + indices, column pointers, c, l, u, x and the
+    anchor x_0, writes x_bar and x, gathers y once; dual reads values +
+    indices, row pointers, b, y, the anchor y_0 and the sense byte, writes y,
+    gathers x_bar once.  (A check step, one in 64, also writes T(z) and
+    z - T(z); not counted.)"""
+    primal = nnz * 12 + n * 4 + n * 7 * 8 + m * 8
+    dual = nnz * 12 + m * 4 + m * (4 * 8 + 1) + n * 8
+    return primal, dual
+
+
+def fp64_ops_halpern(m, n, nnz):
+    """FP64 operations per launch of the Halpern loop's kernels: one FMA per
+    nonzero plus the epilogue (primal: 7 per column; dual: 6 per row)."""
+    return nnz + 7 * n, nnz + 6 * m
+
+
 def fp64_ops(m, n, nnz):
     """FP64 operations per launch: one FMA per nonzero plus the epilogue
     (primal: 6 per column; dual: 4 per row)."""
     return nnz + 6 * n, nnz + 4 * m
+
+
+def oracle_sample(model, p, eta, iters, algorithm):
+    """`iters` phase-1 steps of the oracle's loop ("averaged" or "halpern")
+    from the start point, with the restart checks every check period; returns
+    the seconds taken.  The start point's setup (for the Halpern loop, the
+    anchor's residual) is not timed."""
+    import oracle
+    from oracle import halpern as H
+    x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
+    if algorithm == "halpern":
+        q = H._params(dict(p, algorithm="halpern"))
+        s = H.HState(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            x_pre, y_pre = H.halpern_step(model, s, q["reflection"])
+            if s.k % q["check_period"] == 0:
+                oracle.evaluate(model, s.xp, s.yp, s.omega)
+                r = H.fixed_point_residual(model, x_pre, y_pre, s.xp, s.yp, s.tau, s.sigma)
+                if H.restart_due(r, s.r0, s.r_prev, s.t, s.k, q):
+                    H.apply_restart(model, s, q, r)
+                else:
+                    s.r_prev = r
+        return time.perf_counter() - t0
+    s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        oracle.pdhg_step(model, s)
+        if s.k % p["check_period"] == 0:
+            xa, ya = s.average()
+            ec = oracle.evaluate(model, s.x, s.y, s.omega)
+            ea = oracle.evaluate(model, xa, ya, s.omega)
+            oracle.restart_check(model, s, p, ec, ea)
+    return time.perf_counter() - t0
+
+
+def headline_algorithm(args):
+    """The loop the headline line measures: the Halpern loop unless
+    --algorithm averaged; the batched workload runs the averaged loop only."""
+    if args.workload == "batch_512" or args.algorithm == "averaged":
+        return "averaged"
+    return "halpern"
 
 
 def run_reference(args, rank, world):
@@ -233,24 +303,11 @@ def run_reference(args, rank, world):
         lp = WORKLOADS[args.workload]()
     model, p, sigma_max, eta = oracle.setup(lp)
     iters = args.cpu_iters
-
-    def one_step():
-        import math
-        x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
-        s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
-        t0 = time.perf_counter()
-        for _ in range(iters):
-            oracle.pdhg_step(model, s)
-            if s.k % p["check_period"] == 0:
-                xa, ya = s.average()
-                ec = oracle.evaluate(model, s.x, s.y, s.omega)
-                ea = oracle.evaluate(model, xa, ya, s.omega)
-                oracle.restart_check(model, s, p, ec, ea)
-        return time.perf_counter() - t0, math.nan
+    alg = headline_algorithm(args)
 
     for _ in range(args.warmup):
-        one_step()
-    times = [one_step()[0] for _ in range(args.steps)]
+        oracle_sample(model, p, eta, iters, alg)
+    times = [oracle_sample(model, p, eta, iters, alg) for _ in range(args.steps)]
     total = sum(times)
     value = iters * args.steps / total
     out = {
@@ -259,35 +316,25 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "m": lp["m"], "n": lp["n"], "nnz": int(lp["row_ptr"][-1]),
-                   "precision": "fp64", "sample_iters_per_step": iters},
+                   "precision": "fp64", "algorithm": alg, "sample_iters_per_step": iters},
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{iters} phase-1 PDHG iterations (with their restart checks) per step on "
-                                   f"the same LP; numpy/scipy single-threaded; setup untimed"},
+                         "sample": f"{iters} phase-1 PDHG iterations of the {alg} loop (with their restart "
+                                   f"checks) per step on the same LP; numpy/scipy single-threaded; setup untimed"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline_sample(lp, iters):
+def cpu_baseline_sample(lp, iters, algorithm="averaged"):
     """The oracle timed on this host on a bounded sample (rank 0, N = 1)."""
     import oracle
     t0 = time.perf_counter()
     model, p, sigma_max, eta = oracle.setup(lp)
     t_setup = time.perf_counter() - t0
-    x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
-    s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
-    t0 = time.perf_counter()
-    for _ in range(iters):
-        oracle.pdhg_step(model, s)
-        if s.k % p["check_period"] == 0:
-            xa, ya = s.average()
-            ec = oracle.evaluate(model, s.x, s.y, s.omega)
-            ea = oracle.evaluate(model, xa, ya, s.omega)
-            oracle.restart_check(model, s, p, ec, ea)
-    dt = time.perf_counter() - t0
+    dt = oracle_sample(model, p, eta, iters, algorithm)
     return {"value": iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} phase-1 PDHG iterations with restart checks on the same LP "
-                      f"({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
+            "sample": f"{iters} phase-1 PDHG iterations of the {algorithm} loop with restart checks on the same "
+                      f"LP ({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
                       f"numpy/scipy, single-threaded"}
 
 
@@ -485,7 +532,8 @@ def main():
     stream = torch.cuda.current_stream()
     g = P.lp_from_dict(lp_dict, stream=stream.cuda_stream)
     if args.mode == "kernels":
-        g.solve(max_iters=64, precision=P.FP32_BULK if args.precision == "fp32" else P.FP64)
+        g.solve(max_iters=64, precision=P.FP32_BULK if args.precision == "fp32" else P.FP64,
+                algorithm=P.HALPERN if args.algorithm == "halpern" else P.AVERAGED)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("pdhg_kernels")
         ms = g.profile_iteration(args.profile_iters)
@@ -503,8 +551,10 @@ def main():
         uuid = None
     peak, peak_kind = measured_peaks()
 
-    def run_arm(precision, cparams=cparams):
-        params = P.default_params(max_iters=args.phase1_max_iters, precision=precision)
+    def run_arm(precision, cparams=cparams, algorithm=None):
+        algorithm = P.AVERAGED if algorithm is None else algorithm
+        params = P.default_params(max_iters=args.phase1_max_iters, precision=precision, algorithm=algorithm)
+        halpern = algorithm == P.HALPERN
 
         def step():
             r1 = g.solve(params)
@@ -541,7 +591,10 @@ def main():
         value = total_iters_all / (total_ms * 1e-3)
         # kernel durations: event-bracketed replays of the two iteration kernels
         ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
-        if precision == P.FP64:
+        if halpern:
+            b_primal, b_dual = algorithmic_bytes_halpern(m, n, nnz)
+            f_primal, f_dual = fp64_ops_halpern(m, n, nnz)
+        elif precision == P.FP64:
             b_primal, b_dual = algorithmic_bytes(m, n, nnz)
             f_primal, f_dual = fp64_ops(m, n, nnz)
         else:
@@ -551,12 +604,12 @@ def main():
         ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
         achieved = b_dom / (ms_dom * 1e-3) / 1e9
         tr = traffic_record() if precision == P.FP64 else None
-        key = "dram_bytes_per_launch_" + dom
+        key = ("halpern_" if halpern else "") + "dram_bytes_per_launch_" + dom
         roofline = {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": float(tr[key]) if tr and key in tr else None,
             "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
-                      + ("32>" if precision == P.FP32_BULK else ">") + f" ({dom} step)",
+                      + ("H>" if halpern else "32>" if precision == P.FP32_BULK else ">") + f" ({dom} step)",
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": b_dom, "launch_ms": ms_dom,
             "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
@@ -594,18 +647,25 @@ def main():
             "us_per_iter": res["total_ms"] * 1e3 / max(1, res["total_iters"]),
         }
 
+    # the headline: the Halpern loop (FP64) unless --algorithm averaged; with
+    # --algorithm both the averaged loop's arms follow as blocks: FP64, FP32
+    # bulk, and the corner row option (not the paper's rule: rows inactive
+    # at the phase-1 point kept as inequalities)
     arms = {}
-    if args.precision in ("fp64", "both"):
-        arms["fp64"] = run_arm(P.FP64)
-    if args.precision in ("fp32", "both"):
-        arms["fp32"] = run_arm(P.FP32_BULK)
-    # the corner row option (not the paper's rule): the same step with rows
-    # inactive at the phase-1 point kept as inequalities, FP64 and FP32 bulk
-    if args.corner_rows == "paper" and not args.no_row_option and args.precision == "both":
-        cp_opt = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed, row_rule=1)
-        arms["fp64_rows"] = run_arm(P.FP64, cp_opt)
-        arms["fp32_rows"] = run_arm(P.FP32_BULK, cp_opt)
-    head = arms["fp64"] if "fp64" in arms else arms["fp32"]
+    head_alg = headline_algorithm(args)
+    if head_alg == "halpern":
+        arms["halpern"] = run_arm(P.FP64, algorithm=P.HALPERN)
+    if args.algorithm in ("averaged", "both"):
+        if args.precision in ("fp64", "both"):
+            arms["fp64"] = run_arm(P.FP64)
+        if args.precision in ("fp32", "both"):
+            arms["fp32"] = run_arm(P.FP32_BULK)
+        if args.corner_rows == "paper" and not args.no_row_option and args.precision == "both":
+            cp_opt = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
+                                             row_rule=1)
+            arms["fp64_rows"] = run_arm(P.FP64, cp_opt)
+            arms["fp32_rows"] = run_arm(P.FP32_BULK, cp_opt)
+    head = arms["halpern"] if head_alg == "halpern" else (arms["fp64"] if "fp64" in arms else arms["fp32"])
     params = head["params"]
     value = head["value"]
     total_ms = head["total_ms"]
@@ -650,10 +710,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(lp_dict, args.cpu_iters)
+        cpu = cpu_baseline_sample(lp_dict, args.cpu_iters, head_alg)
 
     if rank == 0:
-        head_is_fp64 = "fp64" in arms
+        head_is_fp64 = head_alg == "halpern" or "fp64" in arms
         out = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -663,18 +723,30 @@ def main():
                        "precision": "fp64" if head_is_fp64 else "fp32_bulk",
                        "phase1_max_iters": args.phase1_max_iters, "corner_max_iters": args.corner_max_iters,
                        "corner_seed": args.corner_seed, "corner_rows": args.corner_rows, "eps_rel": 1e-6,
+                       "algorithm": head_alg,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
         }
         out.update(summary(head))
         out.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                     "clocks": clk})
-        if head_is_fp64 and "fp32" in arms:
+        if head_alg == "halpern" and "fp64" in arms:
+            a = arms["fp64"]
+            blk = {"note": "the averaged loop (cuPDLP.jl-style restarts on the KKT error of the current and "
+                           "average points), FP64, the paper's corner row rule",
+                   "value": a["value"], "unit": "iters/s", "time_to_corner_s": a["total_ms"] / args.steps * 1e-3,
+                   "halpern_speedup_time_to_corner": (a["total_ms"] / total_ms) if total_ms > 0 else None,
+                   "roofline": a["roofline"], "gpu_launches": a["launches"], "clocks": a["clocks"]}
+            blk.update(summary(a))
+            out["averaged_fp64"] = blk
+        if "fp64" in arms and "fp32" in arms:
+            a64 = arms["fp64"]
             f = arms["fp32"]
             blk = {"value": f["value"], "unit": "iters/s", "dtype": "f32 values, float-float iterates, row sums "
                                                                    "and running sums; f64 checks and KKT",
                    "time_to_corner_s": f["total_ms"] / args.steps * 1e-3,
-                   "speedup_vs_fp64_time_to_corner": (total_ms / f["total_ms"]) if f["total_ms"] > 0 else None,
+                   "speedup_vs_averaged_fp64_time_to_corner": (a64["total_ms"] / f["total_ms"]) if f["total_ms"] > 0
+                   else None,
                    "roofline": f["roofline"], "gpu_launches": f["launches"], "clocks": f["clocks"]}
             blk.update(summary(f))
             out["fp32_bulk"] = blk

@@ -67,6 +67,21 @@ extern "C" {
 #define PDHGC_PHASE1  0
 #define PDHGC_CORNER  1
 
+/* ---- inner loop (pdhgc_params.algorithm) ---------------------------------
+ * PDHGC_ALG_AVERAGED: cuPDLP.jl-style restarted PDHG; restarts compare the
+ *   omega-weighted KKT error of the current iterate and of the running
+ *   average, and the better of the two is returned.
+ * PDHGC_ALG_HALPERN: the form of cuPDLP+, which Section 4.1 says the paper's
+ *   PDHG follows.  It runs anchored (Halpern) steps on the reflected PDHG
+ *   operator and keeps no averages:
+ *     z <- w_t ((1 + rho) T(z) - rho z) + (1 - w_t) z_0,  w_t = (t+1)/(t+2)
+ *   z_0 is the last restart point.  Restarts test the fixed-point residual
+ *   ||z - T(z)|| in the PDHG metric; the primal weight follows a PID rule on
+ *   the anchor's movement; every check evaluates, and returns, the PDHG
+ *   output T(z).  FP64 only. */
+#define PDHGC_ALG_AVERAGED 0
+#define PDHGC_ALG_HALPERN  1
+
 /* Sense codes are ASCII: '=' (61), '<' (60), '>' (62). */
 
 /*
@@ -87,7 +102,12 @@ typedef struct pdhgc_params {
     int32_t ruiz_iters;    /* Ruiz infinity-norm passes (10, 0..100) */
     int32_t power_iters;   /* power iterations for sigma_max (100, 1..10000) */
     int32_t precision;     /* PDHGC_FP64 or PDHGC_FP32_BULK */
-    int32_t reserved;
+    int32_t algorithm;     /* PDHGC_ALG_AVERAGED (default) or PDHGC_ALG_HALPERN (FP64 only) */
+    /* the Halpern loop only: */
+    double  reflection;    /* rho in [0, 1]; 1 (default): the reflected operator 2T - I */
+    double  pid_kp, pid_ki, pid_kd; /* primal-weight PID gains in log space (0.99, 0.01, 0):
+                              e = log(omega) - log(|y+ - y0| / |x+ - x0|) at a restart,
+                              I += e, log(omega) -= kp e + ki I + kd (e - e_prev) */
 } pdhgc_params;
 
 /*
@@ -122,7 +142,8 @@ typedef struct pdhgc_corner_params {
  */
 typedef struct pdhgc_report {
     int32_t status;        /* PDHGC_STATUS_* */
-    int32_t chosen;        /* 0: current iterate returned, 1: average returned */
+    int32_t chosen;        /* 0: current iterate returned, 1: average returned,
+                              2: the PDHG output T(z) of the last check (Halpern loop) */
     int64_t iters;         /* PDHG iterations of the phase */
     int64_t restarts;
     double  rP2, rD2;      /* ||r_P||_2, ||r_D||_2 */
@@ -206,9 +227,11 @@ int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z,
 /*
  * pdhgc_get_iterates — the solver's state in scaled space, user order:
  * current x_hat (n), y_hat (m) and the running averages of the iterates
- * since the last restart (zeros when no iteration ran since it).  Any
- * pointer may be NULL.  iters_out (may be NULL) receives {k, t, restarts}.
- * For parity tests against a reference implementation.
+ * since the last restart (zeros when no iteration ran since it).  After a
+ * Halpern-loop phase, x_avg / y_avg receive instead the PDHG output T(z) of
+ * the last check step, the point the phase returns.  Any pointer may be
+ * NULL.  iters_out (may be NULL) receives {k, t, restarts}.  For parity
+ * tests against a reference implementation.
  */
 int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double* y_avg,
                        int64_t* iters_out, int on_device);
@@ -304,7 +327,8 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
  * weight, restarts and termination, then the report); an LP's x_bar and y
  * live in the CTA's shared memory.  `reports` (count entries, may be NULL)
  * receives one report per LP in the caller's order; `seconds` is that LP's
- * device time.  Both precisions are supported.
+ * device time.  Both precisions are supported; the inner loop is the
+ * averaged one (INVALID_ARG for PDHGC_ALG_HALPERN, here and in the tuner).
  */
 int pdhgc_batch_solve(pdhgc_batch* batch, const pdhgc_params* params, pdhgc_report* reports);
 
@@ -546,7 +570,9 @@ int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t
  * phase's model as plain launches on the handle's stream, each kernel
  * bracketed by CUDA events, and writes the mean duration in milliseconds of
  * one launch of the primal step (the A' pass, ms_out[0]) and of the dual
- * step (the A pass, ms_out[1]).  The replayed iterations are real: they
+ * step (the A pass, ms_out[1]).  After a Halpern-loop phase the replayed
+ * kernels are that loop's (a step inside a chunk, not a check step).  The
+ * replayed iterations are real: they
  * advance the iterate state, which is left inconsistent with the phase's
  * report (x1/y1 and the corner result are not touched).  For profiling.
  * Errors: NO_PHASE1, INVALID_ARG (iters < 1 or ms_out NULL).

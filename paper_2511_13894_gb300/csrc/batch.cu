@@ -1235,6 +1235,8 @@ int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* 
       !(p.eta_factor > 0.0 && p.eta_factor < 1.0) || !(p.time_limit_s > 0.0) ||
       (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK))
     return set_berr(PDHGC_ERR_INVALID_ARG, "parameter out of range");
+  if (p.algorithm != PDHGC_ALG_AVERAGED)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched solver runs the averaged loop only");
   B->params = p;
   B->precision = p.precision;
   B->have_phase1 = 0;
@@ -1348,6 +1350,8 @@ int pdhgc_batch_tune(pdhgc_batch* B, const pdhgc_params* params, int32_t tune_it
   if (params) p = *params; else pdhgc_default_params(&p);
   if (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK)
     return set_berr(PDHGC_ERR_INVALID_ARG, "precision must be PDHGC_FP64 or PDHGC_FP32_BULK");
+  if (p.algorithm != PDHGC_ALG_AVERAGED)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched solver runs the averaged loop only");
   p.max_iters = tune_iters;
   p.eps_rel = -1.0;
   B->precision = p.precision;

@@ -32,6 +32,12 @@ struct Scalars {
   int at_check, at_limit, pi_zero, error;
   // last evaluation of the current (0) and average (1) point
   double kkt[2], rel_p[2], rel_d[2], rel_gap[2], rel_kkt[2], rP2[2];
+  // Halpern loop (algorithm == PDHGC_ALG_HALPERN): reflection, PID gains,
+  // fixed-point residual of the last check, of the anchor and of the
+  // previous check in this epoch, PID integral and last error
+  int algorithm;
+  double rho, pid_kp, pid_ki, pid_kd;
+  double fpr, fpr0, fpr_prev, pid_int, pid_eprev;
 };
 
 struct DevModel {
@@ -52,6 +58,18 @@ struct DevIter {
   double* sum_y;
   double* x_r;
   double* y_r;
+};
+
+// Halpern loop buffers: the PDHG output T(z) = (xp, yp) of a check step and
+// z - T(z) = (dx, dy); hw[i] = (t + i + 1) / (t + i + 2), the anchoring
+// weight of step i of the next chunk (t = steps since the anchor).  The
+// anchor is DevIter::x_r / y_r.
+struct DevHalpern {
+  double* xp;
+  double* yp;
+  double* dx;
+  double* dy;
+  double* hw;
 };
 
 
@@ -210,6 +228,90 @@ __device__ inline void decide_step(Scalars* S, const double* q, int mode) {
   S->t1_ns = global_ns();
 }
 
+// The Halpern loop's decision at a check, from the 14 folded quantities q of
+// EvalRowsH (0..6) and EvalColsH (7..13): the Section 2 ratios of T(z) (slot
+// 0; slot 1 repeats it), the fixed-point residual
+//   r = sqrt(|dx|^2 / tau + |dy|^2 / sigma + 2 dy' A_hat dx),
+// termination as in decide_step (the returned point is always T(z):
+// chosen = 2), then the restart test on r against the anchor's residual
+// fpr0 and the previous check's fpr_prev, with the PID primal-weight update
+// on a restart.  mode 0 (the start point's probe) only records fpr0.
+__device__ inline void decide_halpern(Scalars* S, const double* q, int mode) {
+  const double om = S->omega;
+  const double nrp2 = q[0], rP2 = sqrt(q[1]), by = q[3], dy0 = q[4], dy2 = q[5], cross = q[6];
+  const double nrd2 = q[7], rD2 = sqrt(q[8]), cx = q[10], bnd = q[11], dx0 = q[12], dx2 = q[13];
+  const double pobj = cx, dobj = by + bnd, gap = pobj - dobj;
+  S->kkt[0] = sqrt(om * nrp2 + nrd2 / om + gap * gap);
+  S->rP2[0] = rP2;
+  S->rel_p[0] = rP2 / (1.0 + S->nb);
+  S->rel_d[0] = rD2 / (1.0 + S->nc);
+  S->rel_gap[0] = fabs(gap) / (1.0 + fabs(pobj) + fabs(dobj));
+  S->rel_kkt[0] = fmax(S->rel_p[0], fmax(S->rel_d[0], S->rel_gap[0]));
+  S->kkt[1] = S->kkt[0];
+  S->rP2[1] = S->rP2[0];
+  S->rel_p[1] = S->rel_p[0];
+  S->rel_d[1] = S->rel_d[0];
+  S->rel_gap[1] = S->rel_gap[0];
+  S->rel_kkt[1] = S->rel_kkt[0];
+  const double r = sqrt(fmax(dx2 / S->tau + dy2 / S->sigma + 2.0 * cross, 0.0));
+  S->fpr = r;
+  if (mode == 0) {
+    S->fpr0 = r;
+    S->fpr_prev = INFINITY;
+    return;
+  }
+  S->restart_to = 0;
+  const double elapsed = (double)(global_ns() - S->t0_ns) * 1e-9;
+  const bool finite = isfinite(S->kkt[0]) && isfinite(r);
+  if (S->phase == 0) {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_NUMERICAL; S->chosen = 2;
+    } else if (S->at_check && S->rel_kkt[0] <= S->eps_rel) {
+      S->done = 1; S->status = PDHGC_STATUS_OPTIMAL; S->chosen = 2;
+    } else if (S->at_limit) {
+      S->done = 1; S->status = PDHGC_STATUS_ITER_LIMIT; S->chosen = 2;
+    } else if (elapsed > S->time_limit_s) {
+      S->done = 1; S->status = PDHGC_STATUS_TIME_LIMIT; S->chosen = 2;
+    }
+  } else {
+    if (!finite) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 2;
+    } else if (S->at_check && S->k >= S->min_iters) {
+      const bool met = S->stop_rule == 1 ? S->rel_kkt[0] <= S->eps_rel : rP2 <= S->eps_rel * (1.0 + S->nb);
+      if (met) {
+        S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 2;
+      }
+    }
+    if (!S->done && (S->at_limit || elapsed > S->time_limit_s)) {
+      S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 2;
+    }
+  }
+  if (!S->done) {
+    const bool restart = r <= S->beta_suff * S->fpr0 || (r <= S->beta_nec * S->fpr0 && r > S->fpr_prev) ||
+                         (double)S->t >= S->beta_art * (double)S->k;
+    if (!restart) {
+      S->fpr_prev = r;
+    } else {
+      const double dx = sqrt(dx0), dy = sqrt(dy0);
+      if (dx > 1e-10 && dy > 1e-10) {
+        const double e = log(om) - log(dy / dx);
+        S->pid_int += e;
+        const double lo = log(om) - (S->pid_kp * e + S->pid_ki * S->pid_int + S->pid_kd * (e - S->pid_eprev));
+        S->pid_eprev = e;
+        S->omega = exp(lo);
+      }
+      S->fpr0 = r;
+      S->fpr_prev = INFINITY;
+      S->t = 0;
+      S->restarts += 1;
+      S->restart_to = 3;
+      S->tau = S->eta / S->omega;
+      S->sigma = S->eta * S->omega;
+    }
+  }
+  S->t1_ns = global_ns();
+}
+
 // ---------------------------------------------------------------------------
 // The SpMV kernel
 //
@@ -221,7 +323,7 @@ __device__ inline void decide_step(Scalars* S, const double* q, int mode) {
 //              slice's rows is contiguous, so every value / index load of a
 //              warp is one coalesced 256 + 128-byte access, there is no
 //              shared memory and no barrier, and a row costs exactly one FMA
-//              per nonzero; eight gathers are kept in flight per lane
+//              per nonzero; PDHGC_GATHER_BATCH gathers are kept in flight per lane
 // The row sum goes straight into the operator's fused epilogue, and the
 // epilogue's partial sums are folded per block in a fixed order.
 //
@@ -688,6 +790,171 @@ struct EvalColsOp {
       part[6 * wv + 4] += bnd;
       part[6 * wv + 5] += d * d;
     }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The Halpern loop (PDHGC_ALG_HALPERN): one step from z = (x, y) forms the
+// PDHG output T(z) = (x+, y+) exactly as PrimalOp / DualOp do, then moves z
+// to the anchored combination
+//   z <- w ((1 + rho) T(z) - rho z) + (1 - w) z_0,  w = hw[it],
+// evaluated as z_0 + w (r - z_0) with r = T(z) + rho (T(z) - z).  A check
+// step (the last of a chunk, or of the phase) also stores T(z) and z - T(z)
+// for the evaluation; `probe` forms T(z) of the start point only, leaving z.
+// ---------------------------------------------------------------------------
+struct PrimalOpH {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const Scalars* S;
+  int it, last_it, probe;
+  const double* __restrict__ y;
+  DevModel md;
+  DevIter w;
+  DevHalpern h;
+  __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
+  __device__ const double* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  struct Pre {
+    double c, l, u, x, x0, tau, wt, rho;
+    bool last;
+  };
+  __device__ Pre prefetch(int j) const {
+    const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
+    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.x_r[j], S->tau, h.hw[it], S->rho, last};
+  }
+  __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
+    const double g = p.c - a.v[0];
+    const double xn = clamp_i(p.x - p.tau * g, p.l, p.u);
+    w.xbar[j] = 2.0 * xn - p.x;
+    if (!probe) {
+      const double r = fma(p.rho, xn - p.x, xn);
+      w.x[j] = fma(p.wt, r - p.x0, p.x0);
+    }
+    if (p.last) {
+      h.xp[j] = xn;
+      h.dx[j] = p.x - xn;
+    }
+  }
+};
+
+struct DualOpH {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  const Scalars* S;
+  int it, last_it, probe;
+  const double* __restrict__ xbar;
+  DevModel md;
+  DevIter w;
+  DevHalpern h;
+  __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
+  __device__ const double* gsrc(int) const { return xbar; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  struct Pre {
+    double b, y, y0, sigma, wt, rho;
+    bool ge, last;
+  };
+  __device__ Pre prefetch(int i) const {
+    const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
+    return Pre{md.bhat[i], w.y[i], w.y_r[i], S->sigma, h.hw[it], S->rho, md.ge[i] != 0, last};
+  }
+  __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
+    double yn = p.y + p.sigma * (p.b - a.v[0]);
+    if (p.ge && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
+    if (!probe) {
+      const double r = fma(p.rho, yn - p.y, yn);
+      w.y[i] = fma(p.wt, r - p.y0, p.y0);
+    }
+    if (p.last) {
+      h.yp[i] = yn;
+      h.dy[i] = p.y - yn;
+    }
+  }
+};
+
+// Halpern check, rows: r_hat = b_hat - A_hat x+ (max(., 0) on '>' rows),
+//   r_hat^2, (r_hat/D_r)^2, max |r_hat/D_r|, b_hat y+, (y+ - y_0)^2,
+//   dy^2 and dy (A_hat dx) for the metric residual
+struct EvalRowsH {
+  using Acc = SumD<2>;
+  static constexpr int NQ = 7;
+  static constexpr unsigned kMaxMask = 1u << 2;
+  const Scalars* S;
+  DevHalpern h;
+  const double* __restrict__ y_r;
+  DevModel md;
+  __device__ bool skip() const { return S->done; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  static constexpr int NG = 2;
+  using VT = double;
+  using GT = double;
+  __device__ const double* gsrc(int i) const { return i == 0 ? h.xp : h.dx; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 2>& g) const {
+    a.v[0] = fma(v, g.v[0], a.v[0]);
+    a.v[1] = fma(v, g.v[1], a.v[1]);
+  }
+  __device__ void epilogue(int i, const Acc& a, double* part) const {
+    const double b = md.bhat[i], dr = md.Dr[i];
+    double r = b - a.v[0];
+    if (md.ge[i]) r = fmax(r, 0.0);
+    const double ru = r / dr;
+    const double yp = h.yp[i], dy = h.dy[i];
+    const double d = yp - y_r[i];
+    part[0] += r * r;
+    part[1] += ru * ru;
+    part[2] = fmax(part[2], fabs(ru));
+    part[3] += b * yp;
+    part[4] += d * d;
+    part[5] += dy * dy;
+    part[6] += dy * a.v[1];
+  }
+};
+
+// Halpern check, columns: lam = c_hat - A_hat' y+, z = proj(lam), r_D = lam - z,
+//   r_D^2, (r_D/D_c)^2, max |r_D/D_c|, c_hat x+, l z^+ - u z^- (finite
+//   bounds), (x+ - x_0)^2, dx^2; optionally z of T(z) for the restart history
+struct EvalColsH {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 7;
+  static constexpr unsigned kMaxMask = 1u << 2;
+  const Scalars* S;
+  DevHalpern h;
+  const double* __restrict__ x_r;
+  DevModel md;
+  double* __restrict__ z_out;
+  __device__ bool skip() const { return S->done; }
+  __device__ double row_ctx(int) const { return 0.0; }
+  static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
+  __device__ const double* gsrc(int) const { return h.yp; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double* part) const {
+    const double c = md.chat[j], l = md.lhat[j], u = md.uhat[j], dc = md.Dc[j];
+    const double lam = c - a.v[0];
+    const double z = proj_dual(lam, l, u);
+    if (z_out) z_out[j] = z;
+    const double rd = lam - z;
+    const double rdu = rd / dc;
+    const double xp = h.xp[j], dx = h.dx[j];
+    const double bnd = (l != -INFINITY ? l * fmax(z, 0.0) : 0.0) - (u != INFINITY ? u * fmax(-z, 0.0) : 0.0);
+    const double d = xp - x_r[j];
+    part[0] += rd * rd;
+    part[1] += rdu * rdu;
+    part[2] = fmax(part[2], fabs(rdu));
+    part[3] += c * xp;
+    part[4] += bnd;
+    part[5] += d * d;
+    part[6] += dx * dx;
   }
 };
 

@@ -226,6 +226,8 @@ struct PhaseInit {
   long long max_iters, min_iters;
   int check_period, phase, stop_rule;
   int use_cc2;  // corner: primal weight from ||c_hat'|| (cc2[0]) and ||c'|| (cc2[1])
+  int algorithm;  // PDHGC_ALG_*
+  double rho, pid_kp, pid_ki, pid_kd;  // Halpern loop
 };
 
 __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
@@ -261,7 +263,24 @@ __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
   S->at_limit = 0;
   S->error = 0;
   S->kkt_prev = INFINITY;
+  S->algorithm = pi.algorithm;
+  S->rho = pi.rho;
+  S->pid_kp = pi.pid_kp;
+  S->pid_ki = pi.pid_ki;
+  S->pid_kd = pi.pid_kd;
+  S->fpr = S->fpr0 = 0.0;
+  S->fpr_prev = INFINITY;
+  S->pid_int = 0.0;
+  S->pid_eprev = 0.0;
   S->t0_ns = global_ns();
+}
+
+// Halpern loop: the anchoring weights (t + i + 1) / (t + i + 2) of the
+// steps i < P of the next chunk, t = steps since the anchor
+__global__ void k_halpern_weights(const Scalars* S, double* hw, int P) {
+  if (S->done) return;
+  const long long t = S->t;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) hw[i] = (double)(t + i + 1) / (double)(t + i + 2);
 }
 
 // after a chunk of iterations: iteration counters and 1/t for the averages
@@ -310,6 +329,30 @@ __global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, con
   if (use_handle) cudaGraphSetConditional(h, S->done ? 0u : 1u);
 }
 
+// Fold the 7 + 7 Halpern check quantities, then decide_halpern.
+__global__ void k_decide_h(Scalars* S, const double* __restrict__ pA, int ntA, const double* __restrict__ pT,
+                           int ntT, int mode, cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ double s_tmp[32];
+  __shared__ double q[14];
+  if (S->done) {
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  for (int qi = 0; qi < 7; ++qi) {
+    const double v = block_fold(pA + (size_t)qi * ntA, ntA, qi == 2, s_tmp);
+    if (threadIdx.x == 0) q[qi] = v;
+    __syncthreads();
+  }
+  for (int qi = 0; qi < 7; ++qi) {
+    const double v = block_fold(pT + (size_t)qi * ntT, ntT, qi == 2, s_tmp);
+    if (threadIdx.x == 0) q[7 + qi] = v;
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  decide_halpern(S, q, mode);
+  if (mode != 0 && use_handle) cudaGraphSetConditional(h, S->done ? 0u : 1u);
+}
+
 // restart history of phase 1 (guidance features): slot e mod 8 holds
 // (x_hat, z_hat) of restart point e, the start point being e = 0
 struct RingRec {
@@ -319,12 +362,30 @@ struct RingRec {
   const double* z_avg;
 };
 
-// restart: jump to the candidate, new restart point, sums cleared
-__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter32 w32, RingRec rr) {
+// restart: jump to the candidate, new restart point, sums cleared.
+// restart_to 3 (Halpern loop): the iterate and the anchor become T(z).
+__global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter32 w32, RingRec rr, DevHalpern hz) {
   const int rt = S->restart_to;
   if (rt == 0 || S->done) return;
-  const double inv_t = S->inv_t;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rt == 3) {
+    if (i < n) {
+      const double xn = hz.xp[i];
+      w.x[i] = xn;
+      w.x_r[i] = xn;
+      if (rr.rx) {
+        const size_t slot = (size_t)(S->restarts % 8) * (size_t)n;
+        rr.rx[slot + i] = (float)xn;
+        rr.rz[slot + i] = (float)rr.z_cur[i];
+      }
+    }
+    if (i < m) {
+      w.y[i] = hz.yp[i];
+      w.y_r[i] = hz.yp[i];
+    }
+    return;
+  }
+  const double inv_t = S->inv_t;
   if (i < n) {
     const double xn = rt == 2 ? w.sum_x[i] * inv_t : w.x[i];
     w.x[i] = xn;
@@ -372,16 +433,20 @@ __global__ void k_ring_init(int n, const double* __restrict__ x, RingRec rr) {
 // corner limit)
 // The returned x is clamped to the phase's box: an average of FP32-bulk
 // iterates may lie an FP32 ulp outside it (a no-op for the FP64 iteration)
+// (chosen 2, Halpern loop: the PDHG output T(z) of the last check)
 __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo, double* yo,
                            const double* x_fallback, const double* __restrict__ lhat,
-                           const double* __restrict__ uhat) {
+                           const double* __restrict__ uhat, DevHalpern hz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool out = S->chosen == 2;
   const bool avg = S->chosen == 1 && S->t > 0;
   const double inv_t = S->inv_t;
   const bool fallback = x_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
-  if (i < n)
-    xo[i] = fallback ? x_fallback[i] : fmin(fmax(avg ? w.sum_x[i] * inv_t : w.x[i], lhat[i]), uhat[i]);
-  if (yo && i < m) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
+  if (i < n) {
+    const double xv = out ? hz.xp[i] : (avg ? w.sum_x[i] * inv_t : w.x[i]);
+    xo[i] = fallback ? x_fallback[i] : fmin(fmax(xv, lhat[i]), uhat[i]);
+  }
+  if (yo && i < m) yo[i] = out ? hz.yp[i] : (avg ? w.sum_y[i] * inv_t : w.y[i]);
 }
 
 // Section 3: a '>' row whose dual is non-trivial becomes '='.  ax (optional,
@@ -547,6 +612,9 @@ struct pdhgc_lp {
   int *row_perm = nullptr, *col_perm = nullptr;
   // iterates
   DevIter it{};
+  // Halpern-loop buffers, allocated on the first Halpern solve
+  bool have_h = false;
+  DevHalpern hz{};
   // FP32-bulk buffers, allocated on the first FP32 solve
   bool have32 = false;
   Iter32 it32{};
@@ -762,6 +830,26 @@ int launch_eval(pdhgc_lp* lp, const DevModel& md, cudaStream_t st, bool record_z
   return PDHGC_OK;
 }
 
+// the Halpern check: T(z) and z - T(z) of the last step against the anchor
+int launch_eval_h(pdhgc_lp* lp, const DevModel& md, cudaStream_t st, bool record_z) {
+  const DevIter& w = lp->it;
+  RET(launch_tiles(lp, false, true, EvalRowsH{lp->S, lp->hz, w.y_r, md}, lp->pA, st));
+  RET(launch_tiles(lp, true, true, EvalColsH{lp->S, lp->hz, w.x_r, md, record_z ? lp->z_cur : nullptr}, lp->pT,
+                   st));
+  return PDHGC_OK;
+}
+
+int ensure_halpern(pdhgc_lp* lp) {
+  if (lp->have_h) return PDHGC_OK;
+  RET(lp->alloc(&lp->hz.xp, (size_t)lp->n));
+  RET(lp->alloc(&lp->hz.yp, (size_t)lp->m));
+  RET(lp->alloc(&lp->hz.dx, (size_t)lp->n));
+  RET(lp->alloc(&lp->hz.dy, (size_t)lp->m));
+  RET(lp->alloc(&lp->hz.hw, (size_t)4096));
+  lp->have_h = true;
+  return PDHGC_OK;
+}
+
 // Runs one phase: init, the device-driven loop graph, finalize.
 int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi,
               const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback) {
@@ -769,6 +857,9 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
+  const bool halpern = pi.algorithm == PDHGC_ALG_HALPERN;
+  if (halpern) RET(ensure_halpern(lp));
+  const DevHalpern hz = lp->hz;
   const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
                        lp->it32.ylo};
@@ -786,6 +877,17 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   if (ring) {
     k_ring_init<<<grid_for(n), 256, 0, st>>>(n, lp->it.x, rr);
     lp->launches++;
+    CKL();
+  }
+  if (halpern) {
+    // the anchor's fixed-point residual: T of the start point (not an
+    // iteration), its check quantities, and the first chunk's weights
+    RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
+    RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
+    RET(launch_eval_h(lp, md, st, false));
+    k_decide_h<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+    k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, pi.check_period);
+    lp->launches += 2;
     CKL();
   }
 
@@ -809,7 +911,13 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const int64_t before = lp->launches;
   int rc = PDHGC_OK;
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
-    if (fp32) {
+    if (halpern) {
+      const int last = pi.check_period - 1;
+      rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, nullptr, cs, true);
+      if (rc == PDHGC_OK)
+        rc = launch_tiles(lp, false, true, DualOpH{lp->S, i, last, 0, lp->it.xbar, md, lp->it, hz}, nullptr, cs,
+                          true);
+    } else if (fp32) {
       rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, i, lp->it32.y, md32, it32}, nullptr, cs, true);
       if (rc == PDHGC_OK)
         rc = launch_tiles(lp, false, true, DualOp32{lp->S, i, lp->it32.xbar, md32, it32}, nullptr, cs, true);
@@ -827,12 +935,19 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   if (rc == PDHGC_OK) {
     k_pre_check<<<1, 32, 0, cs>>>(lp->S);
     lp->launches++;
-    rc = launch_eval(lp, md, cs, ring);
+    rc = halpern ? launch_eval_h(lp, md, cs, ring) : launch_eval(lp, md, cs, ring);
   }
   if (rc == PDHGC_OK) {
-    k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
-    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr);
+    if (halpern)
+      k_decide_h<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
+    else
+      k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
+    k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr, hz);
     lp->launches += 2;
+    if (halpern) {
+      k_halpern_weights<<<1, 256, 0, cs>>>(lp->S, hz.hw, pi.check_period);
+      lp->launches++;
+    }
   }
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &captured);
@@ -844,7 +959,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   std::unique_ptr<CUgraphExec_st, void (*)(cudaGraphExec_t)> e_guard(exec,
                                                                     [](cudaGraphExec_t e) { cudaGraphExecDestroy(e); });
   CK(cudaGraphLaunch(exec, st));
-  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat);
+  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat, hz);
   lp->launches++;
   CKL();
   CK(cudaStreamSynchronize(st));
@@ -915,6 +1030,14 @@ int check_params(const pdhgc_params* p) {
     return set_err(PDHGC_ERR_INVALID_ARG, "parameter out of range");
   if (p->precision != PDHGC_FP64 && p->precision != PDHGC_FP32_BULK)
     return set_err(PDHGC_ERR_INVALID_ARG, "precision must be PDHGC_FP64 or PDHGC_FP32_BULK");
+  if (p->algorithm != PDHGC_ALG_AVERAGED && p->algorithm != PDHGC_ALG_HALPERN)
+    return set_err(PDHGC_ERR_INVALID_ARG, "algorithm must be PDHGC_ALG_AVERAGED or PDHGC_ALG_HALPERN");
+  if (p->algorithm == PDHGC_ALG_HALPERN) {
+    if (p->precision != PDHGC_FP64) return set_err(PDHGC_ERR_INVALID_ARG, "the Halpern loop runs in FP64 only");
+    if (!(p->reflection >= 0.0 && p->reflection <= 1.0) || !std::isfinite(p->pid_kp) ||
+        !std::isfinite(p->pid_ki) || !std::isfinite(p->pid_kd))
+      return set_err(PDHGC_ERR_INVALID_ARG, "reflection must lie in [0, 1] and the PID gains be finite");
+  }
   return PDHGC_OK;
 }
 
@@ -1018,6 +1141,11 @@ int corner_run(pdhgc_lp* lp, const pdhgc_corner_params& cp, const double* x_star
   pi.phase = 1;
   pi.stop_rule = cp.stop_rule;
   pi.use_cc2 = 1;
+  pi.algorithm = p.algorithm;
+  pi.rho = p.reflection;
+  pi.pid_kp = p.pid_kp;
+  pi.pid_ki = p.pid_ki;
+  pi.pid_kd = p.pid_kd;
   if (p.precision == PDHGC_FP32_BULK) {
     RET(to32(lp, lp->chat_c, lp->chat_c32, lp->n, st));
     RET(to32(lp, lp->lhat_c, lp->lhat_c32, lp->n, st));
@@ -1290,6 +1418,11 @@ void pdhgc_default_params(pdhgc_params* p) {
   p->ruiz_iters = 10;
   p->power_iters = 100;
   p->precision = PDHGC_FP64;
+  p->algorithm = PDHGC_ALG_AVERAGED;
+  p->reflection = 1.0;
+  p->pid_kp = 0.99;
+  p->pid_ki = 0.01;
+  p->pid_kd = 0.0;
 }
 
 void pdhgc_default_corner_params(pdhgc_corner_params* p) {
@@ -1464,6 +1597,11 @@ int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out) {
   pi.phase = 0;
   pi.stop_rule = 0;
   pi.use_cc2 = 0;
+  pi.algorithm = p.algorithm;
+  pi.rho = p.reflection;
+  pi.pid_kp = p.pid_kp;
+  pi.pid_ki = p.pid_ki;
+  pi.pid_kd = p.pid_kd;
   RET(run_phase(lp, model_orig(lp), model32_orig(lp), pi, nullptr, nullptr, lp->x1, lp->y1, nullptr));
   pdhgc_report r{};
   RET(fill_phase_report(lp, &r));
@@ -1648,7 +1786,7 @@ int pdhgc_get_state(pdhgc_lp* lp, void* buf, size_t* bytes) {
   }
   StateHeader h{};
   std::memcpy(h.magic, kStateMagic, 8);
-  h.version = 1;
+  h.version = 2;  // 2: pdhgc_params carries the inner-loop fields
   h.m = m;
   h.n = n;
   h.nnz = lp->nnz;
@@ -1683,7 +1821,7 @@ int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes) {
   if (bytes < sizeof(StateHeader)) return set_err(PDHGC_ERR_INVALID_ARG, "state buffer too short");
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 2)
     return set_err(PDHGC_ERR_INVALID_ARG, "not a pdhgc state (magic or version)");
   if (h.m != m || h.n != n || h.nnz != lp->nnz || bytes != state_bytes(m, n))
     return set_err(PDHGC_ERR_INVALID_ARG, "state was taken from an LP of another shape");
@@ -1785,6 +1923,8 @@ int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double
   CK(cudaMemcpyAsync(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const double inv_t = S.t > 0 ? 1.0 / (double)S.t : 0.0;
+  // after a Halpern-loop phase the second pair is the PDHG output T(z)
+  const bool out = S.algorithm == PDHGC_ALG_HALPERN && lp->have_h;
   struct V {
     double* dst;
     const double* src;
@@ -1793,8 +1933,8 @@ int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double
     double scale;
   } vs[4] = {{x, lp->it.x, lp->col_perm, n, 1.0},
              {y, lp->it.y, lp->row_perm, m, 1.0},
-             {x_avg, lp->it.sum_x, lp->col_perm, n, inv_t},
-             {y_avg, lp->it.sum_y, lp->row_perm, m, inv_t}};
+             {x_avg, out ? lp->hz.xp : lp->it.sum_x, lp->col_perm, n, out ? 1.0 : inv_t},
+             {y_avg, out ? lp->hz.yp : lp->it.sum_y, lp->row_perm, m, out ? 1.0 : inv_t}};
   for (const V& v : vs) {
     if (!v.dst) continue;
     double* tmp = v.len == n ? lp->tmp_n : lp->tmp_m;
@@ -1907,6 +2047,7 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   cudaStream_t st = lp->stream;
   const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
+  const bool halpern = lp->params.algorithm == PDHGC_ALG_HALPERN && lp->have_h;
   const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
   const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
                        lp->it32.ylo};
@@ -1924,13 +2065,18 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   int rc = PDHGC_OK;
   for (int i = 0; i < iters && rc == PDHGC_OK; ++i) {
     CK(cudaEventRecord(ev[3 * i], st));
-    if (fp32)
+    // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
+    if (halpern)
+      rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, nullptr, st);
+    else if (fp32)
       rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, 0, lp->it32.y, md32, it32}, nullptr, st);
     else
       rc = launch_tiles(lp, true, true, PrimalOp{lp->S, 0, lp->it.y, md, lp->it}, nullptr, st);
     if (rc != PDHGC_OK) break;
     CK(cudaEventRecord(ev[3 * i + 1], st));
-    if (fp32)
+    if (halpern)
+      rc = launch_tiles(lp, false, true, DualOpH{lp->S, 0, 1, 0, lp->it.xbar, md, lp->it, lp->hz}, nullptr, st);
+    else if (fp32)
       rc = launch_tiles(lp, false, true, DualOp32{lp->S, 0, lp->it32.xbar, md32, it32}, nullptr, st);
     else
       rc = launch_tiles(lp, false, true, DualOp{lp->S, 0, lp->it.xbar, md, lp->it}, nullptr, st);

@@ -36,6 +36,7 @@ STATUS_NAMES = {0: "NONE", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "TIME_LIMIT", 4: "N
 GUIDE_FEATURES, GUIDE_FEAT_STRIDE, GUIDE_PARAMS = 18, 32, 5441
 FP64, FP32_BULK = 0, 1
 PHASE1, CORNER = 0, 1
+AVERAGED, HALPERN = 0, 1  # pdhgc_params.algorithm (PDHGC_ALG_*)
 
 
 class PdhgcError(RuntimeError):
@@ -51,7 +52,8 @@ class Params(C.Structure):
                 ("check_period", C.c_int32), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("theta", C.c_double), ("eta_factor", C.c_double),
                 ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("algorithm", C.c_int32), ("reflection", C.c_double), ("pid_kp", C.c_double),
+                ("pid_ki", C.c_double), ("pid_kd", C.c_double)]
 
 
 class CornerParams(C.Structure):
@@ -248,6 +250,7 @@ class LP:
         return x, y, z
 
     def get_iterates(self, device: bool = False):
+        """Scaled iterates; x_avg / y_avg hold T(z) after a Halpern-loop phase."""
         (x, y, xa, ya), ptrs = self._outs([self.n, self.m, self.n, self.m], device)
         it = (C.c_int64 * 3)()
         _check(lib.pdhgc_get_iterates(self._h, *ptrs, C.cast(it, _vp), int(device)), "pdhgc_get_iterates")

@@ -44,6 +44,12 @@ def test_default_params_match_the_paper_and_readings(lib):
     p = P.default_params()
     assert p.eps_rel == 1e-6 and p.check_period == 64 and p.ruiz_iters == 10 and p.power_iters == 100
     assert (p.beta_suff, p.beta_nec, p.beta_art, p.theta, p.eta_factor) == (0.2, 0.8, 0.36, 0.5, 0.998)
+    # the inner loop defaults to the averaged one; the Halpern loop's readings
+    import oracle.halpern as H
+    assert p.algorithm == P.AVERAGED
+    assert (p.reflection, p.pid_kp, p.pid_ki, p.pid_kd) == (
+        H.HALPERN_DEFAULTS["reflection"], H.HALPERN_DEFAULTS["pid_kp"],
+        H.HALPERN_DEFAULTS["pid_ki"], H.HALPERN_DEFAULTS["pid_kd"])
     cp = P.default_corner_params()
     assert cp.eps_abs == 1e-6 and cp.min_iters == 100 and cp.obj_scale == 1.0
     assert cp.stop_rule == 0 and cp.row_rule == 0  # the Section 3.1 stop and Section 3 row rules

@@ -1,0 +1,154 @@
+"""The Halpern loop (PDHGC_ALG_HALPERN) of the CUDA path against the oracle's
+(oracle.halpern), through the C-ABI (needs a GB300).
+
+Same bar as the averaged loop: iterates after 100 steps to 1e-10 relative
+(both sides run the same FP64 steps; they differ in rounding order only, and
+the anchored combination z_0 + w (r - z_0) on the device is w r + (1 - w) z_0
+in the oracle), equal iteration counts, restarts, statuses and metric counts.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import guide as oguide
+from tests.test_gpu_parity import ITER_TOL, _lp_cases, rel_err
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2511_13894_gb300.pdhgc")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+HP = dict(algorithm="halpern")
+
+
+@pytest.mark.parametrize("name", list(_lp_cases()))
+def test_halpern_iterates_after_100_match_oracle(name):
+    lp = _lp_cases()[name]()
+    ref = oracle.run_iterations(lp, 100, HP)
+    s = ref["state"]
+    g = P.lp_from_dict(lp)
+    rep = g.solve(max_iters=100, eps_rel=-1.0, algorithm=P.HALPERN)
+    assert rep["status_name"] == "ITER_LIMIT" and rep["iters"] == 100 and rep["chosen"] == 2
+    it = g.get_iterates()
+    assert it["k"] == 100 and it["t"] == s.t and it["restarts"] == s.restarts
+    assert s.restarts >= 1  # the first check always restarts (t = k)
+    assert rel_err(it["x"], s.x) <= ITER_TOL
+    assert rel_err(it["y"], s.y) <= ITER_TOL
+    # the PDHG output of the last step, which the phase returns
+    assert rel_err(it["x_avg"], s.xp) <= ITER_TOL
+    assert rel_err(it["y_avg"], s.yp) <= ITER_TOL
+    # the primal weight after the PID update(s)
+    assert abs(g.get_scaling()["omega"] - s.omega) <= 1e-10 * s.omega
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed", "transport_30x70"])
+def test_halpern_full_solve_matches_oracle(name):
+    lp = _lp_cases()[name]()
+    ref = oracle.solve(lp, HP)
+    g = P.lp_from_dict(lp)
+    rep = g.solve(algorithm=P.HALPERN)
+    assert rep["status_name"] == "OPTIMAL" and ref["status"] == oracle.OPTIMAL
+    assert rep["iters"] == ref["iters"] and rep["restarts"] == ref["restarts"]
+    assert rep["rel_kkt"] <= 1e-6
+    x, y, z = g.get_solution()
+    xo, yo, zo = oracle.unscale(ref["model"], ref["x_hat"], ref["y_hat"])
+    assert rel_err(x, xo) <= 1e-8 and rel_err(y, yo) <= 1e-8 and rel_err(z, zo) <= 1e-8
+    orep = oracle.kkt_report(ref["model"], ref["x_hat"], ref["y_hat"])
+    for k in ("rP2", "rD2", "pobj", "dobj"):
+        assert abs(rep[k] - orep[k]) <= 1e-7 * (1.0 + abs(orep[k])), k
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure"):
+        assert rep[k] == orep[k], k
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq"])
+@pytest.mark.parametrize("row_rule", [0, 1])
+def test_halpern_corner_phase_matches_oracle(name, row_rule):
+    lp = _lp_cases()[name]()
+    ref1 = oracle.solve(lp, HP)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=11, row_rule=row_rule))
+    g = P.lp_from_dict(lp)
+    g.solve(algorithm=P.HALPERN)
+    rep = g.corner_phase(obj_seed=11, row_rule=row_rule)
+    assert rep["status_name"] == "CORNER_DONE" and refc["status"] == oracle.CORNER_DONE
+    assert rep["iters"] == refc["iters"] and rep["restarts"] == refc["restarts"]
+    x, y, z = g.get_solution(P.CORNER)
+    xo, yo, zo = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+    assert rel_err(x, xo) <= 1e-7
+    orep = oracle.kkt_report(ref1["model"], refc["x_hat"], refc["y_hat"])
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure", "primal_push_est"):
+        assert rep[k] == orep[k], k
+
+
+def test_halpern_corner_limit_keeps_the_phase1_point():
+    lp = _lp_cases()["bounded_ineq"]()
+    ref1 = oracle.solve(lp, HP)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=11, max_iters=128))
+    g = P.lp_from_dict(lp)
+    g.solve(algorithm=P.HALPERN)
+    rep = g.corner_phase(obj_seed=11, max_iters=128)
+    assert rep["status_name"] == "CORNER_LIMIT" and refc["status"] == oracle.CORNER_LIMIT
+    x1 = g.get_solution(P.PHASE1)[0]
+    assert np.array_equal(g.get_solution(P.CORNER)[0], x1)
+
+
+def test_halpern_edge_shapes():
+    one = dict(m=1, n=1, row_ptr=np.array([0, 1]), col_idx=np.array([0], dtype=np.int32), val=np.array([2.0]),
+               b=np.array([3.0]), c=np.array([1.0]), lb=np.zeros(1), ub=np.full(1, np.inf),
+               sense=np.array([oracle.EQ], dtype=np.int8))
+    empty_row = dict(m=3, n=2, row_ptr=np.array([0, 2, 2, 3]), col_idx=np.array([0, 1, 1], dtype=np.int32),
+                     val=np.array([1.0, 1.0, 1.0]), b=np.array([1.0, 0.0, 0.25]), c=np.array([1.0, 2.0]),
+                     lb=np.zeros(2), ub=np.full(2, np.inf),
+                     sense=np.array([oracle.EQ, oracle.EQ, oracle.GE], dtype=np.int8))
+    no_nnz = dict(m=1, n=2, row_ptr=np.array([0, 0]), col_idx=np.zeros(0, dtype=np.int32), val=np.zeros(0),
+                  b=np.array([0.0]), c=np.array([1.0, -1.0]), lb=np.array([0.0, -1.0]), ub=np.array([5.0, 2.0]),
+                  sense=np.array([oracle.EQ], dtype=np.int8))
+    for lp in (one, empty_row, no_nnz):
+        ref = oracle.run_iterations(lp, 100, HP)
+        g = P.lp_from_dict(lp)
+        g.solve(max_iters=100, eps_rel=-1.0, algorithm=P.HALPERN)
+        it = g.get_iterates()
+        s = ref["state"]
+        assert rel_err(it["x"], s.x) <= ITER_TOL and rel_err(it["y"], s.y) <= ITER_TOL
+        full = oracle.solve(lp, HP)
+        rep = P.lp_from_dict(lp).solve(algorithm=P.HALPERN)
+        assert rep["status"] == full["status"] and rep["iters"] == full["iters"]
+
+
+def test_halpern_restart_history_feeds_the_guidance_features():
+    # the ring of restart points (T(z) at each restart) matches the oracle's
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(5), 5)
+    r1 = oracle.solve(lp, HP)
+    g = P.lp_from_dict(lp)
+    rep = g.solve(algorithm=P.HALPERN)
+    assert rep["iters"] == r1["iters"] and rep["restarts"] == r1["restarts"]
+    feat, elig = g.guide_features(obj_seed=7)
+    F, E = oguide.features(r1, dict(obj_seed=7))
+    bits = feat.view(torch.int16).cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    got = bits.view(np.float32).astype(np.float64)[:, :18]
+    assert np.all(np.abs(got - F) <= 2.0 ** -7 * np.abs(F) + 1e-30)
+    assert np.array_equal(elig.cpu().numpy().astype(bool), E)
+
+
+def test_halpern_refused_where_not_built():
+    lp = lpgen.small_face_lp(0)
+    g = P.lp_from_dict(lp)
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK)
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        g.solve(algorithm=P.HALPERN, reflection=1.5)
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        g.solve(algorithm=7)
+    B = P.Batch([lpgen.batch_lp(i) for i in range(2)])
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        B.solve(algorithm=P.HALPERN)
+
+
+def test_halpern_profile_iteration_times_its_kernels():
+    lp = lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000)
+    g = P.lp_from_dict(lp)
+    g.solve(algorithm=P.HALPERN)
+    ms = g.profile_iteration(5)
+    assert ms[0] > 0.0 and ms[1] > 0.0
