@@ -237,14 +237,18 @@ def algorithmic_bytes_halpern(m, n, nnz):
 
 def fp64_ops_halpern(m, n, nnz):
     """FP64 operations per launch of the Halpern loop's kernels: one FMA per
-    nonzero plus the epilogue (primal: 7 per column; dual: 6 per row)."""
+    nonzero plus the epilogue (primal: c - A'y, the step, x_bar, then two
+    for the reflected point and two for the anchored combination, 7 per
+    column; dual: 6 per row)."""
     return nnz + 7 * n, nnz + 6 * m
 
 
 def fp64_ops(m, n, nnz):
     """FP64 operations per launch: one FMA per nonzero plus the epilogue
-    (primal: 6 per column; dual: 4 per row)."""
-    return nnz + 6 * n, nnz + 4 * m
+    (primal: c - A'y, the step, x_bar and the running sum, 4 per column;
+    dual: b - A x_bar, the step and the running sum, 3 per row; the clamps
+    run on the integer pipe)."""
+    return nnz + 4 * n, nnz + 3 * m
 
 
 def oracle_sample(model, p, eta, iters, algorithm):
