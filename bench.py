@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="both",
                     help="inner loop of the headline (averaged) and of an extra block (halpern); 'both' "
                          "adds the Halpern loop (FP64, the paper's row rule) beside the averaged arms")
+    ap.add_argument("--obj-scale-sweep", type=str, default=None,
+                    help="comma-separated corner objective scales (Section 5's study): one phase 1 with the "
+                         "headline loop, then one timed corner phase per scale; prints its own JSON line")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-iters", type=int, default=50)
     ap.add_argument("--cpu-iters", type=int, default=640,
@@ -495,6 +498,48 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
         print(json.dumps(out), flush=True)
 
 
+def run_obj_scale_sweep(args, g, P, torch, stream):
+    """Section 5's objective-scale study on the workload: Algorithm 1's random
+    objective is obj_scale * U[0,1).  Phase 1 runs once (headline loop); each
+    (scale, omega_rule) then gets one corner phase from the same phase-1
+    point, timed with CUDA events, reporting iterations, status, the corner
+    measure and the primal push estimate of its result.  omega_rule 0 starts
+    the corner phase's primal weight from the scaled objective (the phase is
+    then scale-equivariant); 1 keeps phase 1's weight, the setting in which
+    the scale changes the dual's share of the iteration."""
+    alg = P.HALPERN if headline_algorithm(args) == "halpern" else P.AVERAGED
+    r1 = g.solve(P.default_params(max_iters=args.phase1_max_iters, algorithm=alg))
+    rows_rule = 1 if args.corner_rows == "active" else 0
+
+    def cparams(scale, omega_rule):
+        return P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
+                                       obj_scale=scale, row_rule=rows_rule, omega_rule=omega_rule)
+
+    scales = [float(v) for v in args.obj_scale_sweep.split(",")]
+    g.corner_phase(cparams(scales[0], 1))  # warm-up
+    rows = []
+    for omega_rule in (1, 0):
+        for scale in scales:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = g.corner_phase(cparams(scale, omega_rule))
+            e1.record(stream)
+            e1.synchronize()
+            rows.append({"obj_scale": scale, "omega_rule": omega_rule, "status": rc["status_name"],
+                         "iters": rc["iters"], "restarts": rc["restarts"], "ms": e0.elapsed_time(e1),
+                         "corner_measure": rc["corner_measure"], "primal_push_est": rc["primal_push_est"],
+                         "candidates": rc["candidates"], "off_bound_p": rc["off_bound_p"],
+                         "rel_kkt": rc["rel_kkt"]})
+    print(json.dumps({"mode": "obj_scale_sweep", "workload": args.workload,
+                      "algorithm": "halpern" if alg == P.HALPERN else "averaged",
+                      "corner_rows": args.corner_rows, "corner_max_iters": args.corner_max_iters,
+                      "phase1": {"status": r1["status_name"], "iters": r1["iters"], "omega": r1["omega"],
+                                 "corner_measure": r1["corner_measure"], "primal_push_est": r1["primal_push_est"]},
+                      "runs": rows}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -544,6 +589,9 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"mode": "kernels", "workload": args.workload, "primal_ms": ms[0], "dual_ms": ms[1]}))
+        return
+    if args.obj_scale_sweep:
+        run_obj_scale_sweep(args, g, P, torch, stream)
         return
     cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
                                       row_rule=1 if args.corner_rows == "active" else 0)

@@ -127,6 +127,13 @@ typedef struct pdhgc_corner_params {
                               row also looks active at the phase-1 point, its slack (a_i x - b_i in the '>'
                               form) no larger than |y_i|, so that rows the phase-1 point is clearly off
                               keep their sense */
+    int32_t  omega_rule;   /* starting primal weight: 0 (default) ||c_hat'|| / ||b_hat|| of the corner
+                              model, as at a phase start; PDHG with omega proportional to ||c|| is
+                              scale-equivariant, so obj_scale then changes nothing beyond rounding (and,
+                              in the averaged loop, the gap term of its restart test).  1: phase 1's final
+                              primal weight, so that obj_scale rescales the dual's share of the
+                              iteration, the setting of Section 5's objective-scale study */
+    int32_t  reserved;
 } pdhgc_corner_params;
 
 /*
@@ -332,7 +339,8 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
  */
 int pdhgc_batch_solve(pdhgc_batch* batch, const pdhgc_params* params, pdhgc_report* reports);
 
-/* pdhgc_batch_corner_phase — Algorithm 1 for every LP (as pdhgc_corner_phase). */
+/* pdhgc_batch_corner_phase — Algorithm 1 for every LP (as pdhgc_corner_phase;
+ * omega_rule 0 only, INVALID_ARG otherwise). */
 int pdhgc_batch_corner_phase(pdhgc_batch* batch, const pdhgc_corner_params* params, pdhgc_report* reports);
 
 /* pdhgc_batch_get_solution — x (n) and y (m) of LP `lp`, user order, host pointers (either may be NULL). */

@@ -220,7 +220,8 @@ def run_iterations(lp, iters, params=None):
 def corner_phase(phase1, corner_params=None, hold=None):
     """Algorithm 1 with the Halpern loop: the corner model of
     `oracle.pdhg.corner_model`, a fresh anchor at (proj(x1), 0) with its
-    residual measured, the primal weight and PID state reset; stop once
+    residual measured, the primal weight (oracle.pdhg.corner_omega0) and PID
+    state reset; stop once
     k >= min_iters and the PDHG output of a check meets the Section 3.1
     primal rule (or the full test with stop_rule "kkt"); on a limit the
     phase-1 point is kept."""
@@ -232,7 +233,7 @@ def corner_phase(phase1, corner_params=None, hold=None):
     eta = phase1["eta"]
     x1, y1 = phase1["x_hat"], phase1["y_hat"]
     cm, info = P.corner_model(model, x1, y1, cp, hold)
-    s = HState(cm, P.project_box(x1, cm.lhat, cm.uhat), np.zeros(model.m), eta, P.initial_omega(cm))
+    s = HState(cm, P.project_box(x1, cm.lhat, cm.uhat), np.zeros(model.m), eta, P.corner_omega0(phase1, cm, cp))
     t0 = time.perf_counter()
     nb = float(np.linalg.norm(model.b_user))
     status, x_corner = None, None

@@ -70,6 +70,7 @@ CORNER_DEFAULTS = dict(
     obj_scale=1.0,       # Algorithm 1: obj = Uniform([0,1]^n); Section 5 studies smaller scales
     stop_rule="primal",  # Section 3.1 rule; "kkt" (full convergence) exists for tests only
     row_rule=0,          # 0: Section 3's row rule; 1: an option, only rows active at the phase-1 point
+    omega_rule=0,        # 0: omega_0 from the corner objective (reading); 1: keep phase 1's final omega
 )
 
 METRIC_TOL = 1e-6        # Section 4.2: both tolerances 1e-6
@@ -555,6 +556,19 @@ def corner_model(model: Model, x_hat1, y_hat1, cp, hold=None):
                     fixed=fix_up | fix_lo, held_mask=held)
 
 
+def corner_omega0(phase1, cm, cp):
+    """The corner phase's starting primal weight.  omega_rule 0 (reading):
+    ||c_hat'|| / ||b_hat|| of the corner model, as at a phase start; PDHG with
+    omega proportional to ||c|| is scale-equivariant (c, y and omega scaled
+    together leave the x iterates unchanged), so obj_scale then has no effect
+    beyond rounding and the averaged loop's gap term.  omega_rule 1: phase 1's
+    final primal weight, so that obj_scale rescales the dual's share of the
+    iteration, the setting of Section 5's objective-scale study."""
+    if cp.get("omega_rule", 0) == 1:
+        return phase1["state"].omega
+    return initial_omega(cm)
+
+
 def corner_phase(phase1, corner_params=None, hold=None):
     """Algorithm 1 on the phase-1 result: build M_hat, run PDHG from (x, 0)
     with the same step size, stop once k >= min_iters and the primal residual
@@ -573,7 +587,7 @@ def corner_phase(phase1, corner_params=None, hold=None):
     eta = phase1["eta"]
     x1, y1 = phase1["x_hat"], phase1["y_hat"]
     cm, info = corner_model(model, x1, y1, cp, hold)
-    s = State(cm, project_box(x1, cm.lhat, cm.uhat), np.zeros(model.m), eta, initial_omega(cm))
+    s = State(cm, project_box(x1, cm.lhat, cm.uhat), np.zeros(model.m), eta, corner_omega0(phase1, cm, cp))
     t0 = time.perf_counter()
     nb = float(np.linalg.norm(model.b_user))
     status = None

@@ -1271,6 +1271,8 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
       !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
       (cp.row_rule != 0 && cp.row_rule != 1))
     return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  if (cp.omega_rule != 0)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched corner phase starts omega from the corner objective only");
   cudaStream_t st = B->stream;
   std::fill(B->extc.begin(), B->extc.end(), 0);
   BatchParams bp = make_params(B->params, &cp);

@@ -228,6 +228,7 @@ struct PhaseInit {
   int use_cc2;  // corner: primal weight from ||c_hat'|| (cc2[0]) and ||c'|| (cc2[1])
   int algorithm;  // PDHGC_ALG_*
   double rho, pid_kp, pid_ki, pid_kd;  // Halpern loop
+  double omega0;  // > 0: the starting primal weight (corner omega_rule 1); else from ||c_hat|| / ||b_hat||
 };
 
 __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
@@ -246,7 +247,7 @@ __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
   S->check_period = pi.check_period;
   S->phase = pi.phase;
   S->stop_rule = pi.stop_rule;
-  S->omega = (nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0;
+  S->omega = pi.omega0 > 0.0 ? pi.omega0 : ((nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0);
   S->tau = S->eta / S->omega;
   S->sigma = S->eta * S->omega;
   S->k = 0;
@@ -1089,7 +1090,7 @@ int setup_mat(pdhgc_lp* lp, pdhgc_lp::Mat& M, const Csr& C, cudaStream_t st) {
 int check_corner_params(const pdhgc_corner_params& cp) {
   if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
       !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
-      (cp.row_rule != 0 && cp.row_rule != 1))
+      (cp.row_rule != 0 && cp.row_rule != 1) || (cp.omega_rule != 0 && cp.omega_rule != 1))
     return set_err(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
   return PDHGC_OK;
 }
@@ -1141,6 +1142,7 @@ int corner_run(pdhgc_lp* lp, const pdhgc_corner_params& cp, const double* x_star
   pi.phase = 1;
   pi.stop_rule = cp.stop_rule;
   pi.use_cc2 = 1;
+  pi.omega0 = cp.omega_rule == 1 ? lp->rep1.omega : 0.0;
   pi.algorithm = p.algorithm;
   pi.rho = p.reflection;
   pi.pid_kp = p.pid_kp;
@@ -1786,7 +1788,7 @@ int pdhgc_get_state(pdhgc_lp* lp, void* buf, size_t* bytes) {
   }
   StateHeader h{};
   std::memcpy(h.magic, kStateMagic, 8);
-  h.version = 2;  // 2: pdhgc_params carries the inner-loop fields
+  h.version = 3;  // 2: pdhgc_params carries the inner-loop fields; 3: corner omega_rule
   h.m = m;
   h.n = n;
   h.nnz = lp->nnz;
@@ -1821,7 +1823,7 @@ int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes) {
   if (bytes < sizeof(StateHeader)) return set_err(PDHGC_ERR_INVALID_ARG, "state buffer too short");
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 2)
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 3)
     return set_err(PDHGC_ERR_INVALID_ARG, "not a pdhgc state (magic or version)");
   if (h.m != m || h.n != n || h.nnz != lp->nnz || bytes != state_bytes(m, n))
     return set_err(PDHGC_ERR_INVALID_ARG, "state was taken from an LP of another shape");

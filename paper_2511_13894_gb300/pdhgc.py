@@ -59,7 +59,8 @@ class Params(C.Structure):
 class CornerParams(C.Structure):
     _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double), ("min_iters", C.c_int64),
                 ("max_iters", C.c_int64), ("time_limit_s", C.c_double), ("obj_seed", C.c_uint64),
-                ("obj_scale", C.c_double), ("stop_rule", C.c_int32), ("row_rule", C.c_int32)]
+                ("obj_scale", C.c_double), ("stop_rule", C.c_int32), ("row_rule", C.c_int32),
+                ("omega_rule", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Report(C.Structure):

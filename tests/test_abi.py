@@ -53,6 +53,7 @@ def test_default_params_match_the_paper_and_readings(lib):
     cp = P.default_corner_params()
     assert cp.eps_abs == 1e-6 and cp.min_iters == 100 and cp.obj_scale == 1.0
     assert cp.stop_rule == 0 and cp.row_rule == 0  # the Section 3.1 stop and Section 3 row rules
+    assert cp.omega_rule == 0  # omega_0 from the corner objective
     gp = P.GuideParams()
     P.lib.pdhgc_default_guide_params(P.C.byref(gp))
     assert gp.threshold == 0.9 and gp.fallback == 1 and gp.guided_max_iters == 0

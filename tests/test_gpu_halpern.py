@@ -152,3 +152,27 @@ def test_halpern_profile_iteration_times_its_kernels():
     g.solve(algorithm=P.HALPERN)
     ms = g.profile_iteration(5)
     assert ms[0] > 0.0 and ms[1] > 0.0
+
+
+@pytest.mark.parametrize("alg", ["averaged", "halpern"])
+@pytest.mark.parametrize("scale", [1e-6, 1e-2])
+def test_corner_omega_rule_matches_oracle(alg, scale):
+    # Section 5's objective-scale setting: the corner phase keeps phase 1's
+    # primal weight (omega_rule 1) and the random objective is scaled
+    lp = _lp_cases()["bounded_ineq"]()
+    ref1 = oracle.solve(lp, dict(algorithm=alg))
+    refc = oracle.corner_phase(ref1, dict(obj_seed=11, obj_scale=scale, omega_rule=1))
+    g = P.lp_from_dict(lp)
+    g.solve(algorithm=P.HALPERN if alg == "halpern" else P.AVERAGED)
+    rep = g.corner_phase(obj_seed=11, obj_scale=scale, omega_rule=1)
+    assert rep["status_name"] == "CORNER_DONE" and refc["status"] == oracle.CORNER_DONE
+    assert rep["iters"] == refc["iters"] and rep["restarts"] == refc["restarts"]
+    assert abs(rep["omega"] - refc["state"].omega) <= 1e-9 * refc["state"].omega
+    x, y, z = g.get_solution(P.CORNER)
+    xo, yo, zo = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+    assert rel_err(x, xo) <= 1e-7
+    orep = oracle.kkt_report(ref1["model"], refc["x_hat"], refc["y_hat"])
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure", "primal_push_est"):
+        assert rep[k] == orep[k], k
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        g.corner_phase(obj_seed=11, omega_rule=2)

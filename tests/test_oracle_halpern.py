@@ -221,3 +221,28 @@ def test_halpern_corner_primal_rule():
     assert np.all(xc[up] <= x1[up] * (1 + 1e-12) + 1e-15)
     assert np.all(xc[lo] >= x1[lo] * (1 - 1e-12) - 1e-15)
     assert np.array_equal(rc["y_hat"], r1["y_hat"])
+
+
+def test_corner_phase_is_scale_equivariant_with_the_objective_weight():
+    # omega_rule 0 starts omega at ||c_hat'|| / ||b_hat||, proportional to the
+    # objective's scale; scaling c, y and omega together leaves every x
+    # iterate unchanged, and the Halpern loop's restart test and PID weight are
+    # homogeneous in that scaling, so obj_scale changes nothing but rounding
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(3), 3)
+    r1 = oracle.solve(lp, HP)
+    runs = [oracle.corner_phase(r1, dict(obj_seed=11, obj_scale=sc)) for sc in (1.0, 1e-3, 1e-6)]
+    for rc in runs[1:]:
+        assert rc["iters"] == runs[0]["iters"] and rc["restarts"] == runs[0]["restarts"]
+        assert np.max(np.abs(rc["x_hat"] - runs[0]["x_hat"])) <= 1e-9 * (1 + np.max(np.abs(runs[0]["x_hat"])))
+
+
+@pytest.mark.parametrize("alg", ["averaged", "halpern"])
+def test_corner_omega_rule_keeps_the_phase1_weight(alg):
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(3), 3)
+    r1 = oracle.solve(lp, dict(algorithm=alg))
+    # one step, stopped at its limit before any restart: omega is the start value
+    kept = oracle.corner_phase(r1, dict(obj_seed=11, obj_scale=1e-4, omega_rule=1, max_iters=1))
+    fresh = oracle.corner_phase(r1, dict(obj_seed=11, obj_scale=1e-4, omega_rule=0, max_iters=1))
+    assert kept["state"].omega == r1["state"].omega
+    assert fresh["state"].omega == oracle.initial_omega(fresh["corner_model"])
+    assert fresh["state"].omega != kept["state"].omega
