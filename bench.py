@@ -70,8 +70,10 @@ def parse():
     ap.add_argument("--phase1-max-iters", type=int, default=1_000_000)
     ap.add_argument("--corner-max-iters", type=int, default=200_000)
     ap.add_argument("--corner-seed", type=int, default=1)
-    ap.add_argument("--no-row-option", action="store_true",
-                    help="skip the extra arms that time the corner phase with the row_rule = 1 option")
+    ap.add_argument("--row-option", action="store_true",
+                    help="add the averaged loop's arms (FP64, FP32 bulk) that time the corner phase with the "
+                         "row_rule = 1 option (kept out of the default run to hold its timed work near a minute)")
+    ap.add_argument("--no-row-option", action="store_true", help="leave the row-option arms out (the default)")
     ap.add_argument("--corner-rows", choices=["paper", "active"], default="paper",
                     help="paper: Section 3's row rule; active: the option that keeps rows inactive at the "
                          "phase-1 point as inequalities (row_rule = 1)")
@@ -257,8 +259,8 @@ def fp64_ops(m, n, nnz):
 def oracle_sample(model, p, eta, iters, algorithm):
     """`iters` phase-1 steps of the oracle's loop ("averaged" or "halpern")
     from the start point, with the restart checks every check period; returns
-    the seconds taken.  The start point's setup (for the Halpern loop, the
-    anchor's residual) is not timed."""
+    (seconds taken, final state).  The start point's setup (for the Halpern
+    loop, the anchor's residual) is not timed."""
     import oracle
     from oracle import halpern as H
     x0 = oracle.project_box(np.zeros(model.n), model.lhat, model.uhat)
@@ -275,7 +277,7 @@ def oracle_sample(model, p, eta, iters, algorithm):
                     H.apply_restart(model, s, q, r)
                 else:
                     s.r_prev = r
-        return time.perf_counter() - t0
+        return time.perf_counter() - t0, s
     s = oracle.State(model, x0, np.zeros(model.m), eta, oracle.initial_omega(model))
     t0 = time.perf_counter()
     for _ in range(iters):
@@ -285,7 +287,7 @@ def oracle_sample(model, p, eta, iters, algorithm):
             ec = oracle.evaluate(model, s.x, s.y, s.omega)
             ea = oracle.evaluate(model, xa, ya, s.omega)
             oracle.restart_check(model, s, p, ec, ea)
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, s
 
 
 def headline_algorithm(args):
@@ -314,7 +316,7 @@ def run_reference(args, rank, world):
 
     for _ in range(args.warmup):
         oracle_sample(model, p, eta, iters, alg)
-    times = [oracle_sample(model, p, eta, iters, alg) for _ in range(args.steps)]
+    times = [oracle_sample(model, p, eta, iters, alg)[0] for _ in range(args.steps)]
     total = sum(times)
     value = iters * args.steps / total
     out = {
@@ -338,7 +340,7 @@ def cpu_baseline_sample(lp, iters, algorithm="averaged"):
     t0 = time.perf_counter()
     model, p, sigma_max, eta = oracle.setup(lp)
     t_setup = time.perf_counter() - t0
-    dt = oracle_sample(model, p, eta, iters, algorithm)
+    dt, _ = oracle_sample(model, p, eta, iters, algorithm)
     return {"value": iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} phase-1 PDHG iterations of the {algorithm} loop with restart checks on the same "
                       f"LP ({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
@@ -712,7 +714,7 @@ def main():
             arms["fp64"] = run_arm(P.FP64)
         if args.precision in ("fp32", "both"):
             arms["fp32"] = run_arm(P.FP32_BULK)
-        if args.corner_rows == "paper" and not args.no_row_option and args.precision == "both":
+        if args.corner_rows == "paper" and args.row_option and not args.no_row_option and args.precision == "both":
             cp_opt = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
                                              row_rule=1)
             arms["fp64_rows"] = run_arm(P.FP64, cp_opt)

@@ -1,0 +1,46 @@
+"""Host-side logic of bench.py (no GPU): which loop the headline runs, the
+algorithmic byte counts, and that the CPU-baseline and reference legs time
+exactly the oracle's own iteration."""
+import argparse
+
+import numpy as np
+import pytest
+
+import bench
+import lpgen
+import oracle
+
+
+def _args(**kw):
+    a = argparse.Namespace(workload="power_law_m100k_n400k", algorithm="both")
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def test_headline_algorithm():
+    assert bench.headline_algorithm(_args()) == "halpern"
+    assert bench.headline_algorithm(_args(algorithm="halpern")) == "halpern"
+    assert bench.headline_algorithm(_args(algorithm="averaged")) == "averaged"
+    # the batched workload runs the averaged loop only
+    assert bench.headline_algorithm(_args(workload="batch_512")) == "averaged"
+
+
+def test_halpern_bytes_differ_by_the_sums_and_the_anchor():
+    m, n, nnz = 1000, 4000, 30000
+    p_avg, d_avg = bench.algorithmic_bytes(m, n, nnz)
+    p_h, d_h = bench.algorithmic_bytes_halpern(m, n, nnz)
+    # primal: the running sum's read and write (16 B) become the anchor's read (8 B)
+    assert p_avg - p_h == 8 * n
+    # dual: likewise per row
+    assert d_avg - d_h == 8 * m
+
+
+@pytest.mark.parametrize("alg", ["averaged", "halpern"])
+def test_cpu_sample_is_the_oracle_iteration(alg):
+    lp = lpgen.small_face_lp(0)
+    model, p, sigma_max, eta = oracle.setup(lp)
+    _, s = bench.oracle_sample(model, p, eta, 130, alg)
+    ref = oracle.run_iterations(lp, 130, dict(algorithm=alg))["state"]
+    assert s.k == ref.k == 130 and s.restarts == ref.restarts
+    assert np.array_equal(s.x, ref.x) and np.array_equal(s.y, ref.y)
