@@ -44,3 +44,11 @@ def test_cpu_sample_is_the_oracle_iteration(alg):
     ref = oracle.run_iterations(lp, 130, dict(algorithm=alg))["state"]
     assert s.k == ref.k == 130 and s.restarts == ref.restarts
     assert np.array_equal(s.x, ref.x) and np.array_equal(s.y, ref.y)
+
+
+def test_step_roofline():
+    # 100 MB per iteration, 1000 iterations in 50 ms: 50 us each, 2 TB/s
+    r = bench.step_roofline(100e6, 50.0, 1000, 8000.0)
+    assert r["us_per_iter"] == pytest.approx(50.0)
+    assert r["achieved"] == pytest.approx(2000.0)
+    assert r["frac"] == pytest.approx(0.25)
