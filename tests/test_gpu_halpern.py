@@ -176,3 +176,22 @@ def test_corner_omega_rule_matches_oracle(alg, scale):
         assert rep[k] == orep[k], k
     with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
         g.corner_phase(obj_seed=11, omega_rule=2)
+
+
+def test_halpern_checkpoint_restore_resumes_at_the_corner_phase():
+    # the state carries the parameters (the inner loop among them): a restored
+    # handle runs the corner phase in the Halpern loop, bit for bit as the
+    # original handle does
+    lp = _lp_cases()["bounded_ineq"]()
+    g = P.lp_from_dict(lp)
+    r1 = g.solve(algorithm=P.HALPERN)
+    state = g.get_state()
+    c_orig = g.corner_phase(obj_seed=5)
+    x_orig, _, _ = g.get_solution(P.CORNER)
+    h = P.lp_from_dict(lp)
+    h.set_state(state)
+    assert h.kkt_report(P.PHASE1)["rel_kkt"] == r1["rel_kkt"]
+    c_rest = h.corner_phase(obj_seed=5)
+    assert c_rest["iters"] == c_orig["iters"] and c_rest["chosen"] == c_orig["chosen"] == 2
+    x_rest, _, _ = h.get_solution(P.CORNER)
+    assert np.array_equal(x_rest, x_orig)
