@@ -1,8 +1,10 @@
 // C-ABI of the PDHG + corner-push library (include/pdhgc.h): handle,
-// device memory, setup kernels, the graph-driven restarted PDHG loop,
-// Algorithm 1, reports and accessors; the phase-1 restart history, features,
-// labels and held corner phase of the learned guidance; checkpoint/restore;
-// the random-gather probe.
+// device memory, setup kernels, the graph-driven restarted PDHG loop in its
+// two forms (averaged, and the reflected restarted Halpern loop of cuPDLP+
+// that Section 4.1 names), Algorithm 1 with its corner primal-weight rule,
+// reports and accessors; the phase-1 restart history, features, labels and
+// held corner phase of the learned guidance; checkpoint/restore; the
+// random-gather probe.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -430,7 +432,7 @@ __global__ void k_ring_init(int n, const double* __restrict__ x, RingRec rr) {
   }
 }
 
-// end of a phase: the returned point (current or average; the phase-1 x on a
+// end of a phase: the returned point (current, average or T(z); the phase-1 x on a
 // corner limit)
 // The returned x is clamped to the phase's box: an average of FP32-bulk
 // iterates may lie an FP32 ulp outside it (a no-op for the FP64 iteration)
