@@ -57,13 +57,15 @@ def _nearest(x, lb, ub):
     return np.where(dl <= du, lb, ub)
 
 
-def compare(net, lp, corner_seed, threshold=0.9, corner_max_iters=300_000, guided_max_iters=0):
+def compare(net, lp, corner_seed, threshold=0.9, corner_max_iters=300_000, guided_max_iters=0,
+            phase1_params=None):
     """Plain corner phase versus the guided one on the same phase-1 result.
     The plain run judges the network: a held column is wrong when the plain
-    corner did not leave it at the bound it was held at."""
+    corner did not leave it at the bound it was held at.  `phase1_params`
+    (a Params, as for build_dataset) selects e.g. the Halpern loop."""
     import torch
     g = P.lp_from_dict(lp)
-    r1 = g.solve()
+    r1 = g.solve(phase1_params) if phase1_params is not None else g.solve()
     t0 = time.perf_counter()
     rp = g.corner_phase(obj_seed=int(corner_seed), max_iters=int(corner_max_iters))
     torch.cuda.synchronize()
