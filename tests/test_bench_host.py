@@ -52,3 +52,17 @@ def test_step_roofline():
     assert r["us_per_iter"] == pytest.approx(50.0)
     assert r["achieved"] == pytest.approx(2000.0)
     assert r["frac"] == pytest.approx(0.25)
+
+
+def test_headline_bound_follows_the_larger_fraction():
+    hbm = {"achieved": 2187.0, "peak": 6789.6, "unit": "GB/s", "frac": 2187.0 / 6789.6,
+           "peak_source": "measured hbm_gbs"}
+    fp64 = {"achieved_tflops": 0.415, "peak_tflops": 1.25, "frac": 0.415 / 1.25}
+    top = bench.headline_bound(hbm, fp64)
+    assert top["bound"] == "alu" and top["unit"] == "TFLOP/s"
+    assert top["achieved"] == 0.415 and top["peak"] == 1.25 and top["frac"] == pytest.approx(0.332)
+    fp64_low = dict(fp64, achieved_tflops=0.3, frac=0.24)
+    top = bench.headline_bound(hbm, fp64_low)
+    assert top["bound"] == "hbm" and top["unit"] == "GB/s" and top["peak"] == 6789.6
+    # the FP64 unit rate the docstring derives
+    assert 152 * 2 * 2 * 2.07e9 / 1e12 == pytest.approx(1.26, abs=0.01)
