@@ -262,6 +262,41 @@ def step_roofline(bytes_per_iter, total_ms, total_iters, peak):
                     "time per iteration (checks included)"}
 
 
+def kernel_roofline(m, n, nnz, fp32, halpern, ms_primal, ms_dual, peak, peak_kind, traffic_rec):
+    """Roofline of the dominant iteration kernel from its replayed duration:
+    algorithmic bytes and FP64 operations per launch of the loop's kernels,
+    the HBM and FP64-pipe views, the bound they name (headline_bound), and
+    the recorded ncu DRAM traffic when the record matches the sources."""
+    if halpern:
+        b_primal, b_dual = algorithmic_bytes_halpern(m, n, nnz)
+        f_primal, f_dual = fp64_ops_halpern(m, n, nnz)
+    elif not fp32:
+        b_primal, b_dual = algorithmic_bytes(m, n, nnz)
+        f_primal, f_dual = fp64_ops(m, n, nnz)
+    else:
+        b_primal, b_dual = algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
+        f_primal, f_dual = 0, 0  # the running sums are float-float pairs: no FP64 work per launch
+    dom = "primal" if ms_primal >= ms_dual else "dual"
+    ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
+    achieved = b_dom / (ms_dom * 1e-3) / 1e9
+    key = ("halpern_" if halpern else "") + "dram_bytes_per_launch_" + dom
+    roofline = {
+        # the record holds the FP64 kernels' counters only
+        "traffic": float(traffic_rec[key]) if traffic_rec and not fp32 and key in traffic_rec else None,
+        "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
+                  + ("H>" if halpern else "32>" if fp32 else ">") + f" ({dom} step)",
+        "algorithmic_bytes_per_launch": b_dom, "bytes_per_launch": [b_primal, b_dual], "launch_ms": ms_dom,
+        "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
+        "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs"},
+        "fp64": {"ops_per_launch": f_dom, "achieved_tflops": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12,
+                 "peak_tflops": FP64_PEAK_TFLOPS,
+                 "frac": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                 "note": "every FP64 pipe operation counted as one FMA (2 flops) against 1.25 TFLOP/s"},
+    }
+    return dict(headline_bound(roofline["hbm"], roofline["fp64"]), **roofline)
+
+
 def headline_bound(hbm, fp64):
     """The roofline's top-level fields: the larger of the HBM and FP64-pipe
     fractions names the bound, and achieved / peak / unit / frac are that
@@ -672,34 +707,11 @@ def main():
         value = total_iters_all / (total_ms * 1e-3)
         # kernel durations: event-bracketed replays of the two iteration kernels
         ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
-        if halpern:
-            b_primal, b_dual = algorithmic_bytes_halpern(m, n, nnz)
-            f_primal, f_dual = fp64_ops_halpern(m, n, nnz)
-        elif precision == P.FP64:
-            b_primal, b_dual = algorithmic_bytes(m, n, nnz)
-            f_primal, f_dual = fp64_ops(m, n, nnz)
-        else:
-            b_primal, b_dual = algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
-            f_primal, f_dual = 0, 0  # the running sums are float-float pairs: no FP64 work per launch
+        roofline = kernel_roofline(m, n, nnz, precision == P.FP32_BULK, halpern, ms_primal, ms_dual, peak,
+                                   peak_kind, traffic_record())
         dom = "primal" if ms_primal >= ms_dual else "dual"
-        ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
-        achieved = b_dom / (ms_dom * 1e-3) / 1e9
-        tr = traffic_record() if precision == P.FP64 else None
-        key = ("halpern_" if halpern else "") + "dram_bytes_per_launch_" + dom
-        roofline = {
-            "traffic": float(tr[key]) if tr and key in tr else None,
-            "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
-                      + ("H>" if halpern else "32>" if precision == P.FP32_BULK else ">") + f" ({dom} step)",
-            "algorithmic_bytes_per_launch": b_dom, "launch_ms": ms_dom,
-            "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
-            "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": f"{peak_kind} hbm_gbs"},
-            "fp64": {"ops_per_launch": f_dom, "achieved_tflops": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12,
-                     "peak_tflops": FP64_PEAK_TFLOPS,
-                     "frac": 2.0 * f_dom / (ms_dom * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                     "note": "every FP64 pipe operation counted as one FMA (2 flops) against 1.25 TFLOP/s"},
-        }
-        roofline = dict(headline_bound(roofline["hbm"], roofline["fp64"]), **roofline)
+        ms_dom = roofline["launch_ms"]
+        b_primal, b_dual = roofline["bytes_per_launch"]
         # the random-gather ceiling: the same number of random loads from a
         # vector of the gathered length, warm in L2 (pdhgc_probe_gather)
         g_len = m if dom == "primal" else n

@@ -66,3 +66,29 @@ def test_headline_bound_follows_the_larger_fraction():
     assert top["bound"] == "hbm" and top["unit"] == "GB/s" and top["peak"] == 6789.6
     # the FP64 unit rate the docstring derives
     assert 152 * 2 * 2 * 2.07e9 / 1e12 == pytest.approx(1.26, abs=0.01)
+
+
+@pytest.mark.parametrize("fp32, halpern, ms, alg_bytes, kernel", [
+    (False, True, (0.02894, 0.02048), 63281924, "spmv<PrimalOpH> (primal step)"),
+    (False, False, (0.02758, 0.02004), 66481924, "spmv<PrimalOp> (primal step)"),
+    (True, False, (0.02266, 0.01812), 46854616, "spmv<PrimalOp32> (primal step)"),
+])
+def test_kernel_roofline(fp32, halpern, ms, alg_bytes, kernel):
+    # the 100k x 400k workload with the replayed durations of the default bench
+    m, n, nnz = 100000, 400000, 3206827
+    rec = {"dram_bytes_per_launch_primal": "57635840", "halpern_dram_bytes_per_launch_primal": "57580032"}
+    r = bench.kernel_roofline(m, n, nnz, fp32, halpern, ms[0], ms[1], 6789.6, "measured", rec)
+    assert r["kernel"] == kernel and r["algorithmic_bytes_per_launch"] == alg_bytes
+    assert r["hbm"]["achieved"] == pytest.approx(alg_bytes / (ms[0] * 1e-3) / 1e9)
+    assert r["traffic"] == (None if fp32 else float(rec[("halpern_" if halpern else "") +
+                                                       "dram_bytes_per_launch_primal"]))
+    assert r["bound"] in ("hbm", "alu")
+    top = r["fp64"] if r["bound"] == "alu" else r["hbm"]
+    assert r["frac"] == top["frac"] and r["frac"] >= min(r["hbm"]["frac"], r["fp64"]["frac"])
+    if fp32:
+        assert r["fp64"]["frac"] == 0.0 and r["bound"] == "hbm"
+    if halpern:
+        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"  # the measured headline case
+    assert sum(r["bytes_per_launch"]) == sum(bench.algorithmic_bytes_halpern(m, n, nnz) if halpern else
+                                             bench.algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
+                                             if fp32 else bench.algorithmic_bytes(m, n, nnz))
