@@ -7,8 +7,9 @@ are re-exported here lazily so that `paper_2511_13894_gb300.build` can run
 before the library exists.
 """
 
-_EXPORTS = {"lp_create", "lp_from_dict", "LP", "uniform", "default_params", "default_corner_params",
-            "PdhgcError", "FP64", "FP32_BULK", "PHASE1", "CORNER", "STATUS_NAMES", "lib"}
+_EXPORTS = {"lp_create", "lp_from_dict", "LP", "Batch", "Guide", "uniform", "probe_gather",
+            "default_params", "default_corner_params", "Params", "CornerParams", "Report", "PdhgcError",
+            "FP64", "FP32_BULK", "AVERAGED", "HALPERN", "PHASE1", "CORNER", "STATUS_NAMES", "lib"}
 
 
 def __getattr__(name):

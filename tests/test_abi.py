@@ -129,3 +129,9 @@ def test_host_validation_errors(lib):
     ub2 = lp["ub"].copy()
     ub2[0] = -np.inf
     _expect(-3, ub=ub2)
+
+
+def test_package_exports_exist(lib):
+    import paper_2511_13894_gb300 as pkg
+    for name in pkg._EXPORTS:
+        assert getattr(pkg, name) is not None, name
