@@ -246,3 +246,36 @@ def test_corner_omega_rule_keeps_the_phase1_weight(alg):
     assert kept["state"].omega == r1["state"].omega
     assert fresh["state"].omega == oracle.initial_omega(fresh["corner_model"])
     assert fresh["state"].omega != kept["state"].omega
+
+
+def test_halpern_guided_corner_with_an_empty_hold_is_the_plain_corner():
+    lp = lpgen.small_face_lp(8)
+    r = oracle.solve(lp, HP)
+    cp = dict(obj_seed=2)
+    plain = oracle.corner_phase(r, cp)
+    g = oracle.corner_phase(r, cp, hold=np.zeros(lp["n"], dtype=bool))
+    assert g["iters"] == plain["iters"] and g["status"] == plain["status"]
+    assert np.array_equal(g["x_hat"], plain["x_hat"]) and g["info"]["held"] == 0
+
+
+def test_halpern_held_columns_end_at_their_bound():
+    # the held columns' T(z) is projected onto l_hat = u_hat = the bound, so
+    # the returned point holds them exactly there (the reflected iterate itself
+    # may sit an ulp off)
+    from oracle import guide
+    lp = lpgen.with_bounds_and_inequalities(lpgen.small_face_lp(9), 9)
+    r = oracle.solve(lp, HP)
+    model = r["model"]
+    cp = dict(obj_seed=4)
+    elig = guide.eligible(r, dict(oracle.CORNER_DEFAULTS, **cp))
+    x1 = model.Dc * r["x_hat"]
+    dist = np.where(elig, np.minimum(x1 - model.l, model.u - x1), np.inf)
+    hold = np.zeros(lp["n"], dtype=bool)
+    hold[np.argsort(dist)[:5]] = True
+    g = oracle.corner_phase(r, cp, hold=hold)
+    held = g["info"]["held_mask"]
+    assert held.sum() == hold.sum() > 0
+    nb = P.nearest_bound(r["x_hat"], model.lhat, model.uhat)
+    assert np.array_equal(g["state"].xp[held], nb[held])
+    if g["status"] == oracle.CORNER_DONE:
+        assert np.array_equal(g["x_hat"][held], nb[held])
