@@ -77,9 +77,17 @@ def parse():
     ap.add_argument("--corner-rows", choices=["paper", "active"], default="paper",
                     help="paper: Section 3's row rule; active: the option that keeps rows inactive at the "
                          "phase-1 point as inequalities (row_rule = 1)")
-    ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="both",
-                    help="inner loop of the headline (averaged) and of an extra block (halpern); 'both' "
-                         "adds the Halpern loop (FP64, the paper's row rule) beside the averaged arms")
+    ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="halpern",
+                    help="inner loop of the headline: halpern (the default; FP64 headline plus an FP32-bulk "
+                         "block), averaged, or both (the Halpern headline plus the averaged loop's arms)")
+    ap.add_argument("--blocks", type=str, default="transport",
+                    help="comma-separated extra workloads measured after the headline (Halpern loop only): "
+                         "transport (transportation_1000x2000, FP64 and FP32 bulk), batch (batch_512); "
+                         "'' for none")
+    ap.add_argument("--block-warmup", type=int, default=1, help="untimed steps of each extra block")
+    ap.add_argument("--block-steps", type=int, default=2, help="timed steps of each extra block")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="threads of the all-core oracle sample (0: every core os.cpu_count() reports)")
     ap.add_argument("--obj-scale-sweep", type=str, default=None,
                     help="comma-separated corner objective scales (Section 5's study): one phase 1 with the "
                          "headline loop, then one timed corner phase per scale; prints its own JSON line")
@@ -240,12 +248,25 @@ def algorithmic_bytes_halpern(m, n, nnz):
     return primal, dual
 
 
+def algorithmic_bytes_halpern32(m, n, nnz):
+    """Bytes per launch of the Halpern loop's FP32-bulk kernels, a step inside
+    a chunk: primal reads FP32 values + int32 indices, column pointers, c, l,
+    u (FP32), the float-float x (8 B) and anchor (8 B), writes x (8 B) and the
+    FP32 x_bar, gathers the FP32 y once; dual reads values + indices, row
+    pointers, b, the float-float y and anchor and the sense byte, writes y
+    (8 B), gathers x_bar once."""
+    primal = nnz * 8 + n * 4 + n * (3 * 4 + 8 + 8 + 8 + 4) + m * 4
+    dual = nnz * 8 + m * 4 + m * (4 + 8 + 8 + 8 + 1) + n * 4
+    return primal, dual
+
+
 def fp64_ops_halpern(m, n, nnz):
     """FP64 operations per launch of the Halpern loop's kernels: one FMA per
-    nonzero plus the epilogue (primal: c - A'y, the step, x_bar, then two
-    for the reflected point and two for the anchored combination, 7 per
-    column; dual: 6 per row)."""
-    return nnz + 7 * n, nnz + 6 * m
+    nonzero plus the epilogue (primal: c - A'y, the step and x_bar, which is
+    also the reflected point (rho = 1), then two for the anchored combination,
+    5 per column; dual: b - A x_bar, the step, the reflected point and two for
+    the anchored combination, 5 per row)."""
+    return nnz + 5 * n, nnz + 5 * m
 
 
 def step_roofline(bytes_per_iter, total_ms, total_iters, peak):
@@ -267,7 +288,10 @@ def kernel_roofline(m, n, nnz, fp32, halpern, ms_primal, ms_dual, peak, peak_kin
     algorithmic bytes and FP64 operations per launch of the loop's kernels,
     the HBM and FP64-pipe views, the bound they name (headline_bound), and
     the recorded ncu DRAM traffic when the record matches the sources."""
-    if halpern:
+    if halpern and fp32:
+        b_primal, b_dual = algorithmic_bytes_halpern32(m, n, nnz)
+        f_primal, f_dual = 0, 0  # float-float iterates and anchors: no FP64 work inside a chunk
+    elif halpern:
         b_primal, b_dual = algorithmic_bytes_halpern(m, n, nnz)
         f_primal, f_dual = fp64_ops_halpern(m, n, nnz)
     elif not fp32:
@@ -284,7 +308,8 @@ def kernel_roofline(m, n, nnz, fp32, halpern, ms_primal, ms_dual, peak, peak_kin
         # the record holds the FP64 kernels' counters only
         "traffic": float(traffic_rec[key]) if traffic_rec and not fp32 and key in traffic_rec else None,
         "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
-                  + ("H>" if halpern else "32>" if fp32 else ">") + f" ({dom} step)",
+                  + ("H32>" if halpern and fp32 else "H>" if halpern else "32>" if fp32 else ">")
+                  + f" ({dom} step)",
         "algorithmic_bytes_per_launch": b_dom, "bytes_per_launch": [b_primal, b_dual], "launch_ms": ms_dom,
         "other_kernel_ms": ms_dual if dom == "primal" else ms_primal,
         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -396,17 +421,79 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline_sample(lp, iters, algorithm="averaged"):
-    """The oracle timed on this host on a bounded sample (rank 0, N = 1)."""
+def _replica_sample(workload, iters, algorithm, barrier, out_q):
+    """One all-core replica (a spawned process): builds the workload's LP and
+    the oracle's model untimed, waits at the barrier, then times `iters`
+    oracle iterations."""
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    import oracle
+    lp = WORKLOADS[workload]()
+    model, p, sigma_max, eta = oracle.setup(lp)
+    barrier.wait()
+    dt, _ = oracle_sample(model, p, eta, iters, algorithm)
+    out_q.put(dt)
+
+
+def cpu_all_cores_sample(workload, iters, algorithm, procs):
+    """The oracle on every core: `procs` spawned processes, one replica of
+    the workload each (as the GPU replicas of a multi-GPU run), timed from a
+    common barrier; the value is all replicas' iterations over the slowest
+    one's time.  (The oracle's scipy products hold the GIL, so threads would
+    not run them in parallel; a replica per core is the all-core rate.)"""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_replica_sample, args=(workload, iters, algorithm, barrier, q)) for _ in range(procs)]
+    for pr in ps:
+        pr.start()
+    times = [q.get() for _ in range(procs)]
+    for pr in ps:
+        pr.join()
+    return {"value": procs * iters / max(times), "unit": "iters/s", "cores": procs, "kind": "oracle replicas",
+            "sample": f"{procs} processes, one replica of {workload} each, {iters} phase-1 iterations of the "
+                      f"{algorithm} loop per replica from a common barrier; slowest replica {max(times):.1f} s"}
+
+
+def cpu_time_to_corner(lp, algorithm):
+    """The oracle's own time-to-corner (phase 1 to 1e-6, then Algorithm 1 to
+    the Section 3.1 rule) on a small LP, single-threaded."""
+    import oracle
+    t0 = time.perf_counter()
+    r1 = oracle.solve(lp, dict(algorithm=algorithm))
+    rc = oracle.corner_phase(r1, dict(obj_seed=1))
+    return {"seconds": time.perf_counter() - t0, "phase1_iters": r1["iters"], "corner_iters": rc["iters"],
+            "corner_status": "CORNER_DONE" if rc["status"] == oracle.CORNER_DONE else "CORNER_LIMIT",
+            "workload": lp.get("name")}
+
+
+def cpu_baseline_sample(lp, iters, algorithm="averaged", threads=0, workload=None, gpu_step_iters=None):
+    """The oracle timed on this host on a bounded sample (rank 0, N = 1):
+    one core, then (when `workload` names it) every core as replicas; the
+    core count; the time-to-corner the one-core rate implies for the GPU
+    step's iteration count; the oracle's measured time-to-corner on the
+    200 x 500 LP."""
     import oracle
     t0 = time.perf_counter()
     model, p, sigma_max, eta = oracle.setup(lp)
     t_setup = time.perf_counter() - t0
     dt, _ = oracle_sample(model, p, eta, iters, algorithm)
-    return {"value": iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} phase-1 PDHG iterations of the {algorithm} loop with restart checks on the same "
-                      f"LP ({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
-                      f"numpy/scipy, single-threaded"}
+    nproc = os.cpu_count() or 1
+    out = {"value": iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle", "nproc": nproc,
+           "sample": f"{iters} phase-1 PDHG iterations of the {algorithm} loop with restart checks on the same "
+                     f"LP ({dt:.1f} s; scaling + power-iteration setup {t_setup:.1f} s not counted); "
+                     f"numpy/scipy, single-threaded"}
+    if gpu_step_iters:
+        out["time_to_corner_extrapolated_s"] = gpu_step_iters / out["value"]
+        out["time_to_corner_note"] = ("the GPU step's phase-1 + corner iterations at the one-core oracle rate "
+                                      "(an extrapolation, not a run)")
+    if workload is not None and nproc > 1:
+        procs = threads if threads > 0 else nproc
+        out["cores_all"] = cpu_all_cores_sample(workload, max(64, iters // 4), algorithm, procs)
+    small = lpgen.small_face_lp(0)
+    out["random_face_m200_n500_time_to_corner"] = cpu_time_to_corner(small, algorithm)
+    return out
 
 
 def batch_bytes_per_iter(lp, s_v=4, s_x=4, s_sum=8, s_lo=4):
@@ -559,7 +646,8 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e_ms},
             "gpu_launches": launches, "clocks": clk,
         }
-        print(json.dumps(out), flush=True)
+        return out
+    return None
 
 
 def run_obj_scale_sweep(args, g, P, torch, stream):
@@ -604,6 +692,19 @@ def run_obj_scale_sweep(args, g, P, torch, stream):
                       "runs": rows}), flush=True)
 
 
+def corner_speedup(base, other):
+    """Time-to-corner speedup of `other` over `base` (ratio of their step
+    times), reported only when every timed step of both arms ended its
+    corner phase at Section 3.1's rule (CORNER_DONE); otherwise null with
+    the reason, so that two runs stopped at a limit are never compared."""
+    sb = [rc["status_name"] for _, rc in base["reps"]]
+    so = [rc["status_name"] for _, rc in other["reps"]]
+    ok = all(v == "CORNER_DONE" for v in sb + so)
+    return {"value": (base["total_ms"] / other["total_ms"]) if ok and other["total_ms"] > 0 else None,
+            "base_corner_status": sorted(set(sb)), "corner_status": sorted(set(so)),
+            "reason": None if ok else "a corner phase stopped at its limit: no time-to-corner to compare"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -628,13 +729,16 @@ def main():
         B = P.Batch(lpgen.batch_lps(512), stream=torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("batch_kernel")
-        B.solve(max_iters=args.profile_iters, eps_rel=-1.0, precision=P.FP32_BULK)
+        B.solve(max_iters=args.profile_iters, eps_rel=-1.0, precision=P.FP32_BULK,
+                algorithm=P.HALPERN if args.algorithm == "halpern" else P.AVERAGED)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"mode": "kernels", "workload": "batch_512", "iters": args.profile_iters}))
         return
     if args.workload == "batch_512":
-        run_batch_workload(args, rank, world, local, torch, P, dist, barrier)
+        out = run_batch_workload(args, rank, world, local, torch, P, dist, barrier)
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
@@ -646,7 +750,7 @@ def main():
     g = P.lp_from_dict(lp_dict, stream=stream.cuda_stream)
     if args.mode == "kernels":
         g.solve(max_iters=64, precision=P.FP32_BULK if args.precision == "fp32" else P.FP64,
-                algorithm=P.HALPERN if args.algorithm == "halpern" else P.AVERAGED)
+                algorithm=P.AVERAGED if args.algorithm == "averaged" else P.HALPERN)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("pdhg_kernels")
         ms = g.profile_iteration(args.profile_iters)
@@ -667,24 +771,29 @@ def main():
         uuid = None
     peak, peak_kind = measured_peaks()
 
-    def run_arm(precision, cparams=cparams, algorithm=None):
-        algorithm = P.AVERAGED if algorithm is None else algorithm
+    def run_arm(h, dims, precision, cparams=cparams, algorithm=P.HALPERN, warmup=None, steps=None):
+        """Times `steps` steps (phase 1 + corner phase) of handle h after
+        `warmup` untimed ones, L2 flushed between steps; then the kernel
+        replays, the roofline and the gather ceiling."""
+        warmup = args.warmup if warmup is None else warmup
+        steps = args.steps if steps is None else steps
+        mm, nn, nz = dims
         params = P.default_params(max_iters=args.phase1_max_iters, precision=precision, algorithm=algorithm)
         halpern = algorithm == P.HALPERN
 
         def step():
-            r1 = g.solve(params)
-            rc = g.corner_phase(cparams)
+            r1 = h.solve(params)
+            rc = h.corner_phase(cparams)
             return r1, rc
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         clocks = ClockSampler(uuid)
         clocks.start()
-        launches0 = g.kernel_launches()
+        launches0 = h.kernel_launches()
         step_ms, iters, reps = [], [], []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1.0)  # L2 flush: 512 MiB write between steps
             torch.cuda.synchronize()
             barrier()
@@ -700,31 +809,31 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             iters.append(r1["iters"] + rc["iters"])
             reps.append((r1, rc))
-        launches = g.kernel_launches() - launches0
+        launches = h.kernel_launches() - launches0
         clk = clocks.stop()
         total_iters = sum(iters)
         total_ms, total_iters_all = aggregate(dist, sum(step_ms), total_iters, "cuda")
         value = total_iters_all / (total_ms * 1e-3)
         # kernel durations: event-bracketed replays of the two iteration kernels
-        ms_primal, ms_dual = g.profile_iteration(args.profile_iters)
-        roofline = kernel_roofline(m, n, nnz, precision == P.FP32_BULK, halpern, ms_primal, ms_dual, peak,
+        ms_primal, ms_dual = h.profile_iteration(args.profile_iters)
+        roofline = kernel_roofline(mm, nn, nz, precision == P.FP32_BULK, halpern, ms_primal, ms_dual, peak,
                                    peak_kind, traffic_record())
         dom = "primal" if ms_primal >= ms_dual else "dual"
         ms_dom = roofline["launch_ms"]
         b_primal, b_dual = roofline["bytes_per_launch"]
         # the random-gather ceiling: the same number of random loads from a
         # vector of the gathered length, warm in L2 (pdhgc_probe_gather)
-        g_len = m if dom == "primal" else n
+        g_len = mm if dom == "primal" else nn
         g_bytes = 8 if precision == P.FP64 else 4
-        ms_g = P.probe_gather(g_len, nnz, g_bytes, reps=20)
-        roofline["gather"] = {"gathers_per_launch": nnz, "vector_elems": g_len, "elem_bytes": g_bytes,
-                              "ceiling_ms": ms_g, "ceiling_gathers_per_s": nnz / (ms_g * 1e-3),
-                              "achieved_gathers_per_s": nnz / (ms_dom * 1e-3), "frac": ms_g / ms_dom,
+        ms_g = P.probe_gather(g_len, nz, g_bytes, reps=20)
+        roofline["gather"] = {"gathers_per_launch": nz, "vector_elems": g_len, "elem_bytes": g_bytes,
+                              "ceiling_ms": ms_g, "ceiling_gathers_per_s": nz / (ms_g * 1e-3),
+                              "achieved_gathers_per_s": nz / (ms_dom * 1e-3), "frac": ms_g / ms_dom,
                               "note": "pdhgc_probe_gather: the same count of random loads alone"}
         roofline["step"] = step_roofline(b_primal + b_dual, total_ms, total_iters, peak)
         r1, rc = reps[-1]
-        return dict(value=value, total_ms=total_ms, total_iters=total_iters, launches=launches, clocks=clk,
-                    roofline=roofline, r1=r1, rc=rc, params=params)
+        return dict(value=value, total_ms=total_ms, steps=steps, warmup=warmup, total_iters=total_iters,
+                    launches=launches, clocks=clk, roofline=roofline, r1=r1, rc=rc, reps=reps, params=params)
 
     def summary(res):
         r1, rc = res["r1"], res["rc"]
@@ -732,39 +841,73 @@ def main():
             "phase1": {"status": r1["status_name"], "iters": r1["iters"], "restarts": r1["restarts"],
                        "rel_kkt": r1["rel_kkt"], "seconds": r1["seconds"], "corner_measure": r1["corner_measure"],
                        "candidates": r1["candidates"], "off_bound_p": r1["off_bound_p"],
-                       "should_corner": r1["should_corner"]},
+                       "primal_push_est": r1["primal_push_est"], "should_corner": r1["should_corner"]},
             "corner": {"status": rc["status_name"], "iters": rc["iters"], "restarts": rc["restarts"],
                        "seconds": rc["seconds"], "corner_measure": rc["corner_measure"],
                        "candidates": rc["candidates"], "off_bound_p": rc["off_bound_p"],
-                       "rel_p": rc["rel_p"], "rel_kkt": rc["rel_kkt"]},
+                       "primal_push_est": rc["primal_push_est"], "rel_p": rc["rel_p"], "rel_kkt": rc["rel_kkt"]},
             "us_per_iter": res["total_ms"] * 1e3 / max(1, res["total_iters"]),
         }
 
-    # the headline: the Halpern loop (FP64) unless --algorithm averaged; with
-    # --algorithm both the averaged loop's arms follow as blocks: FP64, FP32
-    # bulk, and the corner row option (not the paper's rule: rows inactive
-    # at the phase-1 point kept as inequalities)
-    arms = {}
+    def block(res, note, dtype):
+        b = {"note": note, "dtype": dtype, "value": res["value"], "unit": "iters/s",
+             "steps": res["steps"], "warmup": res["warmup"],
+             "time_to_corner_s": res["total_ms"] / res["steps"] * 1e-3,
+             "roofline": res["roofline"], "gpu_launches": res["launches"], "clocks": res["clocks"]}
+        b.update(summary(res))
+        return b
+
+    f32_dtype = "f32 values and gathers; float-float iterates, anchors and row sums; f64 checks and KKT"
+    dims = (m, n, nnz)
     head_alg = headline_algorithm(args)
+    arms = {}
     if head_alg == "halpern":
-        arms["halpern"] = run_arm(P.FP64, algorithm=P.HALPERN)
+        arms["halpern"] = run_arm(g, dims, P.FP64)
+        if args.precision in ("fp32", "both"):
+            arms["halpern_fp32"] = run_arm(g, dims, P.FP32_BULK)
     if args.algorithm in ("averaged", "both"):
         if args.precision in ("fp64", "both"):
-            arms["fp64"] = run_arm(P.FP64)
+            arms["fp64"] = run_arm(g, dims, P.FP64, algorithm=P.AVERAGED)
         if args.precision in ("fp32", "both"):
-            arms["fp32"] = run_arm(P.FP32_BULK)
+            arms["fp32"] = run_arm(g, dims, P.FP32_BULK, algorithm=P.AVERAGED)
         if args.corner_rows == "paper" and args.row_option and not args.no_row_option and args.precision == "both":
             cp_opt = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed,
                                              row_rule=1)
-            arms["fp64_rows"] = run_arm(P.FP64, cp_opt)
-            arms["fp32_rows"] = run_arm(P.FP32_BULK, cp_opt)
-    head = arms["halpern"] if head_alg == "halpern" else (arms["fp64"] if "fp64" in arms else arms["fp32"])
+            arms["fp64_rows"] = run_arm(g, dims, P.FP64, cp_opt, algorithm=P.AVERAGED)
+            arms["fp32_rows"] = run_arm(g, dims, P.FP32_BULK, cp_opt, algorithm=P.AVERAGED)
+    if head_alg == "halpern":
+        head = arms["halpern"]
+    else:
+        head = arms["fp64"] if "fp64" in arms else arms["fp32"]
     params = head["params"]
     value = head["value"]
     total_ms = head["total_ms"]
     launches = head["launches"]
     clk = head["clocks"]
     roofline = head["roofline"]
+
+    # the other single-GPU workload: the degenerate transportation LP
+    # (1000 x 2000, n = 2M), Halpern loop in FP64 and FP32 bulk
+    extra = {}
+    if head_alg == "halpern" and args.workload != "transportation_1000x2000" and "transport" in args.blocks:
+        lt = lpgen.large_transportation_lp(0)
+        dt = (lt["m"], lt["n"], int(lt["row_ptr"][-1]))
+        gt = P.lp_from_dict(lt, stream=stream.cuda_stream)
+        t64 = run_arm(gt, dt, P.FP64, warmup=args.block_warmup, steps=args.block_steps)
+        t32 = run_arm(gt, dt, P.FP32_BULK, warmup=args.block_warmup, steps=args.block_steps)
+        gt.close()
+        extra["transportation_1000x2000"] = {
+            "config": {"workload": "transportation_1000x2000", "m": dt[0], "n": dt[1], "nnz": dt[2],
+                       "algorithm": "halpern", "corner_rows": args.corner_rows,
+                       "l2": "flushed between steps (512 MiB write)"},
+            "fp64": block(t64, "Halpern loop, FP64", "f64"),
+            "fp32_bulk": block(t32, "Halpern loop, FP32 bulk", f32_dtype),
+            "speedup_fp32_vs_fp64_time_to_corner": corner_speedup(t64, t32),
+        }
+    if head_alg == "halpern" and "batch" in args.blocks and world == 1:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.warmup, bargs.steps = args.block_warmup, args.block_steps
+        extra["batch_512"] = run_batch_workload(bargs, rank, world, local, torch, P, None, barrier)
 
     # end-to-end through the public API with host buffers (pinned), per step:
     # H2D of the inputs in lp_create, solve, corner, D2H of x, y, z
@@ -803,7 +946,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(lp_dict, args.cpu_iters, head_alg)
+        cpu = cpu_baseline_sample(lp_dict, args.cpu_iters, head_alg, args.cpu_threads, args.workload,
+                                  head["r1"]["iters"] + head["rc"]["iters"])
 
     if rank == 0:
         head_is_fp64 = head_alg == "halpern" or "fp64" in arms
@@ -823,38 +967,29 @@ def main():
         out.update(summary(head))
         out.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                     "clocks": clk})
+        if "halpern_fp32" in arms:
+            b = block(arms["halpern_fp32"], "Halpern loop, FP32 bulk, same workload and corner rule", f32_dtype)
+            b["speedup_vs_fp64_time_to_corner"] = corner_speedup(arms["halpern"], arms["halpern_fp32"])
+            out["halpern_fp32_bulk"] = b
         if head_alg == "halpern" and "fp64" in arms:
-            a = arms["fp64"]
-            blk = {"note": "the averaged loop (cuPDLP.jl-style restarts on the KKT error of the current and "
-                           "average points), FP64, the paper's corner row rule",
-                   "value": a["value"], "unit": "iters/s", "time_to_corner_s": a["total_ms"] / args.steps * 1e-3,
-                   "halpern_speedup_time_to_corner": (a["total_ms"] / total_ms) if total_ms > 0 else None,
-                   "roofline": a["roofline"], "gpu_launches": a["launches"], "clocks": a["clocks"]}
-            blk.update(summary(a))
-            out["averaged_fp64"] = blk
-        if "fp64" in arms and "fp32" in arms:
-            a64 = arms["fp64"]
-            f = arms["fp32"]
-            blk = {"value": f["value"], "unit": "iters/s", "dtype": "f32 values, float-float iterates, row sums "
-                                                                   "and running sums; f64 checks and KKT",
-                   "time_to_corner_s": f["total_ms"] / args.steps * 1e-3,
-                   "speedup_vs_averaged_fp64_time_to_corner": (a64["total_ms"] / f["total_ms"]) if f["total_ms"] > 0
-                   else None,
-                   "roofline": f["roofline"], "gpu_launches": f["launches"], "clocks": f["clocks"]}
-            blk.update(summary(f))
-            out["fp32_bulk"] = blk
+            b = block(arms["fp64"], "the averaged loop (cuPDLP.jl-style restarts on the KKT error of the "
+                                    "current and average points), FP64, the paper's corner row rule", "f64")
+            b["halpern_speedup_time_to_corner"] = corner_speedup(arms["fp64"], arms["halpern"])
+            out["averaged_fp64"] = b
+        if "fp32" in arms:
+            b = block(arms["fp32"], "the averaged loop, FP32 bulk", f32_dtype)
+            if "fp64" in arms:
+                b["speedup_vs_averaged_fp64_time_to_corner"] = corner_speedup(arms["fp64"], arms["fp32"])
+            out["averaged_fp32_bulk"] = b
         if "fp64_rows" in arms:
             a64, a32 = arms["fp64_rows"], arms["fp32_rows"]
-            blk = {"note": "corner phase with row_rule = 1 (an option, not the paper's rule): a row becomes '=' "
-                           "only when its dual is non-trivial and it is active at the phase-1 point",
-                   "fp64": {"value": a64["value"], "unit": "iters/s",
-                            "time_to_corner_s": a64["total_ms"] / args.steps * 1e-3, "clocks": a64["clocks"]},
-                   "fp32_bulk": {"value": a32["value"], "unit": "iters/s",
-                                 "time_to_corner_s": a32["total_ms"] / args.steps * 1e-3, "clocks": a32["clocks"]},
-                   "speedup_fp32_vs_fp64_time_to_corner": a64["total_ms"] / a32["total_ms"] if a32["total_ms"] else None}
-            blk["fp64"].update(summary(a64))
-            blk["fp32_bulk"].update(summary(a32))
-            out["corner_row_option"] = blk
+            out["corner_row_option"] = {
+                "note": "corner phase with row_rule = 1 (an option, not the paper's rule): a row becomes '=' "
+                        "only when its dual is non-trivial and it is active at the phase-1 point",
+                "fp64": block(a64, "averaged loop, FP64, row option", "f64"),
+                "fp32_bulk": block(a32, "averaged loop, FP32 bulk, row option", f32_dtype),
+                "speedup_fp32_vs_fp64_time_to_corner": corner_speedup(a64, a32)}
+        out.update(extra)
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

@@ -250,6 +250,18 @@ int pdhgc_get_iterates(pdhgc_lp* lp, double* x, double* y, double* x_avg, double
 int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalars, int on_device);
 
 /*
+ * pdhgc_get_layout — how the matrix passes split the rows of A (out[0..3])
+ * and of A' (out[4..7]) over the SpMV's row segments, as planned at
+ * lp_create: the number of blocks that each own one row longer than 4096
+ * nonzeros (one CTA per row), of blocks of warp-per-row rows (129..4096
+ * nonzeros), of SELL-32 blocks (rows of at most 128 nonzeros), and the
+ * number of rows in the CTA segment.  `out` is a host array of 8 int64.
+ * A layout query (the paper has no counterpart; the segments implement the
+ * CSR passes of the Section 2 iteration).  Errors: INVALID_ARG.
+ */
+int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out);
+
+/*
  * pdhgc_kkt_eval — the Section 2 residuals, objectives and relative ratios,
  * and the Section 2.1 / 4.2 metrics, of a caller-supplied point (x, y) on an
  * LP given as device arrays, without creating a handle.  The LP arguments

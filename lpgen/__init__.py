@@ -125,6 +125,40 @@ def random_face_lp(m: int, n: int, support: int, seed: int, col_nnz=5, name="ran
                 support=S)
 
 
+def dense_line_lp(m: int, n: int, row_len: int, col_len: int, extra_support: int, seed: int, col_nnz=3):
+    """Random-face LP (canonical form, constructed optimum as in random_face_lp)
+    whose pattern adds one dense row and one dense column: column 0 gets
+    col_len distinct rows and row 0 gets row_len distinct columns, on top of
+    col_nnz rows per column.  With row_len and col_len above 4096 both A and
+    A^T have a row that the one-CTA-per-row path of the SpMV handles."""
+    rng = _rng(seed)
+    counts = np.full(n, min(int(col_nnz), m), dtype=np.int64)
+    counts[0] = min(int(col_len), m)
+    while True:
+        rows, cols = _distinct_rows(rng, counts, m)
+        if np.unique(rows).shape[0] == m:
+            break
+    dense_cols = np.sort(rng.choice(n, size=min(int(row_len), n), replace=False))
+    have0 = set(cols[rows == 0].tolist())
+    add = np.array([j for j in dense_cols if j not in have0], dtype=np.int64)
+    rows = np.concatenate([rows, np.zeros(add.shape[0], dtype=np.int64)])
+    cols = np.concatenate([cols, add])
+    vals = rng.standard_normal(rows.shape[0])
+    row_ptr, col_idx, val = _csr_from_coo(m, n, rows, cols, vals)
+    support = m + extra_support
+    S = np.sort(rng.choice(n, size=support, replace=False))
+    x_star = np.zeros(n)
+    x_star[S] = rng.uniform(0.1, 1.0, size=support)
+    y_star = rng.standard_normal(m)
+    z_star = rng.uniform(0.1, 1.0, size=n)
+    z_star[S] = 0.0
+    b = csr_matvec(row_ptr, col_idx, val, x_star)
+    c = csr_rmatvec(row_ptr, col_idx, val, y_star, n) + z_star
+    return dict(name=f"dense_line_m{m}_n{n}", m=m, n=n, row_ptr=row_ptr, col_idx=col_idx, val=val, b=b,
+                c=c, lb=np.zeros(n), ub=np.full(n, np.inf), sense=np.full(m, EQ, dtype=np.int8),
+                x_star=x_star, y_star=y_star, z_star=z_star, obj_star=float(c @ x_star), support=S)
+
+
 def small_face_lp(seed: int, base_seed: int = 0):
     """200 x 500, 5 nnz per column, |S| = 250 (face dimension >= 50)."""
     return random_face_lp(200, 500, 250, workload_seed(base_seed, 0, seed), 5,

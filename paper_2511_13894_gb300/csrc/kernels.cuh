@@ -62,14 +62,16 @@ struct DevIter {
 
 // Halpern loop buffers: the PDHG output T(z) = (xp, yp) of a check step and
 // z - T(z) = (dx, dy); hw[i] = (t + i + 1) / (t + i + 2), the anchoring
-// weight of step i of the next chunk (t = steps since the anchor).  The
-// anchor is DevIter::x_r / y_r.
+// weight of step i of the next chunk (t = steps since the anchor), and
+// hs[i] = 1 - hw[i] = 1 / (t + i + 2) in FP32 for the FP32-bulk steps.  The
+// anchor is DevIter::x_r / y_r (FP64) and DevIter32::xa / ya (FP32 bulk).
 struct DevHalpern {
   double* xp;
   double* yp;
   double* dx;
   double* dy;
   double* hw;
+  float* hs;
 };
 
 
@@ -830,9 +832,11 @@ struct PrimalOpH {
   __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
     const double g = p.c - a.v[0];
     const double xn = clamp_i(p.x - p.tau * g, p.l, p.u);
-    w.xbar[j] = 2.0 * xn - p.x;
+    const double xb = 2.0 * xn - p.x;
+    w.xbar[j] = xb;
     if (!probe) {
-      const double r = fma(p.rho, xn - p.x, xn);
+      // the reflected point x+ + rho (x+ - x); with rho = 1 it is x_bar itself
+      const double r = p.rho == 1.0 ? xb : fma(p.rho, xn - p.x, xn);
       w.x[j] = fma(p.wt, r - p.x0, p.x0);
     }
     if (p.last) {
@@ -871,7 +875,7 @@ struct DualOpH {
     double yn = p.y + p.sigma * (p.b - a.v[0]);
     if (p.ge && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
     if (!probe) {
-      const double r = fma(p.rho, yn - p.y, yn);
+      const double r = p.rho == 1.0 ? fma(2.0, yn, -p.y) : fma(p.rho, yn - p.y, yn);
       w.y[i] = fma(p.wt, r - p.y0, p.y0);
     }
     if (p.last) {
@@ -1255,6 +1259,8 @@ struct DevIter32 {
   float2* sum_y;
   float* xlo;
   float* ylo;
+  float2* xa;  // Halpern loop: the anchor z_0 as float-float pairs (hi, lo)
+  float2* ya;
 };
 
 // (hi, lo) += (a, b) for float-float pairs, TwoSum of the high parts
@@ -1367,6 +1373,161 @@ struct DualOp32 {
     w.sum_y[i] = sy;
     w.y[i] = yh;
     w.ylo[i] = yl;
+  }
+};
+
+
+// ---------------------------------------------------------------------------
+// The Halpern loop in FP32 bulk: the PDHG output T(z) is formed as in
+// PrimalOp32 / DualOp32 (FP32 values and gathers, float-float row sums and
+// iterates), and the anchored combination is taken on float-float pairs,
+//   r = T(z) + rho (T(z) - z),   z <- r + s (z_0 - r),   s = 1 - w = hs[it],
+// which is the Halpern step w r + (1 - w) z_0 of the FP64 operators.  No
+// FP64 arithmetic runs except on a check step, which widens T(z) and
+// z - T(z) to the FP64 buffers the FP64 evaluation reads.
+// ---------------------------------------------------------------------------
+
+// (ah, al) - (bh, bl) as a normalised pair: TwoSum of the high parts, the low
+// parts added to its error
+__device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float s = ah - bh;
+  const float bb = s - ah;
+  const float err = (ah - (s - bb)) + (-bh - bb);
+  const float t = err + (al - bl);
+  const float h2 = s + t;
+  const float b2 = h2 - s;
+  l = (s - (h2 - b2)) + (t - b2);
+  h = h2;
+}
+
+// (hi, lo) += a * (bh, bl): a * bh exact (fma), a * bl rounded into the low
+// part, both sums TwoSum
+__device__ __forceinline__ void ff_axpy_ff(float& hi, float& lo, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float e = fmaf(a, bl, fmaf(a, bh, -p));
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  const float l = lo + (err + e);
+  const float h2 = s + l;
+  const float b2 = h2 - s;
+  lo = (s - (h2 - b2)) + (l - b2);
+  hi = h2;
+}
+
+// z <- r + s (z_0 - r) with r = T(z) + rho (T(z) - z), all pairs
+__device__ __forceinline__ void ff_halpern(float th, float tl, float zh, float zl, float2 z0, float rho, float s,
+                                           float& oh, float& ol) {
+  float dh, dl;
+  ff_sub(th, tl, zh, zl, dh, dl);
+  float rh = th, rl = tl;
+  ff_axpy_ff(rh, rl, rho, dh, dl);
+  float eh, el;
+  ff_sub(z0.x, z0.y, rh, rl, eh, el);
+  ff_axpy_ff(rh, rl, s, eh, el);
+  oh = rh;
+  ol = rl;
+}
+
+struct PrimalOpH32 {
+  using Acc = SumFF;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = float;
+  using GT = float;
+  const Scalars* S;
+  int it, last_it, probe;
+  const float* __restrict__ y;
+  DevModel32 md;
+  DevIter32 w;
+  DevHalpern h;
+  __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const float* gsrc(int) const { return y; }
+  __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
+  struct Pre {
+    float c, l, u, x, xl, tau, s, rho;
+    float2 x0;
+    bool last;
+  };
+  __device__ Pre prefetch(int j) const {
+    const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
+    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.xlo[j], (float)S->tau, h.hs[it], (float)S->rho,
+               w.xa[j], last};
+  }
+  __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
+    const float g = (p.c - a.hi[0]) - a.lo[0];
+    float th = p.x, tl = p.xl;
+    ff_axpy(th, tl, -p.tau, g);
+    const float xc = clamp_f(th, p.l, p.u);
+    if (xc != th || (th == p.l && tl < 0.0f) || (th == p.u && tl > 0.0f)) {
+      th = xc;
+      tl = 0.0f;
+    }
+    w.xbar[j] = (2.0f * th - p.x) + (2.0f * tl - p.xl);
+    if (!probe) {
+      float oh, ol;
+      ff_halpern(th, tl, p.x, p.xl, p.x0, p.rho, p.s, oh, ol);
+      w.x[j] = oh;
+      w.xlo[j] = ol;
+    }
+    if (p.last) {
+      float dh, dl;
+      ff_sub(p.x, p.xl, th, tl, dh, dl);
+      h.xp[j] = (double)th + (double)tl;
+      h.dx[j] = (double)dh + (double)dl;
+    }
+  }
+};
+
+struct DualOpH32 {
+  using Acc = SumFF;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = float;
+  using GT = float;
+  const Scalars* S;
+  int it, last_it, probe;
+  const float* __restrict__ xbar;
+  DevModel32 md;
+  DevIter32 w;
+  DevHalpern h;
+  __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const float* gsrc(int) const { return xbar; }
+  __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
+  struct Pre {
+    float b, y, yl, sigma, s, rho;
+    float2 y0;
+    bool ge, last;
+  };
+  __device__ Pre prefetch(int i) const {
+    const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
+    return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, h.hs[it], (float)S->rho, w.ya[i], md.ge[i] != 0,
+               last};
+  }
+  __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
+    const float r = (p.b - a.hi[0]) - a.lo[0];
+    float th = p.y, tl = p.yl;
+    ff_axpy(th, tl, p.sigma, r);
+    if (p.ge && (th < 0.0f || (th == 0.0f && tl < 0.0f))) {  // y >= 0 on '>' rows
+      th = 0.0f;
+      tl = 0.0f;
+    }
+    if (!probe) {
+      float oh, ol;
+      ff_halpern(th, tl, p.y, p.yl, p.y0, p.rho, p.s, oh, ol);
+      w.y[i] = oh;
+      w.ylo[i] = ol;
+    }
+    if (p.last) {
+      float dh, dl;
+      ff_sub(p.y, p.yl, th, tl, dh, dl);
+      h.yp[i] = (double)th + (double)tl;
+      h.dy[i] = (double)dh + (double)dl;
+    }
   }
 };
 

@@ -168,6 +168,8 @@ struct Iter32 {
   float* ylo;
   float2* sx;  // float-float running sums
   float2* sy;
+  float2* xa;  // Halpern loop: float-float anchors
+  float2* ya;
 };
 
 __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
@@ -184,6 +186,7 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
       w32.xlo[i] = (float)(x0 - (double)h);
       w32.xbar[i] = h;
       w32.sx[i] = make_float2(0.f, 0.f);
+      w32.xa[i] = make_float2(h, w32.xlo[i]);
     }
   }
   if (i < m) {
@@ -194,6 +197,7 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
       w32.y[i] = 0.0f;
       w32.ylo[i] = 0.0f;
       w32.sy[i] = make_float2(0.f, 0.f);
+      w32.ya[i] = make_float2(0.f, 0.f);
     }
   }
 }
@@ -279,11 +283,25 @@ __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
 }
 
 // Halpern loop: the anchoring weights (t + i + 1) / (t + i + 2) of the
-// steps i < P of the next chunk, t = steps since the anchor
-__global__ void k_halpern_weights(const Scalars* S, double* hw, int P) {
+// steps i < P of the next chunk, t = steps since the anchor, and their
+// complements 1 / (t + i + 2) in FP32 (hs, FP32 bulk)
+__global__ void k_halpern_weights(const Scalars* S, double* hw, float* hs, int P) {
   if (S->done) return;
   const long long t = S->t;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) hw[i] = (double)(t + i + 1) / (double)(t + i + 2);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    hw[i] = (double)(t + i + 1) / (double)(t + i + 2);
+    hs[i] = (float)(1.0 / (double)(t + i + 2));
+  }
+}
+
+// FP32-bulk Halpern loop, end of a phase: FP64 copies of the float-float
+// iterate z for the accessors
+__global__ void k_h32_to64(int n, int m, const float* __restrict__ x32, const float* __restrict__ xlo,
+                           const float* __restrict__ y32, const float* __restrict__ ylo, double* __restrict__ x,
+                           double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (double)x32[i] + (double)xlo[i];
+  if (i < m) y[i] = (double)y32[i] + (double)ylo[i];
 }
 
 // after a chunk of iterations: iteration counters and 1/t for the averages
@@ -376,6 +394,12 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
       const double xn = hz.xp[i];
       w.x[i] = xn;
       w.x_r[i] = xn;
+      if (w32.x) {  // FP32 bulk: the float-float iterate and anchor
+        const float h = (float)xn, lo = (float)(xn - (double)h);
+        w32.x[i] = h;
+        w32.xlo[i] = lo;
+        w32.xa[i] = make_float2(h, lo);
+      }
       if (rr.rx) {
         const size_t slot = (size_t)(S->restarts % 8) * (size_t)n;
         rr.rx[slot + i] = (float)xn;
@@ -383,8 +407,15 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
       }
     }
     if (i < m) {
-      w.y[i] = hz.yp[i];
-      w.y_r[i] = hz.yp[i];
+      const double yn = hz.yp[i];
+      w.y[i] = yn;
+      w.y_r[i] = yn;
+      if (w32.y) {
+        const float h = (float)yn, lo = (float)(yn - (double)h);
+        w32.y[i] = h;
+        w32.ylo[i] = lo;
+        w32.ya[i] = make_float2(h, lo);
+      }
     }
     return;
   }
@@ -744,6 +775,8 @@ int ensure_fp32(pdhgc_lp* lp) {
   RET(lp->alloc(&lp->it32.ylo, m));
   RET(lp->alloc(&lp->it32.sx, n));
   RET(lp->alloc(&lp->it32.sy, m));
+  RET(lp->alloc(&lp->it32.xa, n));
+  RET(lp->alloc(&lp->it32.ya, m));
   RET(lp->alloc(&lp->chat32, n));
   RET(lp->alloc(&lp->lhat32, n));
   RET(lp->alloc(&lp->uhat32, n));
@@ -849,6 +882,7 @@ int ensure_halpern(pdhgc_lp* lp) {
   RET(lp->alloc(&lp->hz.dx, (size_t)lp->n));
   RET(lp->alloc(&lp->hz.dy, (size_t)lp->m));
   RET(lp->alloc(&lp->hz.hw, (size_t)4096));
+  RET(lp->alloc(&lp->hz.hs, (size_t)4096));
   lp->have_h = true;
   return PDHGC_OK;
 }
@@ -863,9 +897,9 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const bool halpern = pi.algorithm == PDHGC_ALG_HALPERN;
   if (halpern) RET(ensure_halpern(lp));
   const DevHalpern hz = lp->hz;
-  const Iter32 w32 = fp32 ? lp->it32 : Iter32{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
-                       lp->it32.ylo};
+  const Iter32 w32 = fp32 ? lp->it32 : Iter32{};
+  const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
+                       lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
   k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
   lp->launches += 2;
@@ -885,11 +919,16 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   if (halpern) {
     // the anchor's fixed-point residual: T of the start point (not an
     // iteration), its check quantities, and the first chunk's weights
-    RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
-    RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
+    if (fp32) {
+      RET(launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 0, 1, lp->it32.y, md32, it32, hz}, nullptr, st));
+      RET(launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 0, 1, lp->it32.xbar, md32, it32, hz}, nullptr, st));
+    } else {
+      RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
+      RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
+    }
     RET(launch_eval_h(lp, md, st, false));
     k_decide_h<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
-    k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, pi.check_period);
+    k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, hz.hs, pi.check_period);
     lp->launches += 2;
     CKL();
   }
@@ -914,7 +953,14 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const int64_t before = lp->launches;
   int rc = PDHGC_OK;
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
-    if (halpern) {
+    if (halpern && fp32) {
+      const int last = pi.check_period - 1;
+      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, i, last, 0, lp->it32.y, md32, it32, hz}, nullptr, cs,
+                        true);
+      if (rc == PDHGC_OK)
+        rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, lp->it32.xbar, md32, it32, hz}, nullptr,
+                          cs, true);
+    } else if (halpern) {
       const int last = pi.check_period - 1;
       rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, nullptr, cs, true);
       if (rc == PDHGC_OK)
@@ -930,7 +976,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
         rc = launch_tiles(lp, false, true, DualOp{lp->S, i, lp->it.xbar, md, lp->it}, nullptr, cs, true);
     }
   }
-  if (rc == PDHGC_OK && fp32) {
+  if (rc == PDHGC_OK && fp32 && !halpern) {
     k_to64<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it32.x, lp->it32.y, lp->it32.xlo, lp->it32.ylo, lp->it32.sx,
                                 lp->it32.sy, md.lhat, md.uhat, lp->it.x, lp->it.y, lp->it.sum_x, lp->it.sum_y);
     lp->launches++;
@@ -948,7 +994,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
     k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr, hz);
     lp->launches += 2;
     if (halpern) {
-      k_halpern_weights<<<1, 256, 0, cs>>>(lp->S, hz.hw, pi.check_period);
+      k_halpern_weights<<<1, 256, 0, cs>>>(lp->S, hz.hw, hz.hs, pi.check_period);
       lp->launches++;
     }
   }
@@ -964,6 +1010,10 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   CK(cudaGraphLaunch(exec, st));
   k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat, hz);
   lp->launches++;
+  if (fp32 && halpern) {
+    k_h32_to64<<<gnm, 256, 0, st>>>(n, m, lp->it32.x, lp->it32.xlo, lp->it32.y, lp->it32.ylo, lp->it.x, lp->it.y);
+    lp->launches++;
+  }
   CKL();
   CK(cudaStreamSynchronize(st));
   int derr = 0;
@@ -1036,7 +1086,6 @@ int check_params(const pdhgc_params* p) {
   if (p->algorithm != PDHGC_ALG_AVERAGED && p->algorithm != PDHGC_ALG_HALPERN)
     return set_err(PDHGC_ERR_INVALID_ARG, "algorithm must be PDHGC_ALG_AVERAGED or PDHGC_ALG_HALPERN");
   if (p->algorithm == PDHGC_ALG_HALPERN) {
-    if (p->precision != PDHGC_FP64) return set_err(PDHGC_ERR_INVALID_ARG, "the Halpern loop runs in FP64 only");
     if (!(p->reflection >= 0.0 && p->reflection <= 1.0) || !std::isfinite(p->pid_kp) ||
         !std::isfinite(p->pid_ki) || !std::isfinite(p->pid_kd))
       return set_err(PDHGC_ERR_INVALID_ARG, "reflection must lie in [0, 1] and the PID gains be finite");
@@ -2045,6 +2094,18 @@ int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t
 
 int64_t pdhgc_kernel_launches(const pdhgc_lp* lp) { return lp ? lp->launches : 0; }
 
+int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out) {
+  if (!lp || !out) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
+  const pdhgc_lp::Mat* mats[2] = {&lp->A, &lp->T};
+  for (int k = 0; k < 2; ++k) {
+    out[4 * k + 0] = mats[k]->nb_cta;
+    out[4 * k + 1] = mats[k]->nb_warp;
+    out[4 * k + 2] = mats[k]->nb_sell;
+    out[4 * k + 3] = mats[k]->cta_rows;
+  }
+  return PDHGC_OK;
+}
+
 int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   if (!lp || iters < 1 || !ms_out) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
   if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
@@ -2053,8 +2114,8 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
   const bool halpern = lp->params.algorithm == PDHGC_ALG_HALPERN && lp->have_h;
   const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
-  const DevIter32 it32{lp->it32.x, lp->it32.y, lp->it32.xbar, lp->it32.sx, lp->it32.sy, lp->it32.xlo,
-                       lp->it32.ylo};
+  const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
+                       lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
   // the replay must not stop on the phase's done flag or iteration limit
   Scalars S;
   CK(cudaMemcpy(&S, lp->S, sizeof(S), cudaMemcpyDeviceToHost));
@@ -2070,7 +2131,9 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   for (int i = 0; i < iters && rc == PDHGC_OK; ++i) {
     CK(cudaEventRecord(ev[3 * i], st));
     // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
-    if (halpern)
+    if (halpern && fp32)
+      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 1, 0, lp->it32.y, md32, it32, lp->hz}, nullptr, st);
+    else if (halpern)
       rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, nullptr, st);
     else if (fp32)
       rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, 0, lp->it32.y, md32, it32}, nullptr, st);
@@ -2078,7 +2141,10 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
       rc = launch_tiles(lp, true, true, PrimalOp{lp->S, 0, lp->it.y, md, lp->it}, nullptr, st);
     if (rc != PDHGC_OK) break;
     CK(cudaEventRecord(ev[3 * i + 1], st));
-    if (halpern)
+    if (halpern && fp32)
+      rc = launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 1, 0, lp->it32.xbar, md32, it32, lp->hz}, nullptr,
+                        st);
+    else if (halpern)
       rc = launch_tiles(lp, false, true, DualOpH{lp->S, 0, 1, 0, lp->it.xbar, md, lp->it, lp->hz}, nullptr, st);
     else if (fp32)
       rc = launch_tiles(lp, false, true, DualOp32{lp->S, 0, lp->it32.xbar, md32, it32}, nullptr, st);

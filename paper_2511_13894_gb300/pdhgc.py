@@ -107,6 +107,7 @@ _sig = {
     "pdhgc_get_solution": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_iterates": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
+    "pdhgc_get_layout": (C.c_int, [_vp, _vp]),
     "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
     "pdhgc_kkt_eval": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp, C.POINTER(Report), _vp]),
@@ -267,6 +268,14 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    def get_layout(self):
+        """pdhgc_get_layout: SpMV row-segment blocks of A and A'."""
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib.pdhgc_get_layout(self._h, out.ctypes.data), "pdhgc_get_layout")
+        keys = ("nb_cta", "nb_warp", "nb_sell", "cta_rows")
+        return dict(A={k: int(out[i]) for i, k in enumerate(keys)},
+                    AT={k: int(out[4 + i]) for i, k in enumerate(keys)})
 
     # -- checkpoint ----------------------------------------------------------------
     def get_state(self) -> bytes:

@@ -70,6 +70,7 @@ def test_headline_bound_follows_the_larger_fraction():
 
 @pytest.mark.parametrize("fp32, halpern, ms, alg_bytes, kernel", [
     (False, True, (0.02894, 0.02048), 63281924, "spmv<PrimalOpH> (primal step)"),
+    (True, True, (0.02289, 0.01843), 43654616, "spmv<PrimalOpH32> (primal step)"),
     (False, False, (0.02758, 0.02004), 66481924, "spmv<PrimalOp> (primal step)"),
     (True, False, (0.02266, 0.01812), 46854616, "spmv<PrimalOp32> (primal step)"),
 ])
@@ -87,8 +88,34 @@ def test_kernel_roofline(fp32, halpern, ms, alg_bytes, kernel):
     assert r["frac"] == top["frac"] and r["frac"] >= min(r["hbm"]["frac"], r["fp64"]["frac"])
     if fp32:
         assert r["fp64"]["frac"] == 0.0 and r["bound"] == "hbm"
-    if halpern:
-        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"  # the measured headline case
-    assert sum(r["bytes_per_launch"]) == sum(bench.algorithmic_bytes_halpern(m, n, nnz) if halpern else
-                                             bench.algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
-                                             if fp32 else bench.algorithmic_bytes(m, n, nnz))
+    if halpern and not fp32:
+        # one FMA per nonzero plus 5 FP64 operations per column (x_bar doubles as the reflected point)
+        assert r["fp64"]["ops_per_launch"] == nnz + 5 * n
+    if halpern and fp32:
+        expect = bench.algorithmic_bytes_halpern32(m, n, nnz)
+    elif halpern:
+        expect = bench.algorithmic_bytes_halpern(m, n, nnz)
+    elif fp32:
+        expect = bench.algorithmic_bytes(m, n, nnz, s_v=4, s_x=4, s_sum=8, s_lo=4)
+    else:
+        expect = bench.algorithmic_bytes(m, n, nnz)
+    assert sum(r["bytes_per_launch"]) == sum(expect)
+
+
+def test_halpern32_bytes():
+    # FP32 bulk halves the value and gathered-vector bytes; the float-float
+    # iterate and anchor keep 8 B each per entry
+    m, n, nnz = 1000, 4000, 30000
+    p32, d32 = bench.algorithmic_bytes_halpern32(m, n, nnz)
+    p64, d64 = bench.algorithmic_bytes_halpern(m, n, nnz)
+    assert p64 - p32 == 4 * nnz + 4 * m + n * (3 * 4 + 8 + 8 + 8 + 4 - 7 * 8) * -1
+    assert d64 - d32 == 4 * nnz + 4 * n + m * (33 - 29)
+
+
+def test_corner_speedup_needs_corners_on_both_arms():
+    def arm(ms, statuses):
+        return {"total_ms": ms, "reps": [({}, {"status_name": st}) for st in statuses]}
+    ok = bench.corner_speedup(arm(300.0, ["CORNER_DONE"] * 3), arm(200.0, ["CORNER_DONE"] * 3))
+    assert ok["value"] == pytest.approx(1.5) and ok["reason"] is None
+    bad = bench.corner_speedup(arm(300.0, ["CORNER_LIMIT"] * 3), arm(200.0, ["CORNER_DONE"] * 3))
+    assert bad["value"] is None and bad["base_corner_status"] == ["CORNER_LIMIT"] and bad["reason"]

@@ -136,8 +136,6 @@ def test_halpern_refused_where_not_built():
     lp = lpgen.small_face_lp(0)
     g = P.lp_from_dict(lp)
     with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
-        g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK)
-    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
         g.solve(algorithm=P.HALPERN, reflection=1.5)
     with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
         g.solve(algorithm=7)
@@ -146,10 +144,95 @@ def test_halpern_refused_where_not_built():
         B.solve(algorithm=P.HALPERN)
 
 
+def test_halpern_corner_phase_on_skewed_power_law_matches_oracle():
+    # 3000 x 12000 with power-law columns up to 2000 nonzeros (warp and SELL
+    # segments), '<' rows and upper bounds: the whole corner phase (about
+    # 51k iterations) takes the oracle's iterations, restarts and counts
+    lp = _lp_cases()["power_law_skewed"]()
+    ref1 = oracle.solve(lp, HP)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=3))
+    g = P.lp_from_dict(lp)
+    r1 = g.solve(algorithm=P.HALPERN)
+    assert r1["iters"] == ref1["iters"] and r1["restarts"] == ref1["restarts"]
+    rep = g.corner_phase(obj_seed=3)
+    assert rep["status_name"] == "CORNER_DONE" and refc["status"] == oracle.CORNER_DONE
+    assert rep["iters"] == refc["iters"] and rep["restarts"] == refc["restarts"]
+    x, _, _ = g.get_solution(P.CORNER)
+    xo, _, _ = oracle.unscale(ref1["model"], refc["x_hat"], refc["y_hat"])
+    assert rel_err(x, xo) <= 1e-7
+    orep = oracle.kkt_report(ref1["model"], refc["x_hat"], refc["y_hat"])
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure", "primal_push_est"):
+        assert rep[k] == orep[k], k
+
+
+# ---------------------------------------------------------------------------
+# The Halpern loop in FP32 bulk: FP32 values and gathers, float-float
+# iterates, anchors and row sums, FP64 checks.  No exact pin exists (a
+# different rounding of the same map); results are judged by the FP64
+# evaluation and by the distance to the FP64 oracle.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed", "transport_30x70"])
+def test_halpern_fp32_bulk_reaches_the_fp64_tolerance(name):
+    lp = _lp_cases()[name]()
+    ref = oracle.solve(lp, HP)
+    g = P.lp_from_dict(lp)
+    rep = g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK)
+    print(f"{name}: Halpern FP32 bulk {rep['iters']} iterations, FP64 oracle {ref['iters']}")
+    assert rep["status_name"] == "OPTIMAL" and rep["precision"] == P.FP32_BULK and rep["chosen"] == 2
+    assert rep["rel_kkt"] <= 1e-6
+    pobj = ref["eval"]["pobj"]
+    assert abs(rep["pobj"] - pobj) <= 1e-5 * (1.0 + abs(pobj))
+    x, _, _ = g.get_solution()
+    assert np.all(x >= lp["lb"] - 1e-12 * np.abs(lp["lb"])) and np.all(x <= lp["ub"] + 1e-12 * np.abs(lp["ub"]))
+
+
+def test_halpern_fp32_bulk_iterate_error_against_the_fp64_oracle():
+    # the stated error of the FP32-bulk Halpern iterates z and T(z) against the
+    # FP64 oracle at k = 100 and k = 1000 (max-norm, relative): FP32 rounding
+    # of the matrix and the gathered vectors (about 6e-8) amplified by the map
+    lp = _lp_cases()["power_law_skewed"]()
+    for k, bound in ((100, 1e-4), (1000, 1e-2)):
+        ref = oracle.run_iterations(lp, k, HP)
+        s = ref["state"]
+        g = P.lp_from_dict(lp)
+        rep = g.solve(max_iters=k, eps_rel=-1.0, algorithm=P.HALPERN, precision=P.FP32_BULK)
+        assert rep["iters"] == k
+        it = g.get_iterates()
+        errs = (rel_err(it["x"], s.x), rel_err(it["y"], s.y), rel_err(it["x_avg"], s.xp),
+                rel_err(it["y_avg"], s.yp))
+        print(f"Halpern FP32 bulk vs FP64 oracle at k={k}: x {errs[0]:.3e} y {errs[1]:.3e} "
+              f"T(z)_x {errs[2]:.3e} T(z)_y {errs[3]:.3e}")
+        assert max(errs) <= bound
+
+
+@pytest.mark.parametrize("name", ["face_200x500_s0", "bounded_ineq", "power_law_skewed"])
+def test_halpern_fp32_bulk_corner_phase(name):
+    # the corner phase in FP32 bulk reaches Section 3.1's rule (CORNER_DONE);
+    # its corner measure is stated beside the FP64 oracle's
+    lp = _lp_cases()[name]()
+    ref1 = oracle.solve(lp, HP)
+    refc = oracle.corner_phase(ref1, dict(obj_seed=3))
+    orep = oracle.kkt_report(ref1["model"], refc["x_hat"], refc["y_hat"])
+    g = P.lp_from_dict(lp)
+    g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK)
+    rep = g.corner_phase(obj_seed=3)
+    print(f"{name}: FP32 corner {rep['iters']} iterations, measure {rep['corner_measure']}; "
+          f"FP64 oracle {refc['iters']}, measure {orep['corner_measure']}")
+    assert rep["status_name"] == "CORNER_DONE" and rep["chosen"] == 2
+    assert rep["rel_p"] <= 1e-6 * (1 + 1e-9)
+    assert rep["corner_measure"] <= orep["corner_measure"] + max(5, lp["m"] // 100)
+    x, _, _ = g.get_solution(P.CORNER)
+    assert np.all(x >= lp["lb"] - 1e-12 * np.abs(lp["lb"])) and np.all(x <= lp["ub"] + 1e-12 * np.abs(lp["ub"]))
+
+
 def test_halpern_profile_iteration_times_its_kernels():
     lp = lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000)
     g = P.lp_from_dict(lp)
     g.solve(algorithm=P.HALPERN)
+    ms = g.profile_iteration(5)
+    assert ms[0] > 0.0 and ms[1] > 0.0
+    g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK)
     ms = g.profile_iteration(5)
     assert ms[0] > 0.0 and ms[1] > 0.0
 

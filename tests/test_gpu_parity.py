@@ -39,6 +39,9 @@ def _lp_cases():
         "power_law_skewed": lambda: lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000),
         "transport_30x70": lambda: lpgen.transportation_lp(30, 70, seed=2),
         "tiny_5x11": lambda: lpgen.tiny_face_lp(5, 11, 7, seed=101),
+        # one row of A with 4500 nonzeros and one column with 4150: both
+        # matrix passes run their one-CTA-per-row segment
+        "dense_lines": lambda: lpgen.dense_line_lp(4200, 12000, 4500, 4150, 400, seed=2, col_nnz=3),
     }
 
 
@@ -190,6 +193,37 @@ def test_kkt_eval_of_a_point_matches_oracle(name):
     # the constructed optimum is optimal: every residual and the gap vanish
     rep = P.kkt_eval(lp, lp["x_star"], lp["y_star"])
     assert rep["rel_kkt"] <= 1e-12
+
+
+@pytest.mark.parametrize("alg", ["averaged", "halpern"])
+def test_dense_lines_run_the_cta_segment_and_match_oracle(alg):
+    # rows longer than 4096 nonzeros (in A and in A') go to the one-CTA-per-row
+    # segment; the full solve takes the oracle's iterations and restarts
+    lp = _lp_cases()["dense_lines"]()
+    g = P.lp_from_dict(lp)
+    lay = g.get_layout()
+    assert lay["A"]["nb_cta"] >= 1 and lay["AT"]["nb_cta"] >= 1, lay
+    ref = oracle.solve(lp, dict(algorithm=alg))
+    rep = g.solve(algorithm=P.HALPERN if alg == "halpern" else P.AVERAGED)
+    assert rep["status_name"] == "OPTIMAL" and ref["status"] == oracle.OPTIMAL
+    assert rep["iters"] == ref["iters"] and rep["restarts"] == ref["restarts"]
+    x, y, z = g.get_solution()
+    xo, yo, zo = oracle.unscale(ref["model"], ref["x_hat"], ref["y_hat"])
+    assert rel_err(x, xo) <= 1e-8 and rel_err(y, yo) <= 1e-8
+    orep = oracle.kkt_report(ref["model"], ref["x_hat"], ref["y_hat"])
+    for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure"):
+        assert rep[k] == orep[k], k
+    # FP32 bulk through the same segments.  Its fixed point is the optimum of
+    # the LP with FP32-rounded scaled coefficients: on the 4500-entry row that
+    # rounding (2^-24 relative per value) leaves an FP64 relative primal
+    # residual of about 2e-6 at that point (an FP64 emulation of the FP32 map
+    # shows the same floor), so the stated bound here is rel-KKT <= 1e-5
+    r32 = g.solve(algorithm=P.HALPERN if alg == "halpern" else P.AVERAGED, precision=P.FP32_BULK,
+                  max_iters=200_000)
+    print(f"dense lines, {alg} FP32 bulk: {r32['status_name']} after {r32['iters']} iterations, "
+          f"rel_p {r32['rel_p']:.2e} rel_d {r32['rel_d']:.2e} rel_gap {r32['rel_gap']:.2e}")
+    assert r32["rel_kkt"] <= 1e-5
+    assert abs(r32["pobj"] - orep["pobj"]) <= 1e-5 * (1.0 + abs(orep["pobj"]))
 
 
 # ---------------------------------------------------------------------------
