@@ -343,6 +343,12 @@ def fp64_ops(m, n, nnz):
     return nnz + 4 * n, nnz + 3 * m
 
 
+def oracle_setup(lp):
+    """The oracle's model, parameters and step size for lp (untimed setup)."""
+    import oracle
+    return oracle.setup(lp)
+
+
 def oracle_sample(model, p, eta, iters, algorithm):
     """`iters` phase-1 steps of the oracle's loop ("averaged" or "halpern")
     from the start point, with the restart checks every check period; returns
@@ -379,8 +385,8 @@ def oracle_sample(model, p, eta, iters, algorithm):
 
 def headline_algorithm(args):
     """The loop the headline line measures: the Halpern loop unless
-    --algorithm averaged; the batched workload runs the averaged loop only."""
-    if args.workload == "batch_512" or args.algorithm == "averaged":
+    --algorithm averaged (the batched workload included)."""
+    if args.algorithm == "averaged":
         return "averaged"
     return "halpern"
 
@@ -496,32 +502,38 @@ def cpu_baseline_sample(lp, iters, algorithm="averaged", threads=0, workload=Non
     return out
 
 
-def batch_bytes_per_iter(lp, s_v=4, s_x=4, s_sum=8, s_lo=4):
+def batch_bytes_per_iter(lp, halpern=False):
+    """Algorithmic bytes of one FP32-bulk iteration of one LP of the batch."""
     m, n, nnz = int(lp["m"]), int(lp["n"]), int(lp["row_ptr"][-1])
-    p, d = algorithmic_bytes(m, n, nnz, s_v, s_x, s_sum, s_lo)
+    if halpern:
+        p, d = algorithmic_bytes_halpern32(m, n, nnz)
+    else:
+        p, d = algorithmic_bytes(m, n, nnz, 4, 4, 8, 4)
     return p + d
 
 
 def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     """512 uneven LPs (random-face construction, m ~ U{50..5000}) in one
-    persistent, graph-captured launch per phase with the autotuned schedule,
-    FP32 bulk.  One step = phase 1 of every LP to rel-KKT 1e-6 plus Algorithm
-    1 on every LP.  Ranks split the LPs round-robin (strong scaling: the batch
+    persistent, graph-captured launch with the autotuned schedule, FP32 bulk,
+    the headline's inner loop.  One step = phase 1 of every LP to rel-KKT
+    1e-6 plus Algorithm 1 on every LP, both in the same launch.  Ranks split the LPs round-robin (strong scaling: the batch
     is fixed).  The single-LP FP64 path on a size-stratified sample of the LPs,
     one after another, gives the sequential reference time."""
     all_lps = lpgen.batch_lps(512)
     lps = shard(all_lps, rank, world)
+    alg = headline_algorithm(args)
+    algorithm = P.HALPERN if alg == "halpern" else P.AVERAGED
     stream = torch.cuda.current_stream()
     B = P.Batch(lps, stream=stream.cuda_stream)
-    params = P.default_params(precision=P.FP32_BULK, max_iters=args.phase1_max_iters)
+    params = P.default_params(precision=P.FP32_BULK, max_iters=args.phase1_max_iters, algorithm=algorithm)
     tuned = B.tune(256, params)  # schedule autotuner (untimed setup)
     cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        r1 = B.solve(params)
-        rc = B.corner_phase(cparams)
-        return r1, rc
+        # both phases of every LP in one persistent launch (no batch-wide
+        # barrier between phase 1 and the corner phase)
+        return B.solve_corner(params, cparams)
 
     for _ in range(args.warmup):
         step()
@@ -550,7 +562,8 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
         barrier()
         step_ms.append(e0.elapsed_time(e1))
         iters.append(sum(a["iters"] + b["iters"] for a, b in zip(r1, rc)))
-        byte_iters += sum((a["iters"] + b["iters"]) * batch_bytes_per_iter(lp) for a, b, lp in zip(r1, rc, lps))
+        byte_iters += sum((a["iters"] + b["iters"]) * batch_bytes_per_iter(lp, alg == "halpern")
+                          for a, b, lp in zip(r1, rc, lps))
         last = (r1, rc)
     clk = clocks.stop()
     launches = B.kernel_launches() - l0
@@ -570,7 +583,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
             g = P.lp_from_dict(all_lps[k], stream=stream.cuda_stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            g.solve(max_iters=args.phase1_max_iters)
+            g.solve(max_iters=args.phase1_max_iters, algorithm=algorithm)
             g.corner_phase(cparams)
             torch.cuda.synchronize()
             t_s += time.perf_counter() - t0
@@ -578,7 +591,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
         est = t_s * len(all_lps) / len(sample)
         seq = {"sample_lps": len(sample), "sample_seconds": t_s, "estimated_seconds_all": est,
                "speedup_batched_vs_sequential_fp64": est / (total_ms / args.steps * 1e-3),
-               "note": "single-LP FP64 path (graph-driven loop, one LP at a time), size-stratified "
+               "note": f"single-LP FP64 path ({alg} loop, graph-driven, one LP at a time), size-stratified "
                        "sample scaled to all LPs"}
     # end to end: batch created from host arrays, both phases, every x and y back
     torch.cuda.synchronize()
@@ -587,8 +600,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     Be.set_block(tuned["threads"])
     Be.set_layout(tuned["sell"])
     Be.set_lanes(tuned["lanes_a"], tuned["lanes_t"])
-    a1 = Be.solve(params)
-    a2 = Be.corner_phase(cparams)
+    a1, a2 = Be.solve_corner(params, cparams)
     d2h = 0
     for k in range(len(lps)):
         x, y = Be.get_solution(k, P.CORNER)
@@ -606,13 +618,15 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
         picks = [by_size[k] for k in range(16, len(by_size), len(by_size) // 16)][:16]
         t_cpu, it_cpu = 0.0, 0
         for lp in picks:
-            c1 = cpu_baseline_sample(lp, 4096)
-            t_cpu += 4096 / c1["value"]
+            model, p, sigma_max, eta = oracle_setup(lp)
+            dt, _ = oracle_sample(model, p, eta, 4096, alg)
+            t_cpu += dt
             it_cpu += 4096
         cpu = {"value": it_cpu / t_cpu, "unit": "iters/s", "cores": 1, "kind": "oracle",
-               "sample": f"4096 phase-1 PDHG iterations with restart checks on each of 16 LPs of the batch "
-                         f"spread over its size range ({t_cpu:.1f} s; setup not counted); numpy/scipy, "
-                         f"single-threaded"}
+               "nproc": os.cpu_count(),
+               "sample": f"4096 phase-1 PDHG iterations of the {alg} loop with restart checks on each of 16 LPs "
+                         f"of the batch spread over its size range ({t_cpu:.1f} s; setup not counted); "
+                         f"numpy/scipy, single-threaded"}
     if rank == 0:
         done = sum(r["status_name"] == "OPTIMAL" for r in r1)
         cdone = sum(r["status_name"] == "CORNER_DONE" for r in rc)
@@ -622,7 +636,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32+f32x2acc", "data": "synthetic",
-            "config": {"workload": "batch_512", "lps": len(all_lps), "lps_per_rank": len(lps),
+            "config": {"workload": "batch_512", "algorithm": alg, "lps": len(all_lps), "lps_per_rank": len(lps),
                        "sum_m": sum(lp["m"] for lp in all_lps), "sum_n": sum(lp["n"] for lp in all_lps),
                        "sum_nnz": sum(int(lp["row_ptr"][-1]) for lp in all_lps), "precision": "fp32_bulk",
                        "schedule": tuned, "corner_max_iters": args.corner_max_iters, "eps_rel": 1e-6,
@@ -635,6 +649,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "iters_max": max(r["iters"] for r in r1),
                        "corner_measure_sum": sum(r["corner_measure"] for r in r1)},
             "corner": {"done": cdone, "lps": len(rc), "iters_sum": sum(r["iters"] for r in rc),
+                       "iters_max": max(r["iters"] for r in rc),
                        "corner_measure_sum": sum(r["corner_measure"] for r in rc)},
             "sequential_fp64": seq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

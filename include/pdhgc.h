@@ -102,7 +102,7 @@ typedef struct pdhgc_params {
     int32_t ruiz_iters;    /* Ruiz infinity-norm passes (10, 0..100) */
     int32_t power_iters;   /* power iterations for sigma_max (100, 1..10000) */
     int32_t precision;     /* PDHGC_FP64 or PDHGC_FP32_BULK */
-    int32_t algorithm;     /* PDHGC_ALG_AVERAGED (default) or PDHGC_ALG_HALPERN (FP64 only) */
+    int32_t algorithm;     /* PDHGC_ALG_AVERAGED (default) or PDHGC_ALG_HALPERN (FP64 or FP32 bulk) */
     /* the Halpern loop only: */
     double  reflection;    /* rho in [0, 1]; 1 (default): the reflected operator 2T - I */
     double  pid_kp, pid_ki, pid_kd; /* primal-weight PID gains in log space (0.99, 0.01, 0):
@@ -346,14 +346,31 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
  * weight, restarts and termination, then the report); an LP's x_bar and y
  * live in the CTA's shared memory.  `reports` (count entries, may be NULL)
  * receives one report per LP in the caller's order; `seconds` is that LP's
- * device time.  Both precisions are supported; the inner loop is the
- * averaged one (INVALID_ARG for PDHGC_ALG_HALPERN, here and in the tuner).
+ * device time.  Both precisions and both inner loops are supported.
+ * Errors: INVALID_ARG (a parameter out of range), CUDA, OOM, and those of
+ * the single-LP path for a handed-off LP.
  */
 int pdhgc_batch_solve(pdhgc_batch* batch, const pdhgc_params* params, pdhgc_report* reports);
 
 /* pdhgc_batch_corner_phase — Algorithm 1 for every LP (as pdhgc_corner_phase;
  * omega_rule 0 only, INVALID_ARG otherwise). */
 int pdhgc_batch_corner_phase(pdhgc_batch* batch, const pdhgc_corner_params* params, pdhgc_report* reports);
+
+/*
+ * pdhgc_batch_solve_corner — phase 1 and Algorithm 1 (Section 3, with the
+ * Section 3.1 stopping rule) for every LP in ONE persistent launch: the CTA
+ * that finishes an LP's phase 1 goes straight on to that LP's corner phase,
+ * so no batch-wide barrier separates the two phases (the results and reports
+ * are those of pdhgc_batch_solve followed by pdhgc_batch_corner_phase with
+ * the same parameters).  reports1 / reports_c (count entries each, either
+ * may be NULL) receive the phase-1 and corner reports in the caller's order.
+ * An LP handed off in phase 1 runs both phases on the single-LP path; one
+ * handed off in its corner phase runs phase 1 and the corner phase there and
+ * keeps the corner result.  Errors: as pdhgc_batch_solve and
+ * pdhgc_batch_corner_phase.
+ */
+int pdhgc_batch_solve_corner(pdhgc_batch* batch, const pdhgc_params* params, const pdhgc_corner_params* cparams,
+                             pdhgc_report* reports1, pdhgc_report* reports_c);
 
 /* pdhgc_batch_get_solution — x (n) and y (m) of LP `lp`, user order, host pointers (either may be NULL). */
 int pdhgc_batch_get_solution(pdhgc_batch* batch, int32_t lp, int which, double* x, double* y);

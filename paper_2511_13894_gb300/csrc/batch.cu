@@ -27,696 +27,13 @@
 
 #include "../../include/pdhgc.h"
 #include "batch.h"
+#include "batch_desc.h"
 #include "host_prep.h"
-#include "kernels.cuh"
 #include "kkt_eval.h"
 
 namespace pdhgc {
 
-// ---------------------------------------------------------------------------
-// Per-LP device view (all pointers are device addresses of this LP's slices
-// of the batch's packed arrays; internal row / column order)
-// ---------------------------------------------------------------------------
-struct LpDesc {
-  int m, n, nnz;
-  int gA, gT;         // lanes per row of the A and A' passes in the CSR layout (autotuned)
-  int sell;           // 1: passes read the SELL-32 copies; 0: CSR rows with gA / gT lanes
-  int smem;           // 1: x_bar and y live in shared memory
-  double b_norm, c_norm;
-  const int *A_rp, *A_col, *T_rp, *T_col;
-  const double *A_val, *T_val;
-  double *A_hat, *T_hat;
-  float *A_hat32, *T_hat32;
-  // SELL-32 copies of the rows with <= kSellMaxLen nonzeros (rows [long, rows))
-  int A_long, A_ns, A_slots, T_long, T_ns, T_slots;
-  const int *A_sptr, *A_sw, *A_scol, *A_smap, *T_sptr, *T_sw, *T_scol, *T_smap;
-  const double *A_sval, *T_sval;
-  double *A_shat, *T_shat;
-  float *A_shat32, *T_shat32;
-  const double *b_int, *c, *l, *u;
-  const int8_t* ge;
-  int8_t* ge_c;
-  double *Dr, *Dc, *rfac, *cfac, *bhat, *chat, *lhat, *uhat;
-  double *chat_c, *lhat_c, *uhat_c;
-  float *bhat32, *chat32, *lhat32, *uhat32, *chat_c32, *lhat_c32, *uhat_c32;
-  double *x, *xbar, *sum_x, *x_r, *y, *sum_y, *y_r;  // FP64 iterates (x_bar, y: global fallback)
-  float *x32, *xbar32, *y32;                          // FP32 iterates (global fallback)
-  float *x32lo, *y32lo;                               // low parts of the float-float FP32 iterates
-  float2 *sx32, *sy32;                                // float-float FP32 running sums
-  double *x1, *y1, *xc;
-  double *pi_v, *pi_w, *pi_u;
-  double* keep;  // eta, sigma_max, ||b_hat||, ||c_hat|| from phase 1 (read by the corner phase)
-  const int *row_perm, *col_perm;
-};
-
 namespace {
-
-// ---- CTA-level building blocks --------------------------------------------
-
-// one pass over the rows of a CSR: G lanes per row, rows round-robin over the
-// CTA's groups; gathers by plain loads (shared or global memory)
-template <int BT, class Op>
-__device__ void cta_rows(const int* __restrict__ rp, const int* __restrict__ col,
-                         const typename Op::VT* __restrict__ val, int rows, int G, const Op& op, double* part) {
-  using PF = Prefetcher<Op>;
-  using GT = typename Op::GT;
-  constexpr int NG = Op::NG;
-  const int tid = threadIdx.x;
-  const int lane = tid & (G - 1);
-  const int gid = tid / G;
-  const int ngroups = BT / G;
-  for (int r0 = 0; r0 < rows; r0 += ngroups) {
-    const int r = r0 + gid;
-    const bool has = r < rows;
-    typename Op::Acc acc;
-    acc.zero();
-    typename PF::Pre pre{};
-    if (has) {
-      if (lane == 0) pre = PF::get(op, r);
-      const double rc = op.row_ctx(r);
-      const int e0 = rp[r], e1 = rp[r + 1];
-      for (int e = e0 + lane; e < e1; e += G) {
-        const int cc = col[e];
-        GV<GT, NG> g;
-#pragma unroll
-        for (int i = 0; i < NG; ++i) g.v[i] = op.gsrc(i)[cc];
-        op.accum(acc, rc, val[e], g);
-      }
-    }
-    for (int off = G >> 1; off > 0; off >>= 1) acc.add(acc.shfl_xor(0xffffffffu, off));
-    if (has && lane == 0) PF::epilogue(op, r, acc, pre, part);
-  }
-}
-
-// one matrix of an LP as a pass reads it: CSR for the long rows, SELL-32
-// slices for the rest
-template <class VT>
-struct BMat {
-  const int* rp;
-  const int* col;
-  const VT* val;
-  int rows, long_rows, nslices;
-  const int* sptr;
-  const int* sw;
-  const int* scol;
-  const VT* sval;
-};
-
-// one pass: long rows with a warp each (CSR), then SELL-32 slices with a lane
-// per row and kBatch coalesced loads in flight, slices round-robin over warps
-template <int BT, class Op>
-__device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* part) {
-  using PF = Prefetcher<Op>;
-  using VT = typename Op::VT;
-  using GT = typename Op::GT;
-  constexpr int NG = Op::NG;
-  constexpr int W = BT / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (M.long_rows > 0) cta_rows<BT>(M.rp, M.col, M.val, M.long_rows, 32, op, part);
-  for (int s = warp; s < M.nslices; s += W) {
-    const int base = M.sptr[s], w = M.sw[s];
-    const int r = M.long_rows + s * kSellH + lane;
-    const bool has = r < M.rows;
-    const int len = has ? M.rp[r + 1] - M.rp[r] : 0;
-    typename PF::Pre pre{};
-    if (has) pre = PF::get(op, r);
-    const double rc = has ? op.row_ctx(r) : 0.0;
-    typename Op::Acc acc;
-    acc.zero();
-    for (int j = 0; j < w; j += kBatch) {
-      VT v[kBatch];
-      int c[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        if (j + u < len) {
-          v[u] = ld_stream(M.sval + base + (j + u) * kSellH + lane);
-          c[u] = ld_stream(M.scol + base + (j + u) * kSellH + lane);
-        }
-      GV<GT, NG> g[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        if (j + u < len)
-#pragma unroll
-          for (int i = 0; i < NG; ++i) g[u].v[i] = op.gsrc(i)[c[u]];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        if (j + u < len) op.accum(acc, rc, v[u], g[u]);
-    }
-    if (has) PF::epilogue(op, r, acc, pre, part);
-  }
-}
-
-// deterministic CTA fold of part[0..nq) (sum, or max where mask bit set) into out[]
-template <int BT>
-__device__ void cta_fold(const double* part, int nq, unsigned max_mask, double* out, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int W = BT / 32;
-  for (int q = 0; q < nq; ++q) {
-    const bool is_max = (max_mask >> q) & 1u;
-    double v = part[q];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double o = __shfl_xor_sync(0xffffffffu, v, off);
-      v = is_max ? fmax(v, o) : v + o;
-    }
-    if (lane == 0) red[q * W + warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nq) {
-    const int q = threadIdx.x;
-    const bool is_max = (max_mask >> q) & 1u;
-    double v = red[q * W];
-    for (int w = 1; w < W; ++w) v = is_max ? fmax(v, red[q * W + w]) : v + red[q * W + w];
-    out[q] = v;
-  }
-  __syncthreads();
-}
-
-template <int BT>
-__device__ double cta_sum(double v, double* red) {
-  double part[1] = {v};
-  double out[1];
-  __shared__ double s_out[1];
-  cta_fold<BT>(part, 1, 0u, s_out, red);
-  out[0] = s_out[0];
-  __syncthreads();
-  return out[0];
-}
-
-struct BatchParams {
-  double eps_rel, beta_suff, beta_nec, beta_art, theta, eta_factor, time_limit_s;
-  long long max_iters;
-  int check_period, ruiz_iters, power_iters;
-  // corner
-  double eps_abs, c_eps_rel, obj_scale, c_time_limit_s;
-  long long c_min_iters, c_max_iters;
-  unsigned long long obj_seed;
-  int stop_rule;
-  int row_rule;
-  // tail handoff: once the queue is empty and at most handoff_running LPs are
-  // still running, an LP past handoff_min_iters iterations of its phase stops
-  // at its next check and is finished on the single-LP path (0: never)
-  int handoff_running;
-  long long handoff_min_iters;
-};
-
-// BatchReport.status of an LP handed to the single-LP path
-constexpr int kStatusHandoff = 100;
-
-// ---- one LP, one CTA ------------------------------------------------------
-
-template <class VT, int BT>
-struct LpSolver {
-  static constexpr bool kF32 = std::is_same<VT, float>::value;
-  const LpDesc& d;
-  const BatchParams& bp;
-  Scalars* S;
-  double* red;  // [32 * BT / 32] reduction scratch
-  double* q;    // [32] folded quantities
-  VT* s_y;      // gathered y (shared or global)
-  VT* s_xbar;   // gathered x_bar (shared or global)
-  const int* queue;  // [0] next LP of the queue, [1] LPs running
-  int count;
-
-  __device__ void fill(double* a, int n, double v) const {
-    for (int i = threadIdx.x; i < n; i += BT) a[i] = v;
-  }
-  // one pass over A (or A') in the layout the tuner chose
-  template <class Op>
-  __device__ void passA(const BMat<typename Op::VT>& M, const Op& op, double* part) const {
-    if (d.sell) cta_pass<BT>(M, op, part);
-    else cta_rows<BT>(M.rp, M.col, M.val, M.rows, d.gA, op, part);
-  }
-  template <class Op>
-  __device__ void passT(const BMat<typename Op::VT>& M, const Op& op, double* part) const {
-    if (d.sell) cta_pass<BT>(M, op, part);
-    else cta_rows<BT>(M.rp, M.col, M.val, M.rows, d.gT, op, part);
-  }
-  // kind 0: original values, 1: scaled FP64
-  __device__ BMat<double> matA(int kind) const {
-    return BMat<double>{d.A_rp, d.A_col, kind ? d.A_hat : d.A_val, d.m, d.A_long, d.A_ns,
-                        d.A_sptr, d.A_sw, d.A_scol, kind ? d.A_shat : d.A_sval};
-  }
-  __device__ BMat<double> matT(int kind) const {
-    return BMat<double>{d.T_rp, d.T_col, kind ? d.T_hat : d.T_val, d.n, d.T_long, d.T_ns,
-                        d.T_sptr, d.T_sw, d.T_scol, kind ? d.T_shat : d.T_sval};
-  }
-  __device__ BMat<float> matA32() const {
-    return BMat<float>{d.A_rp, d.A_col, d.A_hat32, d.m, d.A_long, d.A_ns, d.A_sptr, d.A_sw, d.A_scol, d.A_shat32};
-  }
-  __device__ BMat<float> matT32() const {
-    return BMat<float>{d.T_rp, d.T_col, d.T_hat32, d.n, d.T_long, d.T_ns, d.T_sptr, d.T_sw, d.T_scol, d.T_shat32};
-  }
-
-  __device__ DevModel model(bool corner) const {
-    return corner ? DevModel{d.chat_c, d.lhat_c, d.uhat_c, d.bhat, d.Dr, d.Dc, d.ge_c}
-                  : DevModel{d.chat, d.lhat, d.uhat, d.bhat, d.Dr, d.Dc, d.ge};
-  }
-  __device__ DevModel32 model32(bool corner) const {
-    return corner ? DevModel32{d.chat_c32, d.lhat_c32, d.uhat_c32, d.bhat32, d.ge_c}
-                  : DevModel32{d.chat32, d.lhat32, d.uhat32, d.bhat32, d.ge};
-  }
-  // FP64 view of the current iterates for the evaluation operators
-  __device__ DevIter iter64() const {
-    double* y = kF32 ? d.y : (double*)s_y;
-    double* xbar = kF32 ? d.xbar : (double*)s_xbar;
-    return DevIter{d.x, y, xbar, d.sum_x, d.sum_y, d.x_r, d.y_r};
-  }
-
-  // a0: Ruiz + Pock-Chambolle, scaled copies, power iteration
-  __device__ void setup() {
-    const int m = d.m, n = d.n;
-    fill(d.Dr, m, 1.0);
-    fill(d.Dc, n, 1.0);
-    __syncthreads();
-    double part[1] = {0.0};
-    for (int pass = 0; pass < bp.ruiz_iters; ++pass) {
-      passA(matA(0), ScaleMaxOp<false>{d.Dr, d.Dc, d.rfac}, part);
-      passT(matT(0), ScaleMaxOp<true>{d.Dc, d.Dr, d.cfac}, part);
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += BT) d.Dr[i] *= d.rfac[i];
-      for (int j = threadIdx.x; j < n; j += BT) d.Dc[j] *= d.cfac[j];
-      __syncthreads();
-    }
-    passA(matA(0), ScaleSumOp<false>{d.Dr, d.Dc, d.rfac}, part);
-    passT(matT(0), ScaleSumOp<true>{d.Dc, d.Dr, d.cfac}, part);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += BT) d.Dr[i] *= d.rfac[i];
-    for (int j = threadIdx.x; j < n; j += BT) d.Dc[j] *= d.cfac[j];
-    __syncthreads();
-    // scaled matrix and vectors: (D_r a) D_c, D_r b, D_c c, l / D_c, u / D_c
-    for (int r = threadIdx.x; r < m; r += BT)
-      for (int e = d.A_rp[r]; e < d.A_rp[r + 1]; ++e) {
-        const double v = (d.Dr[r] * d.A_val[e]) * d.Dc[d.A_col[e]];
-        d.A_hat[e] = v;
-        if (kF32) d.A_hat32[e] = (float)v;
-      }
-    for (int j = threadIdx.x; j < n; j += BT)
-      for (int e = d.T_rp[j]; e < d.T_rp[j + 1]; ++e) {
-        const double v = (d.Dr[d.T_col[e]] * d.T_val[e]) * d.Dc[j];
-        d.T_hat[e] = v;
-        if (kF32) d.T_hat32[e] = (float)v;
-      }
-    __syncthreads();
-    for (int k = threadIdx.x; k < d.A_slots; k += BT) {
-      const int e = d.A_smap[k];
-      const double v = e >= 0 ? d.A_hat[e] : 0.0;
-      d.A_shat[k] = v;
-      if (kF32) d.A_shat32[k] = (float)v;
-    }
-    for (int k = threadIdx.x; k < d.T_slots; k += BT) {
-      const int e = d.T_smap[k];
-      const double v = e >= 0 ? d.T_hat[e] : 0.0;
-      d.T_shat[k] = v;
-      if (kF32) d.T_shat32[k] = (float)v;
-    }
-    double nb2 = 0.0, nc2 = 0.0;
-    for (int i = threadIdx.x; i < m; i += BT) {
-      const double bh = d.Dr[i] * d.b_int[i];
-      d.bhat[i] = bh;
-      nb2 += bh * bh;
-      if (kF32) d.bhat32[i] = (float)bh;
-    }
-    for (int j = threadIdx.x; j < n; j += BT) {
-      const double ch = d.Dc[j] * d.c[j];
-      d.chat[j] = ch;
-      d.lhat[j] = d.l[j] / d.Dc[j];
-      d.uhat[j] = d.u[j] / d.Dc[j];
-      nc2 += ch * ch;
-      if (kF32) {
-        d.chat32[j] = (float)ch;
-        d.lhat32[j] = (float)d.lhat[j];
-        d.uhat32[j] = (float)d.uhat[j];
-      }
-    }
-    nb2 = cta_sum<BT>(nb2, red);
-    nc2 = cta_sum<BT>(nc2, red);
-    // power iteration on A_hat' A_hat from v = 1/sqrt(n)
-    fill(d.pi_v, n, 1.0 / sqrt((double)n));
-    __syncthreads();
-    bool zero = false;
-    for (int k = 0; k < bp.power_iters && !zero; ++k) {
-      passA(matA(1), SpmvOp<false>{S, d.pi_v, d.pi_u}, part);
-      __syncthreads();
-      double pw[1] = {0.0};
-      passT(matT(1), SpmvOp<true>{S, d.pi_u, d.pi_w}, pw);
-      const double nw = sqrt(cta_sum<BT>(pw[0], red));
-      if (nw == 0.0) {
-        zero = true;
-        break;
-      }
-      for (int j = threadIdx.x; j < n; j += BT) d.pi_v[j] = d.pi_w[j] / nw;
-      __syncthreads();
-    }
-    double sigma_max = 0.0;
-    if (!zero) {
-      double pu[1] = {0.0};
-      passA(matA(1), SpmvOp<true>{S, d.pi_v, d.pi_u}, pu);
-      sigma_max = sqrt(cta_sum<BT>(pu[0], red));
-    }
-    if (threadIdx.x == 0) {
-      S->sigma_max = sigma_max;
-      S->eta = sigma_max > 0.0 ? bp.eta_factor / sigma_max : 1.0;
-      S->nb_hat = sqrt(nb2);
-      S->nc_hat = sqrt(nc2);
-      d.keep[0] = S->eta;
-      d.keep[1] = S->sigma_max;
-      d.keep[2] = S->nb_hat;
-      d.keep[3] = S->nc_hat;
-    }
-    __syncthreads();
-  }
-
-  // start of a phase (mirrors k_init_scalars / k_init_iterates)
-  __device__ void init_phase(int phase, const double* x_start, double nch, double nc_user) {
-    const int m = d.m, n = d.n;
-    const DevModel md = model(phase == 1);
-    for (int j = threadIdx.x; j < n; j += BT) {
-      const double x0 = x_start ? x_start[j] : fmin(fmax(0.0, md.lhat[j]), md.uhat[j]);
-      d.x[j] = x0;
-      d.x_r[j] = x0;
-      d.sum_x[j] = 0.0;
-      if (kF32) {
-        const float h = (float)x0;
-        d.x32[j] = h;
-        d.x32lo[j] = (float)(x0 - (double)h);
-        d.sx32[j] = make_float2(0.f, 0.f);
-        s_xbar[j] = (VT)h;
-      } else {
-        ((double*)s_xbar)[j] = x0;
-      }
-    }
-    for (int i = threadIdx.x; i < m; i += BT) {
-      s_y[i] = (VT)0;
-      if (kF32) {
-        d.y[i] = 0.0;
-        d.y32lo[i] = 0.0f;
-        d.sy32[i] = make_float2(0.f, 0.f);
-      }
-      d.y_r[i] = 0.0;
-      d.sum_y[i] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      S->eps_rel = phase ? bp.c_eps_rel : bp.eps_rel;
-      S->beta_suff = bp.beta_suff;
-      S->beta_nec = bp.beta_nec;
-      S->beta_art = bp.beta_art;
-      S->theta = bp.theta;
-      S->time_limit_s = phase ? bp.c_time_limit_s : bp.time_limit_s;
-      S->nb = d.b_norm;
-      S->nc = nc_user;
-      S->max_iters = phase ? bp.c_max_iters : bp.max_iters;
-      S->min_iters = phase ? bp.c_min_iters : 0;
-      S->check_period = bp.check_period;
-      S->phase = phase;
-      S->stop_rule = phase ? bp.stop_rule : 0;
-      S->omega = (nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0;
-      S->tau = S->eta / S->omega;
-      S->sigma = S->eta * S->omega;
-      S->k = 0;
-      S->t = 0;
-      S->restarts = 0;
-      S->chunks = 0;
-      S->max_chunks = S->max_iters / S->check_period + 2;
-      S->done = 0;
-      S->status = PDHGC_STATUS_NONE;
-      S->chosen = 0;
-      S->restart_to = 0;
-      S->inv_t = 0.0;
-      S->at_check = 0;
-      S->at_limit = 0;
-      S->kkt_prev = INFINITY;
-      S->t0_ns = global_ns();
-    }
-    __syncthreads();
-  }
-
-  // the 22 KKT quantities of the current and average points, folded
-  __device__ void evaluate(bool corner) {
-    const DevModel md = model(corner);
-    const DevIter w = iter64();
-    double pr[10];
-    for (int i = 0; i < 10; ++i) pr[i] = 0.0;
-    passA(matA(1), EvalRowsOp{S, w.x, w.sum_x, w.y, w.sum_y, w.y_r, md}, pr);
-    cta_fold<BT>(pr, 10, EvalRowsOp::kMaxMask, q, red);
-    double pc[12];
-    for (int i = 0; i < 12; ++i) pc[i] = 0.0;
-    passT(matT(1), EvalColsOp{S, w.y, w.sum_y, w.x, w.sum_x, w.x_r, md}, pc);
-    cta_fold<BT>(pc, 12, EvalColsOp::kMaxMask, q + 10, red);
-  }
-
-  __device__ void iterate(bool corner, int it) {
-    double part[1] = {0.0};
-    if constexpr (kF32) {
-      const DevModel32 md = model32(corner);
-      const DevIter32 w{d.x32, (float*)s_y, (float*)s_xbar, d.sx32, d.sy32, d.x32lo, d.y32lo};
-      passT(matT32(), PrimalOp32{S, it, (float*)s_y, md, w}, part);
-      __syncthreads();
-      passA(matA32(), DualOp32{S, it, (float*)s_xbar, md, w}, part);
-      __syncthreads();
-    } else {
-      const DevModel md = model(corner);
-      const DevIter w{d.x, (double*)s_y, (double*)s_xbar, d.sum_x, d.sum_y, d.x_r, d.y_r};
-      passT(matT(1), PrimalOp{S, it, (double*)s_y, md, w}, part);
-      __syncthreads();
-      passA(matA(1), DualOp{S, it, (double*)s_xbar, md, w}, part);
-      __syncthreads();
-    }
-  }
-
-  // the restarted loop of one phase (mirrors the graph body of run_phase)
-  __device__ void loop(bool corner) {
-    const int m = d.m, n = d.n;
-    const DevModel md = model(corner);
-    if (kF32) {
-      for (int i = threadIdx.x; i < m; i += BT) d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
-    }
-    __syncthreads();
-    evaluate(corner);
-    if (threadIdx.x == 0) decide_step(S, q, 0);
-    __syncthreads();
-    while (true) {
-      const long long k0 = S->k, kmax = S->max_iters;
-      const int P = S->check_period;
-      for (int i = 0; i < P && k0 + i < kmax; ++i) iterate(corner, i);
-      if (threadIdx.x == 0) {
-        long long run = kmax - k0;
-        if (run > P) run = P;
-        if (run < 0) run = 0;
-        S->k += run;
-        S->t += run;
-        S->inv_t = S->t > 0 ? 1.0 / (double)S->t : 0.0;
-        S->at_check = (S->k % P) == 0;
-        S->at_limit = S->k >= kmax;
-        S->chunks += 1;
-        if (S->chunks > S->max_chunks) S->at_limit = 1;
-      }
-      if (kF32) {
-        for (int j = threadIdx.x; j < n; j += BT) {
-          d.x[j] = fmin(fmax((double)d.x32[j] + (double)d.x32lo[j], md.lhat[j]), md.uhat[j]);
-          d.sum_x[j] = (double)d.sx32[j].x + (double)d.sx32[j].y;
-        }
-        for (int i = threadIdx.x; i < m; i += BT) {
-          d.y[i] = (double)((float*)s_y)[i] + (double)d.y32lo[i];
-          d.sum_y[i] = (double)d.sy32[i].x + (double)d.sy32[i].y;
-        }
-      }
-      __syncthreads();
-      evaluate(corner);
-      if (threadIdx.x == 0) {
-        decide_step(S, q, 1);
-        // tail handoff (reads of the queue counters, no wait)
-        if (!S->done && bp.handoff_running > 0 && S->k >= bp.handoff_min_iters &&
-            *(volatile const int*)&queue[0] >= count && *(volatile const int*)&queue[1] <= bp.handoff_running) {
-          S->done = 1;
-          S->status = kStatusHandoff;
-        }
-      }
-      __syncthreads();
-      if (S->done) break;
-      const int rt = S->restart_to;
-      if (rt != 0) {
-        const double inv_t = S->inv_t;
-        const DevIter w = iter64();
-        for (int j = threadIdx.x; j < n; j += BT) {
-          const double xn = rt == 2 ? w.sum_x[j] * inv_t : w.x[j];
-          w.x[j] = xn;
-          w.x_r[j] = xn;
-          w.sum_x[j] = 0.0;
-          if (kF32) {
-            d.sx32[j] = make_float2(0.f, 0.f);
-            if (rt == 2) {
-              const float h = (float)xn;
-              d.x32[j] = h;
-              d.x32lo[j] = (float)(xn - (double)h);
-            }
-          }
-        }
-        for (int i = threadIdx.x; i < m; i += BT) {
-          const double yn = rt == 2 ? w.sum_y[i] * inv_t : w.y[i];
-          w.y[i] = yn;
-          w.y_r[i] = yn;
-          w.sum_y[i] = 0.0;
-          if (kF32) {
-            d.sy32[i] = make_float2(0.f, 0.f);
-            if (rt == 2) {
-              const float h = (float)yn;
-              ((float*)s_y)[i] = h;
-              d.y32lo[i] = (float)(yn - (double)h);
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-
-  // the returned point (mirrors k_finalize)
-  __device__ void finalize(double* xo, double* yo, const double* x_fallback, bool corner) {
-    const DevModel md = model(corner);
-    const DevIter w = iter64();
-    const bool avg = S->chosen == 1 && S->t > 0;
-    const double inv_t = S->inv_t;
-    const bool fallback = x_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
-    for (int j = threadIdx.x; j < d.n; j += BT)
-      xo[j] = fallback ? x_fallback[j] : fmin(fmax(avg ? w.sum_x[j] * inv_t : w.x[j], md.lhat[j]), md.uhat[j]);
-    if (yo)
-      for (int i = threadIdx.x; i < d.m; i += BT) yo[i] = avg ? w.sum_y[i] * inv_t : w.y[i];
-    __syncthreads();
-  }
-
-  // KKT numbers and metrics of (x, y) on the original model (mirrors run_report)
-  __device__ void report(const double* x, const double* y, BatchReport* out) {
-    const DevModel md = model(false);
-    double pr[7];
-    for (int i = 0; i < 7; ++i) pr[i] = 0.0;
-    passA(matA(1), ReportRowsOp{x, y, md, 1e-6}, pr);
-    cta_fold<BT>(pr, 7, ReportRowsOp::kMaxMask, q, red);
-    double pc[8];
-    for (int i = 0; i < 8; ++i) pc[i] = 0.0;
-    passT(matT(1), ReportColsOp{y, x, d.l, d.u, md, 1e-6}, pc);
-    cta_fold<BT>(pc, 8, ReportColsOp::kMaxMask, q + 7, red);
-    if (threadIdx.x == 0) {
-      BatchReport r;
-      r.status = S->status;
-      r.chosen = S->chosen;
-      r.iters = S->k;
-      r.restarts = S->restarts;
-      r.rP2 = sqrt(q[1]);
-      r.rPinf = q[2];
-      r.rD2 = sqrt(q[8]);
-      r.rDinf = q[9];
-      r.pobj = q[10];
-      r.dobj = q[3] + q[11];
-      r.p = q[4] + q[12];
-      r.dd = q[5] + q[13];
-      r.cand = q[6] + q[14];
-      r.omega = S->omega;
-      r.eta = S->eta;
-      r.sigma_max = S->sigma_max;
-      r.seconds = (double)(global_ns() - S->t0_ns) * 1e-9;
-      *out = r;
-    }
-    __syncthreads();
-  }
-
-  __device__ bool handed_off(BatchReport* out) {
-    if (S->status != kStatusHandoff) return false;
-    if (threadIdx.x == 0) {
-      BatchReport r{};
-      r.status = kStatusHandoff;
-      r.iters = S->k;
-      *out = r;
-    }
-    __syncthreads();
-    return true;
-  }
-
-  __device__ void phase1(BatchReport* out) {
-    setup();
-    init_phase(0, nullptr, S->nc_hat, d.c_norm);
-    loop(false);
-    if (handed_off(out)) return;
-    finalize(d.x1, d.y1, nullptr, false);
-    report(d.x1, d.y1, out);
-  }
-
-  // Algorithm 1 (mirrors pdhgc_corner_phase)
-  __device__ void corner(BatchReport* out) {
-    if (threadIdx.x == 0) {
-      S->eta = d.keep[0];
-      S->sigma_max = d.keep[1];
-      S->nb_hat = d.keep[2];
-      S->nc_hat = d.keep[3];
-    }
-    __syncthreads();
-    double pc[2] = {0.0, 0.0};
-    passT(matT(1),
-                 CornerColsOp{d.y1, d.x1, d.col_perm, model(false), d.lhat_c, d.uhat_c, d.chat_c, bp.eps_abs,
-                              bp.obj_scale, bp.obj_seed},
-                 pc);
-    cta_fold<BT>(pc, 2, 0u, q, red);
-    const double cc2 = q[0], cu2 = q[1];
-    if (bp.row_rule == 1) {  // the option: A_hat x1 for the row slacks
-      if (threadIdx.x == 0) S->pi_zero = 0;
-      fill(d.pi_u, d.m, 0.0);
-      __syncthreads();
-      double pu[1] = {0.0};
-      passA(matA(1), SpmvOp<false>{S, d.x1, d.pi_u}, pu);
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < d.m; i += BT) {
-      const double yu = fabs(d.Dr[i] * d.y1[i]);
-      bool to_eq = d.ge[i] && yu > bp.eps_abs;
-      if (to_eq && bp.row_rule == 1) to_eq = d.pi_u[i] / d.Dr[i] - d.b_int[i] <= yu;
-      d.ge_c[i] = (d.ge[i] && !to_eq) ? 1 : 0;
-    }
-    if (kF32)
-      for (int j = threadIdx.x; j < d.n; j += BT) {
-        d.chat_c32[j] = (float)d.chat_c[j];
-        d.lhat_c32[j] = (float)d.lhat_c[j];
-        d.uhat_c32[j] = (float)d.uhat_c[j];
-      }
-    __syncthreads();
-    init_phase(1, d.x1, sqrt(cc2), sqrt(cu2));
-    loop(true);
-    if (handed_off(out)) return;
-    finalize(d.xc, nullptr, d.x1, true);
-    report(d.xc, d.y1, out);
-  }
-};
-
-template <class VT, int BT>
-__global__ void __launch_bounds__(BT) k_batch(const LpDesc* __restrict__ descs, const int* __restrict__ order,
-                                              int count, int* queue, BatchParams bp, int phase,
-                                              BatchReport* reps) {
-  extern __shared__ __align__(16) unsigned char s_vec[];
-  __shared__ Scalars S;
-  __shared__ double red[32 * (BT / 32)];
-  __shared__ double q[32];
-  __shared__ int job;
-  while (true) {
-    if (threadIdx.x == 0) {
-      job = atomicAdd(&queue[0], 1);
-      if (job < count) atomicAdd(&queue[1], 1);
-    }
-    __syncthreads();
-    const int jj = job;
-    __syncthreads();
-    if (jj >= count) break;
-    const int lp = order[jj];
-    const LpDesc& d = descs[lp];
-    VT* sy = d.smem ? reinterpret_cast<VT*>(s_vec) : (std::is_same<VT, float>::value ? (VT*)d.y32 : (VT*)d.y);
-    VT* sxb = d.smem ? reinterpret_cast<VT*>(s_vec) + d.m
-                     : (std::is_same<VT, float>::value ? (VT*)d.xbar32 : (VT*)d.xbar);
-    LpSolver<VT, BT> sol{d, bp, &S, red, q, sy, sxb, queue, count};
-    if (phase == 0)
-      sol.phase1(&reps[lp]);
-    else
-      sol.corner(&reps[lp]);
-    if (threadIdx.x == 0) atomicSub(&queue[1], 1);
-  }
-}
 
 template <class T>
 int dalloc(std::vector<void*>& allocs, T** p, size_t count) {
@@ -747,6 +64,7 @@ struct pdhgc_batch {
   int* d_order = nullptr;
   int* d_queue = nullptr;
   BatchReport* d_rep = nullptr;
+  BatchReport* d_rep2 = nullptr;  // corner reports of the fused call (pdhgc_batch_solve_corner)
   std::vector<BatchReport> h_rep1, h_repc;
   size_t smem_f32 = 0, smem_f64 = 0;
   int block = 1024;
@@ -817,6 +135,11 @@ BatchParams make_params(const pdhgc_params& p, const pdhgc_corner_params* cp) {
   b.check_period = p.check_period;
   b.ruiz_iters = p.ruiz_iters;
   b.power_iters = p.power_iters;
+  b.algorithm = p.algorithm;
+  b.rho = p.reflection;
+  b.pid_kp = p.pid_kp;
+  b.pid_ki = p.pid_ki;
+  b.pid_kd = p.pid_kd;
   if (cp) {
     b.eps_abs = cp->eps_abs;
     b.c_eps_rel = cp->eps_rel;
@@ -834,11 +157,10 @@ BatchParams make_params(const pdhgc_params& p, const pdhgc_corner_params* cp) {
 template <class VT, int BT>
 int launch_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t st) {
   const size_t smem = std::is_same<VT, float>::value ? B->smem_f32 : B->smem_f64;
-  BCK(cudaFuncSetAttribute(k_batch<VT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, per_sm = 0;
+  BCK((batch_kernel_prepare<VT, BT>(smem, &per_sm)));
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<VT, BT>, BT, smem));
   if (per_sm < 1) return set_berr(PDHGC_ERR_CUDA, "batched kernel does not fit on an SM");
   int grid = sms * per_sm;
   if (grid > B->count) grid = B->count;
@@ -847,9 +169,8 @@ int launch_batch(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t 
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
   const cudaError_t me = cudaMemsetAsync(B->d_queue, 0, 2 * sizeof(int), B->cap_stream);
-  k_batch<VT, BT><<<grid, BT, smem, B->cap_stream>>>(B->d_desc, B->d_order, B->count, B->d_queue, bp, phase,
-                                                     B->d_rep);
-  const cudaError_t le = cudaGetLastError();
+  const cudaError_t le = batch_kernel_launch<VT, BT>(grid, smem, B->cap_stream, B->d_desc, B->d_order, B->count,
+                                                      B->d_queue, bp, phase, B->d_rep, B->d_rep2);
   const cudaError_t ce = cudaStreamEndCapture(B->cap_stream, &graph);
   if (me != cudaSuccess || le != cudaSuccess || ce != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -906,10 +227,11 @@ void to_report(const BatchReport& r, int64_t m, double nb, double nc, int precis
 }
 
 // One handed-off LP on the single-LP path (its own stream and handle, run
-// from a host thread so that several run concurrently): phase 1, and for
-// phase 1 the corner phase too (from that handle's own phase-1 result); the
-// result goes back into the batch's scaled internal buffers.
-int finish_on_single_path(pdhgc_batch* B, int k, int phase, const pdhgc_params& p, const pdhgc_corner_params* cp,
+// from a host thread so that several run concurrently).  mode 0: phase 1;
+// 1: the corner phase (phase 1 runs first on that handle, and the corner
+// phase starts from that handle's own phase-1 result); 2: both, each result
+// kept.  The results go back into the batch's scaled internal buffers.
+int finish_on_single_path(pdhgc_batch* B, int k, int mode, const pdhgc_params& p, const pdhgc_corner_params* cp,
                           std::string& err, int64_t& launches) {
   BCK(cudaSetDevice(B->device));
   cudaStream_t st = nullptr;
@@ -920,10 +242,11 @@ int finish_on_single_path(pdhgc_batch* B, int k, int phase, const pdhgc_params& 
                            h.b.data(), h.c.data(), h.lb.empty() ? nullptr : h.lb.data(),
                            h.ub.empty() ? nullptr : h.ub.data(), h.sense.empty() ? nullptr : h.sense.data(), 0, st);
   pdhgc_report r1{}, rc_rep{};
+  std::vector<double> x1(h.n), y1(h.m), xc(h.n), yc(h.m);
   if (rc == PDHGC_OK) rc = pdhgc_solve(lp, &p, &r1);
-  if (rc == PDHGC_OK && phase == 1) rc = pdhgc_corner_phase(lp, cp, &rc_rep);
-  std::vector<double> x(h.n), y(h.m);
-  if (rc == PDHGC_OK) rc = pdhgc_get_solution(lp, phase ? PDHGC_CORNER : PDHGC_PHASE1, x.data(), y.data(), nullptr, 0);
+  if (rc == PDHGC_OK && mode != 1) rc = pdhgc_get_solution(lp, PDHGC_PHASE1, x1.data(), y1.data(), nullptr, 0);
+  if (rc == PDHGC_OK && mode != 0) rc = pdhgc_corner_phase(lp, cp, &rc_rep);
+  if (rc == PDHGC_OK && mode != 0) rc = pdhgc_get_solution(lp, PDHGC_CORNER, xc.data(), yc.data(), nullptr, 0);
   if (rc != PDHGC_OK) err = std::string("handoff of LP ") + std::to_string(k) + ": " + pdhgc_last_error_detail();
   if (lp) {
     launches = pdhgc_kernel_launches(lp);
@@ -931,39 +254,59 @@ int finish_on_single_path(pdhgc_batch* B, int k, int phase, const pdhgc_params& 
   }
   if (rc == PDHGC_OK) {
     const LpDesc& d = B->h_desc[k];
-    std::vector<double> Dc(d.n), Dr(d.m), xh(d.n), yh(d.m);
+    std::vector<double> Dc(d.n), Dr(d.m), x1h(d.n), y1h(d.m), xch(d.n);
     cudaError_t e = cudaMemcpyAsync(Dc.data(), d.Dc, (size_t)d.n * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Dr.data(), d.Dr, (size_t)d.m * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-      for (int j = 0; j < d.n; ++j) xh[j] = x[B->col_perm[k][j]] / Dc[j];
-      for (int i = 0; i < d.m; ++i) yh[i] = B->sign[k][i] * y[B->row_perm[k][i]] / Dr[i];
-      e = cudaMemcpyAsync(phase ? d.xc : d.x1, xh.data(), (size_t)d.n * 8, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess && phase == 0)
-        e = cudaMemcpyAsync(d.y1, yh.data(), (size_t)d.m * 8, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && mode != 1) {
+      for (int j = 0; j < d.n; ++j) x1h[j] = x1[B->col_perm[k][j]] / Dc[j];
+      for (int i = 0; i < d.m; ++i) y1h[i] = B->sign[k][i] * y1[B->row_perm[k][i]] / Dr[i];
+      e = cudaMemcpyAsync(d.x1, x1h.data(), (size_t)d.n * 8, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d.y1, y1h.data(), (size_t)d.m * 8, cudaMemcpyHostToDevice, st);
     }
+    if (e == cudaSuccess && mode != 0) {
+      for (int j = 0; j < d.n; ++j) xch[j] = xc[B->col_perm[k][j]] / Dc[j];
+      e = cudaMemcpyAsync(d.xc, xch.data(), (size_t)d.n * 8, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       rc = PDHGC_ERR_CUDA;
       err = std::string("handoff copy-back: ") + cudaGetErrorString(e);
-    } else if (phase == 0) {
-      B->ext_rep1[k] = r1;
-      B->ext1[k] = 1;
     } else {
-      B->ext_repc[k] = rc_rep;
-      B->extc[k] = 1;
+      if (mode != 1) {
+        B->ext_rep1[k] = r1;
+        B->ext1[k] = 1;
+      }
+      if (mode != 0) {
+        B->ext_repc[k] = rc_rep;
+        B->extc[k] = 1;
+      }
     }
   }
   cudaStreamDestroy(st);
   return rc;
 }
 
-// the LPs a batched phase handed off, finished concurrently
+// the LPs a batched phase handed off, finished concurrently.  phase 0 or 1:
+// that phase's handoffs; 2 (the fused call): an LP handed off in phase 1
+// runs both phases on the single-LP path, one handed off in its corner phase
+// runs the corner phase there (mode 1)
 int run_handoffs(pdhgc_batch* B, int phase, const pdhgc_params& p, const pdhgc_corner_params* cp) {
-  const std::vector<BatchReport>& reps = phase ? B->h_repc : B->h_rep1;
-  std::vector<int> ks;
-  for (int k = 0; k < B->count; ++k)
-    if (reps[k].status == kStatusHandoff) ks.push_back(k);
+  std::vector<int> ks, modes;
+  for (int k = 0; k < B->count; ++k) {
+    if (phase == 2) {
+      if (B->h_rep1[k].status == kStatusHandoff) {
+        ks.push_back(k);
+        modes.push_back(2);
+      } else if (B->h_repc[k].status == kStatusHandoff) {
+        ks.push_back(k);
+        modes.push_back(1);
+      }
+    } else if ((phase ? B->h_repc : B->h_rep1)[k].status == kStatusHandoff) {
+      ks.push_back(k);
+      modes.push_back(phase);
+    }
+  }
   if (ks.empty()) return PDHGC_OK;
   // each worker writes only its LP's slots (result buffers, report, flag)
   std::vector<int> rcs(ks.size(), PDHGC_OK);
@@ -974,12 +317,14 @@ int run_handoffs(pdhgc_batch* B, int phase, const pdhgc_params& p, const pdhgc_c
   try {
     for (; started < ks.size(); ++started)
       th.emplace_back([&, started] {
-        rcs[started] = finish_on_single_path(B, ks[started], phase, p, cp, errs[started], lcount[started]);
+        rcs[started] = finish_on_single_path(B, ks[started], modes[started], p, cp, errs[started],
+                                             lcount[started]);
       });
   } catch (...) {
     // no more threads: finish the rest on this one
   }
-  for (size_t i = started; i < ks.size(); ++i) rcs[i] = finish_on_single_path(B, ks[i], phase, p, cp, errs[i], lcount[i]);
+  for (size_t i = started; i < ks.size(); ++i)
+    rcs[i] = finish_on_single_path(B, ks[i], modes[i], p, cp, errs[i], lcount[i]);
   for (auto& t : th) t.join();
   for (size_t i = 0; i < ks.size(); ++i) B->launches += lcount[i];
   for (size_t i = 0; i < ks.size(); ++i)
@@ -1079,10 +424,19 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   BAL(uhat_c32, N); BAL(x32, N); BAL(xbar32, N); BAL(y32, M); BAL(x32lo, N); BAL(y32lo, M);
   BAL(sx32, N); BAL(sy32, M);
   BAL(ge, M); BAL(ge_c, M);
+  double *hxp, *hyp, *hdx, *hdy, *hw;
+  float* hs;
+  float2 *xa32, *ya32;
+  BAL(hxp, N); BAL(hyp, M); BAL(hdx, N); BAL(hdy, M); BAL(xa32, N); BAL(ya32, M);
+  BAL(hw, 4096 * K); BAL(hs, 4096 * K);
+  float* yh32;
+  float2 *q32, *r032;
+  BAL(yh32, M); BAL(q32, N); BAL(r032, M);
   BAL(B->d_desc, K);
   BAL(B->d_order, K);
   BAL(B->d_queue, 2);
   BAL(B->d_rep, K);
+  BAL(B->d_rep2, K);
 #undef BAL
   cudaStream_t st = B->stream;
   B->h_desc.resize(count);
@@ -1139,6 +493,11 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
     d.x1 = x1 + on; d.y1 = y1 + om; d.xc = xc + on;
     d.pi_v = pi_v + on; d.pi_w = pi_w + on; d.pi_u = pi_u + om;
     d.keep = keep + 4 * (size_t)k;
+    d.hxp = hxp + on; d.hdx = hdx + on; d.hyp = hyp + om; d.hdy = hdy + om;
+    d.xa32 = xa32 + on; d.ya32 = ya32 + om;
+    d.yh32 = yh32 + om; d.q32 = q32 + on; d.r032 = r032 + om;
+    d.hw = hw + 4096 * (size_t)k;
+    d.hs = hs + 4096 * (size_t)k;
     d.row_perm = rperm + om;
     d.col_perm = cperm + on;
     // SELL-32 copies (indices and original values filled here from the slot map)
@@ -1227,16 +586,56 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   return PDHGC_OK;
 }
 
-int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* reports) {
-  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
-  pdhgc_params p;
-  if (params) p = *params; else pdhgc_default_params(&p);
+}  // extern "C"
+
+namespace {
+
+int check_batch_params(const pdhgc_params& p) {
   if (p.max_iters < 1 || p.check_period < 1 || p.check_period > 4096 || p.ruiz_iters < 0 || p.power_iters < 1 ||
       !(p.eta_factor > 0.0 && p.eta_factor < 1.0) || !(p.time_limit_s > 0.0) ||
       (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK))
     return set_berr(PDHGC_ERR_INVALID_ARG, "parameter out of range");
-  if (p.algorithm != PDHGC_ALG_AVERAGED)
-    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched solver runs the averaged loop only");
+  if (p.algorithm != PDHGC_ALG_AVERAGED && p.algorithm != PDHGC_ALG_HALPERN)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "algorithm must be PDHGC_ALG_AVERAGED or PDHGC_ALG_HALPERN");
+  if (p.algorithm == PDHGC_ALG_HALPERN &&
+      (!(p.reflection >= 0.0 && p.reflection <= 1.0) || !std::isfinite(p.pid_kp) || !std::isfinite(p.pid_ki) ||
+       !std::isfinite(p.pid_kd)))
+    return set_berr(PDHGC_ERR_INVALID_ARG, "reflection must lie in [0, 1] and the PID gains be finite");
+  return PDHGC_OK;
+}
+
+int check_batch_corner_params(const pdhgc_corner_params& cp) {
+  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
+      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
+      (cp.row_rule != 0 && cp.row_rule != 1))
+    return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
+  if (cp.omega_rule != 0)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched corner phase starts omega from the corner objective only");
+  return PDHGC_OK;
+}
+
+void fill_reports(pdhgc_batch* B, int which, pdhgc_report* reports) {
+  if (!reports) return;
+  const std::vector<BatchReport>& h = which ? B->h_repc : B->h_rep1;
+  const std::vector<char>& ext = which ? B->extc : B->ext1;
+  const std::vector<pdhgc_report>& er = which ? B->ext_repc : B->ext_rep1;
+  for (int k = 0; k < B->count; ++k) {
+    if (ext[k])
+      reports[k] = er[k];
+    else
+      to_report(h[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, B->precision, &reports[k]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* reports) {
+  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
+  pdhgc_params p;
+  if (params) p = *params; else pdhgc_default_params(&p);
+  RET(check_batch_params(p));
   B->params = p;
   B->precision = p.precision;
   B->have_phase1 = 0;
@@ -1251,13 +650,7 @@ int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* 
   BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
   RET(run_handoffs(B, 0, p, nullptr));
-  for (int k = 0; k < B->count; ++k)
-    if (reports) {
-      if (B->ext1[k])
-        reports[k] = B->ext_rep1[k];
-      else
-        to_report(B->h_rep1[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, p.precision, &reports[k]);
-    }
+  fill_reports(B, 0, reports);
   B->have_phase1 = 1;
   return PDHGC_OK;
 }
@@ -1267,12 +660,7 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
   if (!B->have_phase1) return set_berr(PDHGC_ERR_NO_PHASE1, "pdhgc_batch_solve has not run");
   pdhgc_corner_params cp;
   if (params) cp = *params; else pdhgc_default_corner_params(&cp);
-  if (!(cp.eps_abs >= 0.0) || cp.min_iters < 0 || cp.max_iters < 1 || !(cp.time_limit_s > 0.0) ||
-      !std::isfinite(cp.obj_scale) || (cp.stop_rule != 0 && cp.stop_rule != 1) ||
-      (cp.row_rule != 0 && cp.row_rule != 1))
-    return set_berr(PDHGC_ERR_INVALID_ARG, "corner parameter out of range");
-  if (cp.omega_rule != 0)
-    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched corner phase starts omega from the corner objective only");
+  RET(check_batch_corner_params(cp));
   cudaStream_t st = B->stream;
   std::fill(B->extc.begin(), B->extc.end(), 0);
   BatchParams bp = make_params(B->params, &cp);
@@ -1282,14 +670,38 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
   BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
   RET(run_handoffs(B, 1, B->params, &cp));
-  for (int k = 0; k < B->count; ++k)
-    if (reports) {
-      if (B->extc[k])
-        reports[k] = B->ext_repc[k];
-      else
-        to_report(B->h_repc[k], B->h_desc[k].m, B->h_desc[k].b_norm, B->h_desc[k].c_norm, B->precision,
-                  &reports[k]);
-    }
+  fill_reports(B, 1, reports);
+  B->have_corner = 1;
+  return PDHGC_OK;
+}
+
+int pdhgc_batch_solve_corner(pdhgc_batch* B, const pdhgc_params* params, const pdhgc_corner_params* cparams,
+                             pdhgc_report* reports1, pdhgc_report* reports_c) {
+  if (!B) return set_berr(PDHGC_ERR_INVALID_ARG, "batch is NULL");
+  pdhgc_params p;
+  if (params) p = *params; else pdhgc_default_params(&p);
+  pdhgc_corner_params cp;
+  if (cparams) cp = *cparams; else pdhgc_default_corner_params(&cp);
+  RET(check_batch_params(p));
+  RET(check_batch_corner_params(cp));
+  B->params = p;
+  B->precision = p.precision;
+  B->have_phase1 = 0;
+  B->have_corner = 0;
+  std::fill(B->ext1.begin(), B->ext1.end(), 0);
+  std::fill(B->extc.begin(), B->extc.end(), 0);
+  cudaStream_t st = B->stream;
+  BatchParams bp = make_params(p, &cp);
+  bp.handoff_running = B->handoff_running;
+  bp.handoff_min_iters = B->handoff_min_iters;
+  RET(run_batch(B, bp, 2, st));
+  BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep2, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  RET(run_handoffs(B, 2, p, &cp));
+  fill_reports(B, 0, reports1);
+  fill_reports(B, 1, reports_c);
+  B->have_phase1 = 1;
   B->have_corner = 1;
   return PDHGC_OK;
 }
@@ -1352,8 +764,8 @@ int pdhgc_batch_tune(pdhgc_batch* B, const pdhgc_params* params, int32_t tune_it
   if (params) p = *params; else pdhgc_default_params(&p);
   if (p.precision != PDHGC_FP64 && p.precision != PDHGC_FP32_BULK)
     return set_berr(PDHGC_ERR_INVALID_ARG, "precision must be PDHGC_FP64 or PDHGC_FP32_BULK");
-  if (p.algorithm != PDHGC_ALG_AVERAGED)
-    return set_berr(PDHGC_ERR_INVALID_ARG, "the batched solver runs the averaged loop only");
+  if (p.algorithm != PDHGC_ALG_AVERAGED && p.algorithm != PDHGC_ALG_HALPERN)
+    return set_berr(PDHGC_ERR_INVALID_ARG, "algorithm must be PDHGC_ALG_AVERAGED or PDHGC_ALG_HALPERN");
   p.max_iters = tune_iters;
   p.eps_rel = -1.0;
   B->precision = p.precision;

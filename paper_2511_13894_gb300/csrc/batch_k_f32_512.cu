@@ -1,0 +1,10 @@
+// One instantiation of the batched solver's persistent kernel: float iterates,
+// 512 threads per CTA (a translation unit of its own, so that the four
+// instantiations compile in parallel).
+#include "batch_kernel.cuh"
+
+namespace pdhgc {
+template cudaError_t batch_kernel_prepare<float, 512>(size_t, int*);
+template cudaError_t batch_kernel_launch<float, 512>(int, size_t, cudaStream_t, const LpDesc*, const int*, int, int*,
+                                                  const BatchParams&, int, BatchReport*, BatchReport*);
+}  // namespace pdhgc

@@ -40,6 +40,7 @@ struct Scalars {
   double fpr, fpr0, fpr_prev, pid_int, pid_eprev;
 };
 
+
 struct DevModel {
   const double* chat;
   const double* lhat;
@@ -1429,6 +1430,81 @@ __device__ __forceinline__ void ff_halpern(float th, float tl, float zh, float z
   ol = rl;
 }
 
+// FP32-bulk Halpern iterate.  z = (x, y) and the anchor z_0 = (xa, ya) are
+// float-float pairs.  The gathered vectors are differences from the anchor,
+// gx = fl(x_bar - x_0) (gathered by the dual pass) and gy = fl(y - y_0)
+// (gathered by the primal pass), and q = c_hat - A_hat' y_0, r0 = b_hat -
+// A_hat x_0 are formed in FP64 at every anchor (AnchorColsOp, AnchorRowsOp)
+// and kept as float-float pairs, so that the steps use
+//   c_hat - A_hat' y = q - A_hat' gy,   b_hat - A_hat x_bar = r0 - A_hat gx.
+// The FP32 rounding of the matrix values and of the gathered vectors then
+// scales with the distance from the anchor instead of with the iterate, and
+// the FP32 map's fixed point is that of the FP64 LP (up to that rounding of
+// a vanishing correction).
+struct DevH32 {
+  float* x;
+  float* xlo;
+  float* y;
+  float* ylo;
+  float2* xa;
+  float2* ya;
+  float* gx;
+  float* gy;
+  float2* q;
+  float2* r0;
+};
+
+// a double as a float-float pair
+__device__ __forceinline__ float2 to_ff(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// q = c_hat - A_hat' y_0 at the anchor (pass over A', FP64 matrix and anchor)
+struct AnchorColsOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
+  const Scalars* S;
+  int force;  // 1: at the start of a phase; 0: only after a restart to T(z)
+  const double* __restrict__ y0;
+  const double* __restrict__ chat;
+  float2* __restrict__ q;
+  __device__ bool skip() const { return !force && (S->done || S->restart_to != 3); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const double* gsrc(int) const { return y0; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void epilogue(int j, const Acc& a, double*) const { q[j] = to_ff(chat[j] - a.v[0]); }
+};
+
+// r0 = b_hat - A_hat x_0 at the anchor (pass over A)
+struct AnchorRowsOp {
+  using Acc = SumD<1>;
+  static constexpr int NQ = 0;
+  static constexpr unsigned kMaxMask = 0;
+  static constexpr int NG = 1;
+  using VT = double;
+  using GT = double;
+  const Scalars* S;
+  int force;
+  const double* __restrict__ x0;
+  const double* __restrict__ bhat;
+  float2* __restrict__ r0;
+  __device__ bool skip() const { return !force && (S->done || S->restart_to != 3); }
+  __device__ double row_ctx(int) const { return 0.0; }
+  __device__ const double* gsrc(int) const { return x0; }
+  __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
+  __device__ void epilogue(int i, const Acc& a, double*) const { r0[i] = to_ff(bhat[i] - a.v[0]); }
+};
+
+// (h, l) + (a, b) as a normalised pair
+__device__ __forceinline__ void ff_sum(float ah, float al, float bh, float bl, float& h, float& l) {
+  ff_sub(ah, al, -bh, -bl, h, l);
+}
+
 struct PrimalOpH32 {
   using Acc = SumFF;
   static constexpr int NQ = 0;
@@ -1438,26 +1514,26 @@ struct PrimalOpH32 {
   using GT = float;
   const Scalars* S;
   int it, last_it, probe;
-  const float* __restrict__ y;
-  DevModel32 md;
-  DevIter32 w;
+  DevModel32 md;  // lhat, uhat (c_hat enters through w.q)
+  DevH32 w;
   DevHalpern h;
   __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ const float* gsrc(int) const { return y; }
+  __device__ const float* gsrc(int) const { return w.gy; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
-    float c, l, u, x, xl, tau, s, rho;
-    float2 x0;
+    float l, u, x, xl, tau, s, rho;
+    float2 q, x0;
     bool last;
   };
   __device__ Pre prefetch(int j) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.xlo[j], (float)S->tau, h.hs[it], (float)S->rho,
+    return Pre{md.lhat[j], md.uhat[j], w.x[j], w.xlo[j], (float)S->tau, h.hs[it], (float)S->rho, w.q[j],
                w.xa[j], last};
   }
   __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
-    const float g = (p.c - a.hi[0]) - a.lo[0];
+    // g = c_hat - A_hat' y = q - A_hat' gy
+    const float g = (p.q.x - a.hi[0]) + (p.q.y - a.lo[0]);
     float th = p.x, tl = p.xl;
     ff_axpy(th, tl, -p.tau, g);
     const float xc = clamp_f(th, p.l, p.u);
@@ -1465,7 +1541,14 @@ struct PrimalOpH32 {
       th = xc;
       tl = 0.0f;
     }
-    w.xbar[j] = (2.0f * th - p.x) + (2.0f * tl - p.xl);
+    // x_bar = T - z + T, gathered as its difference from the anchor
+    float dh, dl;
+    ff_sub(th, tl, p.x, p.xl, dh, dl);
+    float bh, bl;
+    ff_sum(th, tl, dh, dl, bh, bl);
+    float eh, el;
+    ff_sub(bh, bl, p.x0.x, p.x0.y, eh, el);
+    w.gx[j] = eh + el;
     if (!probe) {
       float oh, ol;
       ff_halpern(th, tl, p.x, p.xl, p.x0, p.rho, p.s, oh, ol);
@@ -1473,10 +1556,8 @@ struct PrimalOpH32 {
       w.xlo[j] = ol;
     }
     if (p.last) {
-      float dh, dl;
-      ff_sub(p.x, p.xl, th, tl, dh, dl);
       h.xp[j] = (double)th + (double)tl;
-      h.dx[j] = (double)dh + (double)dl;
+      h.dx[j] = -((double)dh + (double)dl);
     }
   }
 };
@@ -1490,38 +1571,41 @@ struct DualOpH32 {
   using GT = float;
   const Scalars* S;
   int it, last_it, probe;
-  const float* __restrict__ xbar;
-  DevModel32 md;
-  DevIter32 w;
+  DevModel32 md;  // ge (b_hat enters through w.r0)
+  DevH32 w;
   DevHalpern h;
   __device__ bool skip() const { return S->done || (!probe && S->k + it >= S->max_iters); }
   __device__ double row_ctx(int) const { return 0.0; }
-  __device__ const float* gsrc(int) const { return xbar; }
+  __device__ const float* gsrc(int) const { return w.gx; }
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
-    float b, y, yl, sigma, s, rho;
-    float2 y0;
+    float y, yl, sigma, s, rho;
+    float2 r0, y0;
     bool ge, last;
   };
   __device__ Pre prefetch(int i) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, h.hs[it], (float)S->rho, w.ya[i], md.ge[i] != 0,
-               last};
+    return Pre{w.y[i], w.ylo[i], (float)S->sigma, h.hs[it], (float)S->rho, w.r0[i], w.ya[i], md.ge[i] != 0, last};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
-    const float r = (p.b - a.hi[0]) - a.lo[0];
+    // r = b_hat - A_hat x_bar = r0 - A_hat gx
+    const float r = (p.r0.x - a.hi[0]) + (p.r0.y - a.lo[0]);
     float th = p.y, tl = p.yl;
     ff_axpy(th, tl, p.sigma, r);
     if (p.ge && (th < 0.0f || (th == 0.0f && tl < 0.0f))) {  // y >= 0 on '>' rows
       th = 0.0f;
       tl = 0.0f;
     }
+    float yh = p.y, yl = p.yl;
     if (!probe) {
-      float oh, ol;
-      ff_halpern(th, tl, p.y, p.yl, p.y0, p.rho, p.s, oh, ol);
-      w.y[i] = oh;
-      w.ylo[i] = ol;
+      ff_halpern(th, tl, p.y, p.yl, p.y0, p.rho, p.s, yh, yl);
+      w.y[i] = yh;
+      w.ylo[i] = yl;
     }
+    // the next primal pass gathers the new y as its difference from the anchor
+    float eh, el;
+    ff_sub(yh, yl, p.y0.x, p.y0.y, eh, el);
+    w.gy[i] = eh + el;
     if (p.last) {
       float dh, dl;
       ff_sub(p.y, p.yl, th, tl, dh, dl);

@@ -170,6 +170,9 @@ struct Iter32 {
   float2* sy;
   float2* xa;  // Halpern loop: float-float anchors
   float2* ya;
+  float* gy;   // Halpern loop: fl(y - y_0), gathered by the primal pass (xbar holds fl(x_bar - x_0))
+  float2* q;   // Halpern loop: c_hat - A_hat' y_0 and b_hat - A_hat x_0 at the anchor
+  float2* r0;
 };
 
 __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
@@ -198,6 +201,7 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
       w32.ylo[i] = 0.0f;
       w32.sy[i] = make_float2(0.f, 0.f);
       w32.ya[i] = make_float2(0.f, 0.f);
+      w32.gy[i] = 0.0f;
     }
   }
 }
@@ -296,9 +300,9 @@ __global__ void k_halpern_weights(const Scalars* S, double* hw, float* hs, int P
 
 // FP32-bulk Halpern loop, end of a phase: FP64 copies of the float-float
 // iterate z for the accessors
-__global__ void k_h32_to64(int n, int m, const float* __restrict__ x32, const float* __restrict__ xlo,
-                           const float* __restrict__ y32, const float* __restrict__ ylo, double* __restrict__ x,
-                           double* __restrict__ y) {
+__global__ void k_h32_to64(const Scalars* S, int n, int m, const float* __restrict__ x32,
+                           const float* __restrict__ xlo, const float* __restrict__ y32,
+                           const float* __restrict__ ylo, double* __restrict__ x, double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = (double)x32[i] + (double)xlo[i];
   if (i < m) y[i] = (double)y32[i] + (double)ylo[i];
@@ -415,6 +419,7 @@ __global__ void k_restart_apply(const Scalars* S, int n, int m, DevIter w, Iter3
         w32.y[i] = h;
         w32.ylo[i] = lo;
         w32.ya[i] = make_float2(h, lo);
+        w32.gy[i] = 0.0f;  // y is the anchor now
       }
     }
     return;
@@ -777,6 +782,9 @@ int ensure_fp32(pdhgc_lp* lp) {
   RET(lp->alloc(&lp->it32.sy, m));
   RET(lp->alloc(&lp->it32.xa, n));
   RET(lp->alloc(&lp->it32.ya, m));
+  RET(lp->alloc(&lp->it32.gy, m));
+  RET(lp->alloc(&lp->it32.q, n));
+  RET(lp->alloc(&lp->it32.r0, m));
   RET(lp->alloc(&lp->chat32, n));
   RET(lp->alloc(&lp->lhat32, n));
   RET(lp->alloc(&lp->uhat32, n));
@@ -887,53 +895,35 @@ int ensure_halpern(pdhgc_lp* lp) {
   return PDHGC_OK;
 }
 
-// Runs one phase: init, the device-driven loop graph, finalize.
-int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi,
-              const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback) {
-  cudaStream_t st = lp->stream;
+// the FP32-bulk Halpern iterate of the handle (the gathered x_bar difference
+// lives in it32.xbar)
+DevH32 h32_of(const pdhgc_lp* lp) {
+  const Iter32& w = lp->it32;
+  return DevH32{w.x, w.xlo, w.y, w.ylo, w.xa, w.ya, w.xbar, w.gy, w.q, w.r0};
+}
+
+// q = c_hat - A_hat' y_0 and r0 = b_hat - A_hat x_0 at the current anchor
+// (FP64 copies x_r, y_r); force = 0: only when the last decision restarted
+int launch_anchor(pdhgc_lp* lp, const DevModel& md, int force, cudaStream_t st) {
+  RET(launch_tiles(lp, true, true, AnchorColsOp{lp->S, force, lp->it.y_r, md.chat, lp->it32.q}, nullptr, st));
+  RET(launch_tiles(lp, false, true, AnchorRowsOp{lp->S, force, lp->it.x_r, md.bhat, lp->it32.r0}, nullptr, st));
+  return PDHGC_OK;
+}
+
+// Builds and launches the loop graph of a phase on the handle's stream:
+// while (!done) { P iterations; pre-check; eval; decide; restart; weights }.
+// fp32 selects the FP32-bulk iteration kernels; the evaluation and the
+// decisions are FP64 in both.  Adds the kernels of the executed bodies to
+// lp->launches once the graph has finished (the caller synchronises).
+int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi, bool fp32,
+                bool ring, const RingRec& rr, int64_t* per_body_out) {
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
-  const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
   const bool halpern = pi.algorithm == PDHGC_ALG_HALPERN;
-  if (halpern) RET(ensure_halpern(lp));
   const DevHalpern hz = lp->hz;
   const Iter32 w32 = fp32 ? lp->it32 : Iter32{};
   const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
                        lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
-  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
-  k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
-  lp->launches += 2;
-  CKL();
-  // phase 1 records its restart history (start point and restart points)
-  const bool ring = pi.phase == 0;
-  const RingRec rr = ring ? RingRec{lp->ring_x, lp->ring_z, lp->z_cur, lp->z_avg} : RingRec{};
-  RET(launch_eval(lp, md, st, ring));
-  k_decide<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
-  lp->launches++;
-  CKL();
-  if (ring) {
-    k_ring_init<<<grid_for(n), 256, 0, st>>>(n, lp->it.x, rr);
-    lp->launches++;
-    CKL();
-  }
-  if (halpern) {
-    // the anchor's fixed-point residual: T of the start point (not an
-    // iteration), its check quantities, and the first chunk's weights
-    if (fp32) {
-      RET(launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 0, 1, lp->it32.y, md32, it32, hz}, nullptr, st));
-      RET(launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 0, 1, lp->it32.xbar, md32, it32, hz}, nullptr, st));
-    } else {
-      RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
-      RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
-    }
-    RET(launch_eval_h(lp, md, st, false));
-    k_decide_h<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
-    k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, hz.hs, pi.check_period);
-    lp->launches += 2;
-    CKL();
-  }
-
-  // the loop: while (!done) { P iterations; pre-check; eval; decide; restart }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   CK(cudaGraphCreate(&graph, 0));
@@ -955,11 +945,9 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
     if (halpern && fp32) {
       const int last = pi.check_period - 1;
-      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, i, last, 0, lp->it32.y, md32, it32, hz}, nullptr, cs,
-                        true);
+      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
       if (rc == PDHGC_OK)
-        rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, lp->it32.xbar, md32, it32, hz}, nullptr,
-                          cs, true);
+        rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
     } else if (halpern) {
       const int last = pi.check_period - 1;
       rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, nullptr, cs, true);
@@ -993,25 +981,82 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
       k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
     k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr, hz);
     lp->launches += 2;
-    if (halpern) {
+    if (halpern && fp32) rc = launch_anchor(lp, md, 0, cs);  // a restart moved the anchor
+    if (halpern && rc == PDHGC_OK) {
       k_halpern_weights<<<1, 256, 0, cs>>>(lp->S, hz.hw, hz.hs, pi.check_period);
       lp->launches++;
     }
   }
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &captured);
-  const int64_t per_body = lp->launches - before;
-  lp->launches = before;  // counted per executed body below
+  *per_body_out = lp->launches - before;
+  lp->launches = before;  // counted per executed body by the caller
   if (rc != PDHGC_OK) return rc;
   if (ce != cudaSuccess) return set_err(PDHGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
   CK(cudaGraphInstantiate(&exec, graph, 0));
   std::unique_ptr<CUgraphExec_st, void (*)(cudaGraphExec_t)> e_guard(exec,
                                                                     [](cudaGraphExec_t e) { cudaGraphExecDestroy(e); });
-  CK(cudaGraphLaunch(exec, st));
+  CK(cudaGraphLaunch(exec, lp->stream));
+  CK(cudaStreamSynchronize(lp->stream));  // the executable graph is destroyed on return
+  return PDHGC_OK;
+}
+
+// Runs one phase: init, the device-driven loop graph, finalize.
+int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi,
+              const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback) {
+  cudaStream_t st = lp->stream;
+  const int n = lp->n, m = lp->m;
+  const int gnm = grid_for(n > m ? n : m);
+  const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
+  const bool halpern = pi.algorithm == PDHGC_ALG_HALPERN;
+  if (halpern) RET(ensure_halpern(lp));
+  const DevHalpern hz = lp->hz;
+  const Iter32 w32 = fp32 ? lp->it32 : Iter32{};
+  const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
+                       lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
+  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
+  k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
+  lp->launches += 2;
+  CKL();
+  // phase 1 records its restart history (start point and restart points)
+  const bool ring = pi.phase == 0;
+  const RingRec rr = ring ? RingRec{lp->ring_x, lp->ring_z, lp->z_cur, lp->z_avg} : RingRec{};
+  RET(launch_eval(lp, md, st, ring));
+  k_decide<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+  lp->launches++;
+  CKL();
+  if (ring) {
+    k_ring_init<<<grid_for(n), 256, 0, st>>>(n, lp->it.x, rr);
+    lp->launches++;
+    CKL();
+  }
+  if (halpern) {
+    // the anchor's fixed-point residual: T of the start point (not an
+    // iteration), its check quantities, and the first chunk's weights
+    if (fp32) {
+      RET(launch_anchor(lp, md, 1, st));
+      RET(launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 0, 1, md32, h32_of(lp), hz}, nullptr, st));
+      RET(launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 0, 1, md32, h32_of(lp), hz}, nullptr, st));
+    } else {
+      RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
+      RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
+    }
+    RET(launch_eval_h(lp, md, st, false));
+    k_decide_h<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+    k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, hz.hs, pi.check_period);
+    lp->launches += 2;
+    CKL();
+  }
+  int64_t per_body = 0;
+  RET(launch_loop(lp, md, md32, pi, fp32, ring, rr, &per_body));
+  long long chunks = 0;
+  CK(cudaMemcpy(&chunks, &lp->S->chunks, sizeof(chunks), cudaMemcpyDeviceToHost));
+  lp->launches += chunks * per_body;
   k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat, hz);
   lp->launches++;
   if (fp32 && halpern) {
-    k_h32_to64<<<gnm, 256, 0, st>>>(n, m, lp->it32.x, lp->it32.xlo, lp->it32.y, lp->it32.ylo, lp->it.x, lp->it.y);
+    k_h32_to64<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it32.x, lp->it32.xlo, lp->it32.y, lp->it32.ylo, lp->it.x,
+                                    lp->it.y);
     lp->launches++;
   }
   CKL();
@@ -1020,9 +1065,6 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   CK(cudaMemcpy(&derr, lp->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (derr != 0) return set_err(PDHGC_ERR_DEVICE, "a bounded device wait ran out (error word " +
                                                       std::to_string(derr) + ")");
-  long long chunks = 0;
-  CK(cudaMemcpy(&chunks, &lp->S->chunks, sizeof(chunks), cudaMemcpyDeviceToHost));
-  lp->launches += chunks * per_body;
   return PDHGC_OK;
 }
 
@@ -2132,7 +2174,7 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     CK(cudaEventRecord(ev[3 * i], st));
     // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
     if (halpern && fp32)
-      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 1, 0, lp->it32.y, md32, it32, lp->hz}, nullptr, st);
+      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, nullptr, st);
     else if (halpern)
       rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, nullptr, st);
     else if (fp32)
@@ -2142,8 +2184,7 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     if (rc != PDHGC_OK) break;
     CK(cudaEventRecord(ev[3 * i + 1], st));
     if (halpern && fp32)
-      rc = launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 1, 0, lp->it32.xbar, md32, it32, lp->hz}, nullptr,
-                        st);
+      rc = launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, nullptr, st);
     else if (halpern)
       rc = launch_tiles(lp, false, true, DualOpH{lp->S, 0, 1, 0, lp->it.xbar, md, lp->it, lp->hz}, nullptr, st);
     else if (fp32)

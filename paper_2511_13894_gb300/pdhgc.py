@@ -118,6 +118,7 @@ _sig = {
                                      _vp, _vp]),
     "pdhgc_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp]),
     "pdhgc_batch_corner_phase": (C.c_int, [_vp, C.POINTER(CornerParams), _vp]),
+    "pdhgc_batch_solve_corner": (C.c_int, [_vp, C.POINTER(Params), C.POINTER(CornerParams), _vp, _vp]),
     "pdhgc_batch_get_solution": (C.c_int, [_vp, C.c_int32, C.c_int, _vp, _vp]),
     "pdhgc_batch_set_block": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_batch_set_lanes": (C.c_int, [_vp, C.c_int32, C.c_int32]),
@@ -454,6 +455,17 @@ class Batch:
         reps = (Report * self.count)()
         _check(lib.pdhgc_batch_corner_phase(self._h, C.byref(p), C.cast(reps, _vp)), "pdhgc_batch_corner_phase")
         return [r.as_dict() for r in reps]
+
+    def solve_corner(self, params: Params | None = None, cparams: CornerParams | None = None):
+        """pdhgc_batch_solve_corner: both phases per LP in one launch; returns
+        (phase-1 reports, corner reports)."""
+        p = params if params is not None else default_params()
+        cp = cparams if cparams is not None else default_corner_params()
+        r1 = (Report * self.count)()
+        rc = (Report * self.count)()
+        _check(lib.pdhgc_batch_solve_corner(self._h, C.byref(p), C.byref(cp), C.cast(r1, _vp), C.cast(rc, _vp)),
+               "pdhgc_batch_solve_corner")
+        return [r.as_dict() for r in r1], [r.as_dict() for r in rc]
 
     def get_solution(self, k: int, which: int = PHASE1):
         x = np.empty(self.n[k])

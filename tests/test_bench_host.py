@@ -22,8 +22,9 @@ def test_headline_algorithm():
     assert bench.headline_algorithm(_args()) == "halpern"
     assert bench.headline_algorithm(_args(algorithm="halpern")) == "halpern"
     assert bench.headline_algorithm(_args(algorithm="averaged")) == "averaged"
-    # the batched workload runs the averaged loop only
-    assert bench.headline_algorithm(_args(workload="batch_512")) == "averaged"
+    # the batched workload follows the same setting
+    assert bench.headline_algorithm(_args(workload="batch_512")) == "halpern"
+    assert bench.headline_algorithm(_args(workload="batch_512", algorithm="averaged")) == "averaged"
 
 
 def test_halpern_bytes_differ_by_the_sums_and_the_anchor():

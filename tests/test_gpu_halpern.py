@@ -132,7 +132,7 @@ def test_halpern_restart_history_feeds_the_guidance_features():
     assert np.array_equal(elig.cpu().numpy().astype(bool), E)
 
 
-def test_halpern_refused_where_not_built():
+def test_halpern_refuses_bad_settings():
     lp = lpgen.small_face_lp(0)
     g = P.lp_from_dict(lp)
     with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
@@ -141,7 +141,7 @@ def test_halpern_refused_where_not_built():
         g.solve(algorithm=7)
     B = P.Batch([lpgen.batch_lp(i) for i in range(2)])
     with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
-        B.solve(algorithm=P.HALPERN)
+        B.solve(algorithm=P.HALPERN, reflection=-0.5)
 
 
 def test_halpern_corner_phase_on_skewed_power_law_matches_oracle():

@@ -213,16 +213,23 @@ def test_dense_lines_run_the_cta_segment_and_match_oracle(alg):
     orep = oracle.kkt_report(ref["model"], ref["x_hat"], ref["y_hat"])
     for k in ("off_bound_p", "zero_rc_d", "candidates", "corner_measure"):
         assert rep[k] == orep[k], k
-    # FP32 bulk through the same segments.  Its fixed point is the optimum of
-    # the LP with FP32-rounded scaled coefficients: on the 4500-entry row that
-    # rounding (2^-24 relative per value) leaves an FP64 relative primal
-    # residual of about 2e-6 at that point (an FP64 emulation of the FP32 map
-    # shows the same floor), so the stated bound here is rel-KKT <= 1e-5
+    # FP32 bulk through the same segments.  In the averaged loop the FP32
+    # map's fixed point is the optimum of the LP with FP32-rounded scaled
+    # coefficients: on the 4500-entry row that rounding (2^-24 relative per
+    # value) leaves an FP64 relative primal residual of about 2e-6, so its
+    # stated bound here is 1e-5.  The Halpern loop's FP32 kernels gather and
+    # multiply only differences from the anchor, with c - A'y_0 and b - A x_0
+    # formed in FP64 at each anchor: its fixed point is the FP64 LP's, and
+    # it meets 1e-6 in the FP64 loop's iterations.
     r32 = g.solve(algorithm=P.HALPERN if alg == "halpern" else P.AVERAGED, precision=P.FP32_BULK,
                   max_iters=200_000)
     print(f"dense lines, {alg} FP32 bulk: {r32['status_name']} after {r32['iters']} iterations, "
           f"rel_p {r32['rel_p']:.2e} rel_d {r32['rel_d']:.2e} rel_gap {r32['rel_gap']:.2e}")
-    assert r32["rel_kkt"] <= 1e-5
+    if alg == "halpern":
+        assert r32["status_name"] == "OPTIMAL" and r32["rel_kkt"] <= 1e-6
+        assert abs(r32["iters"] - ref["iters"]) <= max(640, ref["iters"] // 10)
+    else:
+        assert r32["rel_kkt"] <= 1e-5
     assert abs(r32["pobj"] - orep["pobj"]) <= 1e-5 * (1.0 + abs(orep["pobj"]))
 
 
