@@ -123,6 +123,33 @@ def shard(items, rank, world):
     return items[rank::world]
 
 
+def lpt_partition(weights, world):
+    """Longest-processing-time-first split of items with the given weights
+    over `world` bins: items in decreasing weight (ties by index) each go to
+    the bin with the smallest load so far (ties: the lowest bin).  Graham's
+    bound: the largest load is at most (4/3 - 1/(3 world)) times the optimum.
+    Returns one sorted index list per bin."""
+    order = sorted(range(len(weights)), key=lambda k: (-weights[k], k))
+    loads = [0.0] * world
+    bins = [[] for _ in range(world)]
+    for k in order:
+        b = min(range(world), key=lambda r: (loads[r], r))
+        bins[b].append(k)
+        loads[b] += weights[k]
+    return [sorted(b) for b in bins]
+
+
+def lp_weight(lp):
+    """Per-iteration cost proxy of one LP for the batch split: nonzeros plus
+    rows plus columns (the bytes of an iteration grow with each)."""
+    return int(lp["row_ptr"][-1]) + int(lp["m"]) + int(lp["n"])
+
+
+def shard_lpt(items, weights, rank, world):
+    """The items of one rank under the LPT split of their weights."""
+    return [items[k] for k in lpt_partition(weights, world)[rank]]
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -516,11 +543,13 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     """512 uneven LPs (random-face construction, m ~ U{50..5000}) in one
     persistent, graph-captured launch with the autotuned schedule, FP32 bulk,
     the headline's inner loop.  One step = phase 1 of every LP to rel-KKT
-    1e-6 plus Algorithm 1 on every LP, both in the same launch.  Ranks split the LPs round-robin (strong scaling: the batch
-    is fixed).  The single-LP FP64 path on a size-stratified sample of the LPs,
-    one after another, gives the sequential reference time."""
+    1e-6 plus Algorithm 1 on every LP, both in the same launch.  Ranks split
+    the LPs longest-processing-time-first by their per-iteration cost
+    (strong scaling: the batch is fixed).  The single-LP FP64 path on a
+    size-stratified sample of the LPs, one after another, gives the
+    sequential reference time."""
     all_lps = lpgen.batch_lps(512)
-    lps = shard(all_lps, rank, world)
+    lps = shard_lpt(all_lps, [lp_weight(lp) for lp in all_lps], rank, world)
     alg = headline_algorithm(args)
     algorithm = P.HALPERN if alg == "halpern" else P.AVERAGED
     stream = torch.cuda.current_stream()
@@ -640,7 +669,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "sum_m": sum(lp["m"] for lp in all_lps), "sum_n": sum(lp["n"] for lp in all_lps),
                        "sum_nnz": sum(int(lp["row_ptr"][-1]) for lp in all_lps), "precision": "fp32_bulk",
                        "schedule": tuned, "corner_max_iters": args.corner_max_iters, "eps_rel": 1e-6,
-                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"lp-split x{world}"},
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"lpt-split x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
             "tail_handoff": {"phase1_lps": h1, "corner_lps": hc,
                              "rule": "once the queue is empty and <= 8 LPs run, an LP past 8192 iterations "
