@@ -256,10 +256,29 @@ int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalar
  * nonzeros (one CTA per row), of blocks of warp-per-row rows (129..4096
  * nonzeros), of SELL-32 blocks (rows of at most 128 nonzeros), and the
  * number of rows in the CTA segment.  `out` is a host array of 8 int64.
+ * (The Halpern loop's primal pass can instead run a chunked layout; see
+ * pdhgc_set_primal_layout.)
  * A layout query (the paper has no counterpart; the segments implement the
  * CSR passes of the Section 2 iteration).  Errors: INVALID_ARG.
  */
 int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out);
+
+/*
+ * pdhgc_set_primal_layout — how the Halpern loop runs its primal pass
+ * x+ = proj(x - tau (c - A'y)) (the Section 2 iteration's A' product):
+ * chunked = 0 (the default) uses the row segments of pdhgc_get_layout with
+ * gathers from global memory; chunked = 1 stages the gathered vector y in
+ * shared memory, 200 KB at a time, with one CTA per SM whose warps gather
+ * from shared memory (the layout is planned at lp_create: work units of one
+ * long column or 32 short ones, their entries grouped by chunk).  On the
+ * 100k x 400k LP the chunked pass measured 2-2.5 times slower (each warp
+ * runs its units' short per-chunk segments one after another), so it is
+ * not the default.  The results differ only by the summation order of the
+ * row sums.  Takes effect at the next pdhgc_solve or pdhgc_corner_phase.  A
+ * layout choice for measurement and tests (the paper has no counterpart).
+ * Errors: INVALID_ARG.
+ */
+int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked);
 
 /*
  * pdhgc_kkt_eval — the Section 2 residuals, objectives and relative ratios,

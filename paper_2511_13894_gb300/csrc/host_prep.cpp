@@ -19,7 +19,126 @@ std::vector<int32_t> order_by_decreasing(const std::vector<int64_t>& len) {
   return idx;
 }
 
+// columns by decreasing length, then by decreasing chunk counts q[.][0..2]
+std::vector<int32_t> order_columns(const std::vector<int64_t>& len, const std::vector<int32_t>& q) {
+  std::vector<int32_t> idx(len.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+    if (len[a] != len[b]) return len[a] > len[b];
+    for (int k = 0; k < 3; ++k)
+      if (q[3 * (size_t)a + k] != q[3 * (size_t)b + k]) return q[3 * (size_t)a + k] > q[3 * (size_t)b + k];
+    return false;
+  });
+  return idx;
+}
+
 }  // namespace
+
+void plan_chunks(const Csr& T, int32_t chunk, int32_t sms, ChunkPlan& P) {
+  const int32_t R = T.rows;
+  const int32_t G = T.cols;  // gathered length
+  P = ChunkPlan{};
+  P.chunk = chunk;
+  P.nch = G > 0 ? (G + chunk - 1) / chunk : 1;
+  const int32_t nch = P.nch;
+  auto len = [&](int32_t r) { return T.row_ptr[r + 1] - T.row_ptr[r]; };
+  // units: long rows one by one, then slices of 32 rows
+  int32_t r = 0;
+  while (r < R && len(r) > kChunkLongLen) {
+    P.units.push_back(ChunkUnit{r, 1, 1, 0});
+    ++r;
+  }
+  for (; r < R; r += 32) P.units.push_back(ChunkUnit{r, std::min<int32_t>(32, R - r), 0, 0});
+  P.nunits = (int32_t)P.units.size();
+  P.uc_off.assign((size_t)P.nunits * nch, 0);
+  P.uc_cnt.assign((size_t)P.nunits * nch, 0);
+  std::vector<int64_t> steps(P.nunits, 0);
+  // slot counts per unit and chunk
+  std::vector<int32_t> cnt(nch), wid(nch);
+  int64_t off = 0;
+  for (int32_t u = 0; u < P.nunits; ++u) {
+    const ChunkUnit& U = P.units[u];
+    std::fill(wid.begin(), wid.end(), 0);
+    for (int32_t t = 0; t < U.nrows; ++t) {  // widest row of the unit in each chunk
+      std::fill(cnt.begin(), cnt.end(), 0);
+      const int32_t row = U.row0 + t;
+      for (int32_t e = T.row_ptr[row]; e < T.row_ptr[row + 1]; ++e) cnt[T.col[e] / chunk]++;
+      for (int32_t c = 0; c < nch; ++c) wid[c] = std::max(wid[c], cnt[c]);
+    }
+    for (int32_t c = 0; c < nch; ++c) {
+      const int32_t w = wid[c];
+      P.uc_off[(size_t)u * nch + c] = (int32_t)off;
+      P.uc_cnt[(size_t)u * nch + c] = w;
+      off += U.is_long ? w : (int64_t)w * 32;
+      steps[u] += U.is_long ? (w + 31) / 32 : w;
+    }
+    steps[u] += 1;  // the epilogue
+  }
+  P.nslots = off;
+  P.slot_map.assign((size_t)off, -1);
+  P.slot_idx.assign((size_t)off, kChunkPadIdx);
+  std::vector<int32_t> fill(nch);
+  for (int32_t u = 0; u < P.nunits; ++u) {
+    const ChunkUnit& U = P.units[u];
+    for (int32_t t = 0; t < U.nrows; ++t) {
+      std::fill(fill.begin(), fill.end(), 0);
+      const int32_t row = U.row0 + t;
+      for (int32_t e = T.row_ptr[row]; e < T.row_ptr[row + 1]; ++e) {
+        const int32_t c = T.col[e] / chunk;
+        const int64_t base = P.uc_off[(size_t)u * nch + c];
+        const int64_t s = U.is_long ? base + fill[c] : base + (int64_t)fill[c] * 32 + t;
+        fill[c]++;
+        P.slot_map[(size_t)s] = e;
+        P.slot_idx[(size_t)s] = (uint16_t)(T.col[e] - c * chunk);
+      }
+    }
+  }
+  // warps: longest-processing-time first, at most kChunkMaxUnits units per warp
+  std::vector<int32_t> order(P.nunits);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return steps[a] > steps[b]; });
+  const int32_t per_wave = std::max(1, sms) * kChunkWarps * kChunkMaxUnits;
+  int32_t waves = std::max(1, (P.nunits + per_wave - 1) / per_wave);
+  while (true) {
+    const int32_t blocks = std::max(1, sms) * waves;
+    const int32_t W = blocks * kChunkWarps;
+    std::vector<int64_t> load(W, 0);
+    std::vector<int32_t> nu(W, 0);
+    std::vector<int32_t> wu((size_t)W * kChunkMaxUnits, -1);
+    // a min-heap of (load, warp) over the warps that still have room
+    std::vector<std::pair<int64_t, int32_t>> heap;
+    heap.reserve(W);
+    for (int32_t w = 0; w < W; ++w) heap.push_back({0, w});
+    auto cmp = [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) {
+      return a.first != b.first ? a.first > b.first : a.second > b.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    bool ok = true;
+    for (int32_t u : order) {
+      if (heap.empty()) {
+        ok = false;
+        break;
+      }
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto top = heap.back();
+      heap.pop_back();
+      const int32_t w = top.second;
+      wu[(size_t)w * kChunkMaxUnits + nu[w]] = u;
+      nu[w]++;
+      load[w] += steps[u];
+      if (nu[w] < kChunkMaxUnits) {
+        heap.push_back({load[w], w});
+        std::push_heap(heap.begin(), heap.end(), cmp);
+      }
+    }
+    if (ok) {
+      P.blocks = blocks;
+      P.warp_units.swap(wu);
+      return;
+    }
+    ++waves;
+  }
+}
 
 void plan_segments(Csr& csr) {
   const int32_t R = csr.rows;
@@ -133,10 +252,17 @@ int prepare_lp(Prepared& P, int32_t m, int32_t n, int64_t nnz, const int64_t* ro
   for (int32_t i = 0; i < m; ++i) rlen[i] = row_ptr[i + 1] - row_ptr[i];
   for (int64_t e = 0; e < nnz; ++e) clen[col_idx[e]]++;
   P.row_perm = order_by_decreasing(rlen);
-  P.col_perm = order_by_decreasing(clen);
   P.row_inv.assign(m, 0);
-  P.col_inv.assign(n, 0);
   for (int32_t r = 0; r < m; ++r) P.row_inv[P.row_perm[r]] = r;
+  // per column: entries whose internal row lies in chunk 0, 1, 2 of kChunkElems64 rows
+  std::vector<int32_t> q(3 * (size_t)n, 0);
+  for (int32_t i = 0; i < m; ++i) {
+    const int32_t k = P.row_inv[i] / kChunkElems64;
+    if (k >= 3) continue;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) q[3 * (size_t)col_idx[e] + k]++;
+  }
+  P.col_perm = order_columns(clen, q);
+  P.col_inv.assign(n, 0);
   for (int32_t j = 0; j < n; ++j) P.col_inv[P.col_perm[j]] = j;
 
   // internal A: rows in internal order, entries in the user's order within a row

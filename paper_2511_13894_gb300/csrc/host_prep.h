@@ -1,10 +1,14 @@
 // Host-side layout of an LP for the GPU kernels (plain C++, no CUDA).
 //
-// Rows and columns are renumbered internally by decreasing nnz (stable), so
-// that the 32 rows of a warp have nearly equal lengths; '<' rows are negated
-// into '>' rows (Section 2: inequalities handled implicitly); an explicit CSR
-// of A' is built by a stable counting sort; and each CSR gets its row
-// segments and SELL-32 slots planned.
+// Rows are renumbered internally by decreasing nnz (stable).  Columns are
+// renumbered by decreasing nnz, then (stable, among columns of equal length)
+// by decreasing counts of entries in the row-index ranges [0, C), [C, 2C),
+// [2C, 3C) with C = kChunkElems64, so that the 32 columns of a slice have
+// nearly equal lengths both in total and within each staged chunk of the
+// gathered vector (ChunkPlan).  '<' rows are negated into '>' rows (Section
+// 2: inequalities handled implicitly); an explicit CSR of A' is built by a
+// stable counting sort; and each CSR gets its row segments and SELL-32 slots
+// planned.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -31,6 +35,17 @@ constexpr int kSellMaxLen = kColsPerWarp * kWarpsPerBlock;  // longest row kept 
 constexpr int kWarpMaxLen = 4096;    // longest row given to a single warp
 constexpr int kPad = 8;              // trailing padding elements of every device array
 
+// Chunked primal pass (ChunkPlan): the gathered vector is staged in shared
+// memory kChunkBytes at a time; one CTA of kChunkThreads threads per SM
+constexpr int kChunkBytes = 200 * 1024;
+constexpr int kChunkElems32 = kChunkBytes / 4;  // 51,200 FP32 entries per chunk
+constexpr int kChunkElems64 = kChunkBytes / 8;  // 25,600 FP64 entries per chunk
+constexpr int kChunkThreads = 1024;
+constexpr int kChunkWarps = kChunkThreads / 32;
+constexpr int kChunkMaxUnits = 8;   // work units one warp owns
+constexpr int kChunkLongLen = 128;  // rows longer than this are a unit of their own
+constexpr uint16_t kChunkPadIdx = 0xFFFF;  // index of a padding slot
+
 // one CTA of SELL work: slices [first, first + count), K warps per slice
 struct SellBlock {
   int32_t first;
@@ -56,6 +71,38 @@ struct Csr {
   int32_t nb_sell() const { return (int32_t)sell_blocks.size(); }
   int32_t nblocks() const { return nb_cta() + nb_warp() + nb_sell(); }
 };
+
+// The primal pass over A' (rows = columns j of A, gathered vector of length
+// A'.cols = m) with the gathered vector staged in shared memory `chunk`
+// entries at a time (nch chunks).  Work units: a row longer than
+// kChunkLongLen (its 32 lanes stride over the row's entries in the chunk),
+// or a slice of up to 32 consecutive shorter rows (a lane per row; the
+// slice's entries in the chunk stored column-major, as wide as its widest
+// row there).  Per unit and chunk: the offset and the count (long row) or
+// width (slice) of its slots; a slot holds the CSR index of its entry
+// (slot_map, -1 for padding) and the entry's index within the chunk
+// (slot_idx, kChunkPadIdx for padding).  Units go to the warps of `blocks`
+// CTAs (a multiple of the SM count) longest-processing-time first on their
+// steps, at most kChunkMaxUnits per warp; warp_units lists them (-1: none).
+struct ChunkUnit {
+  int32_t row0;
+  int32_t nrows;
+  int32_t is_long;
+  int32_t pad;
+};
+struct ChunkPlan {
+  int32_t chunk = 0, nch = 0, blocks = 0, nunits = 0;
+  int64_t nslots = 0;
+  std::vector<ChunkUnit> units;
+  std::vector<int32_t> uc_off, uc_cnt;  // nunits * nch
+  std::vector<int32_t> slot_map;
+  std::vector<uint16_t> slot_idx;
+  std::vector<int32_t> warp_units;      // blocks * kChunkWarps * kChunkMaxUnits
+};
+
+// Plans the chunked pass over `T` (A', rows sorted by decreasing length) for
+// chunks of `chunk` (<= 65535) gathered entries on a GPU with `sms` SMs.
+void plan_chunks(const struct Csr& T, int32_t chunk, int32_t sms, ChunkPlan& out);
 
 struct Prepared {
   int32_t m = 0, n = 0;

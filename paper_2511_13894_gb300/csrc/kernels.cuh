@@ -636,6 +636,125 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
 }
 
 // ---------------------------------------------------------------------------
+// The chunked pass (ChunkPlan in host_prep.h): one CTA of kChunkThreads per
+// SM.  For each chunk of the gathered vector the CTA copies the chunk into
+// shared memory with coalesced 16-byte loads, then every warp runs its work
+// units' entries in that chunk, gathering from shared memory; the row sums
+// stay in registers across chunks and the operator's epilogue runs once at
+// the end.  A slice unit (up to 32 rows) gives a lane a row and reads the
+// chunk's slots column-major; a long-row unit lets its 32 lanes stride over
+// the row's slots and reduces them by shuffles.  Padding slots carry
+// kChunkPadIdx and are skipped.
+// ---------------------------------------------------------------------------
+template <class VT>
+struct ChunkMatT {
+  const VT* __restrict__ val;          // slots
+  const uint16_t* __restrict__ idx;    // slots: index within the chunk
+  const ChunkUnit* __restrict__ units;
+  const int* __restrict__ uc_off;      // nunits * nch
+  const int* __restrict__ uc_cnt;
+  const int* __restrict__ warp_units;  // blocks * kChunkWarps * kChunkMaxUnits
+  int nch, chunk, glen;
+};
+
+template <class GT>
+__device__ __forceinline__ void stage_chunk(GT* __restrict__ s, const GT* __restrict__ src, int len) {
+  // 16-byte vector loads (src is 16-byte aligned: the chunk starts at a
+  // multiple of kChunkBytes / sizeof(GT) entries of a cudaMalloc'd array)
+  constexpr int V = 16 / sizeof(GT);
+  const int nv = len / V;
+  const float4* __restrict__ s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(s);
+  for (int t = threadIdx.x; t < nv; t += kChunkThreads) d4[t] = __ldcg(s4 + t);
+  for (int t = nv * V + threadIdx.x; t < len; t += kChunkThreads) s[t] = src[t];
+}
+
+template <class Op, bool kPdl>
+__global__ void __launch_bounds__(kChunkThreads, 1)
+    spmv_chunked(ChunkMatT<typename Op::VT> M, Op op) {
+  using VT = typename Op::VT;
+  using GT = typename Op::GT;
+  using PF = Prefetcher<Op>;
+  static_assert(Op::NG == 1, "one gathered vector");
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  GT* s_g = reinterpret_cast<GT*>(s_raw);
+  if constexpr (!kPdl) {
+    if (op.skip()) return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int* wl = M.warp_units + ((size_t)blockIdx.x * kChunkWarps + warp) * kChunkMaxUnits;
+  int u[kChunkMaxUnits];
+#pragma unroll
+  for (int k = 0; k < kChunkMaxUnits; ++k) u[k] = wl[k];
+  typename Op::Acc acc[kChunkMaxUnits];
+#pragma unroll
+  for (int k = 0; k < kChunkMaxUnits; ++k) acc[k].zero();
+  if constexpr (kPdl) {
+    grid_dep_wait();
+    if (op.skip()) return;  // uniform over the grid
+  }
+  const GT* src = op.gsrc(0);
+  for (int c = 0; c < M.nch; ++c) {
+    const int base = c * M.chunk;
+    __syncthreads();  // every warp is done with the previous chunk
+    stage_chunk(s_g, src + base, min(M.chunk, M.glen - base));
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kChunkMaxUnits; ++k) {
+      if (u[k] < 0) continue;  // uniform within the warp
+      const size_t uc = (size_t)u[k] * M.nch + c;
+      const int off = M.uc_off[uc], cnt = M.uc_cnt[uc];
+      // this lane's slots are off + lane + 32 j: column j of a slice (width
+      // cnt), or entry lane + 32 j of a long row's cnt slots
+      const bool is_long = M.units[u[k]].is_long != 0;
+      const int n_lane = is_long ? (cnt - lane + 31) / 32 : cnt;
+      const VT* vp = M.val + off + lane;
+      const uint16_t* ip = M.idx + off + lane;
+      constexpr int stride = 32;
+      int j = 0;
+      for (; j + 4 <= n_lane; j += 4) {
+        VT v[4];
+        int ii[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[q] = ld_stream(vp + (size_t)(j + q) * stride);
+          ii[q] = __ldg(ip + (size_t)(j + q) * stride);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (ii[q] != kChunkPadIdx) {
+            GV<GT, 1> g;
+            g.v[0] = s_g[ii[q]];
+            op.accum(acc[k], 0.0, v[q], g);
+          }
+      }
+      for (; j < n_lane; ++j) {
+        const int i = __ldg(ip + (size_t)j * stride);
+        if (i != kChunkPadIdx) {
+          GV<GT, 1> g;
+          g.v[0] = s_g[i];
+          op.accum(acc[k], 0.0, ld_stream(vp + (size_t)j * stride), g);
+        }
+      }
+    }
+  }
+  if constexpr (kPdl) grid_dep_launch();
+#pragma unroll
+  for (int k = 0; k < kChunkMaxUnits; ++k) {
+    if (u[k] < 0) continue;
+    const ChunkUnit U = M.units[u[k]];
+    if (U.is_long) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[k].add(acc[k].shfl_xor(0xffffffffu, off));
+      if (lane == 0) PF::epilogue(op, U.row0, acc[k], PF::get(op, U.row0), nullptr);
+    } else if (lane < U.nrows) {
+      const int r = U.row0 + lane;
+      PF::epilogue(op, r, acc[k], PF::get(op, r), nullptr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Epilogue operators
 // ---------------------------------------------------------------------------
 

@@ -643,6 +643,19 @@ struct pdhgc_lp {
     }
   } A, T;
   int ntA = 0, ntT = 0;  // blocks of one pass over A / A' (partials per quantity)
+  // the chunked primal pass over A' (ChunkPlan), per element size of the
+  // gathered vector: slot values are filled from the scaled matrix per solve
+  struct Chunked {
+    int nch = 0, chunk = 0, blocks = 0;
+    int64_t nslots = 0;
+    int* map = nullptr;
+    uint16_t* idx = nullptr;
+    ChunkUnit* units = nullptr;
+    int *uc_off = nullptr, *uc_cnt = nullptr, *warp_units = nullptr;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+  } ch64, ch32;
+  int chunked_primal = 0;  // 1: the Halpern loop's primal pass runs chunked (pdhgc_set_primal_layout)
   // vectors (internal order)
   double *b_int = nullptr, *sign = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
   int8_t* ge = nullptr;
@@ -738,6 +751,55 @@ int launch_tiles(pdhgc_lp* lp, bool transposed, bool scaled, const Op& op, doubl
   return PDHGC_OK;
 }
 
+// the primal pass over A' as the chunked kernel (ChunkPlan): one CTA per SM,
+// the gathered vector staged in shared memory chunk by chunk
+template <class Op>
+int launch_chunked(pdhgc_lp* lp, const Op& op, cudaStream_t st, bool pdl) {
+  using VT = typename Op::VT;
+  using GT = typename Op::GT;
+  const pdhgc_lp::Chunked& C = std::is_same<VT, float>::value ? lp->ch32 : lp->ch64;
+  ChunkMatT<VT> M;
+  if constexpr (std::is_same<VT, float>::value) {
+    M.val = C.val32;
+  } else {
+    M.val = C.val64;
+  }
+  M.idx = C.idx;
+  M.units = C.units;
+  M.uc_off = C.uc_off;
+  M.uc_cnt = C.uc_cnt;
+  M.warp_units = C.warp_units;
+  M.nch = C.nch;
+  M.chunk = C.chunk;
+  M.glen = lp->m;
+  const size_t smem = (size_t)C.chunk * sizeof(GT);  // the attribute is set at lp_create
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C.blocks);
+    cfg.blockDim = dim3(kChunkThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, spmv_chunked<Op, true>, M, op));
+  } else {
+    spmv_chunked<Op, false><<<C.blocks, kChunkThreads, smem, st>>>(M, op);
+  }
+  lp->launches++;
+  CKL();
+  return PDHGC_OK;
+}
+
+// the primal pass of the Halpern loop: chunked, or over the row segments
+template <class Op>
+int launch_primal(pdhgc_lp* lp, const Op& op, cudaStream_t st, bool pdl) {
+  if (lp->chunked_primal) return launch_chunked(lp, op, st, pdl);
+  return launch_tiles(lp, true, true, op, nullptr, st, pdl);
+}
+
 DevModel model_orig(const pdhgc_lp* lp) {
   return DevModel{lp->chat, lp->lhat, lp->uhat, lp->bhat, lp->Dr, lp->Dc, lp->ge};
 }
@@ -806,6 +868,12 @@ int convert_fp32(pdhgc_lp* lp, cudaStream_t st) {
   RET(to32(lp, lp->lhat, lp->lhat32, lp->n, st));
   RET(to32(lp, lp->uhat, lp->uhat32, lp->n, st));
   RET(to32(lp, lp->bhat, lp->bhat32, lp->m, st));
+  if (lp->ch32.nslots > 0) {  // the chunked pass's FP32 slots
+    k_sell_fill<<<grid_for(lp->ch32.nslots), 256, 0, st>>>(lp->ch32.map, lp->T.hat32, lp->ch32.val32,
+                                                          (int)lp->ch32.nslots);
+    lp->launches++;
+    CKL();
+  }
   return PDHGC_OK;
 }
 
@@ -836,6 +904,11 @@ int setup_scaling(pdhgc_lp* lp, const pdhgc_params& p) {
   for (const pdhgc_lp::Mat* M : {&lp->A, &lp->T}) {
     if (M->nslots == 0) continue;  // no nonzeros in SELL rows
     k_sell_fill<<<grid_for(M->nslots), 256, 0, st>>>(M->smap, M->hat, M->shat, M->nslots);
+    lp->launches++;
+  }
+  if (lp->ch64.nslots > 0) {  // the chunked pass's FP64 slots
+    k_sell_fill<<<grid_for(lp->ch64.nslots), 256, 0, st>>>(lp->ch64.map, lp->T.hat, lp->ch64.val64,
+                                                          (int)lp->ch64.nslots);
     lp->launches++;
   }
   k_scale_vectors<<<grid_for(m > n ? m : n), 256, 0, st>>>(m, n, lp->Dr, lp->Dc, lp->b_int, lp->c, lp->l,
@@ -945,12 +1018,12 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
     if (halpern && fp32) {
       const int last = pi.check_period - 1;
-      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
+      rc = launch_primal(lp, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, cs, true);
       if (rc == PDHGC_OK)
         rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
     } else if (halpern) {
       const int last = pi.check_period - 1;
-      rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, nullptr, cs, true);
+      rc = launch_primal(lp, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, cs, true);
       if (rc == PDHGC_OK)
         rc = launch_tiles(lp, false, true, DualOpH{lp->S, i, last, 0, lp->it.xbar, md, lp->it, hz}, nullptr, cs,
                           true);
@@ -1035,10 +1108,10 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
     // iteration), its check quantities, and the first chunk's weights
     if (fp32) {
       RET(launch_anchor(lp, md, 1, st));
-      RET(launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 0, 1, md32, h32_of(lp), hz}, nullptr, st));
+      RET(launch_primal(lp, PrimalOpH32{lp->S, 0, 0, 1, md32, h32_of(lp), hz}, st, false));
       RET(launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 0, 1, md32, h32_of(lp), hz}, nullptr, st));
     } else {
-      RET(launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, nullptr, st));
+      RET(launch_primal(lp, PrimalOpH{lp->S, 0, 0, 1, lp->it.y, md, lp->it, hz}, st, false));
       RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
     }
     RET(launch_eval_h(lp, md, st, false));
@@ -1176,6 +1249,52 @@ int setup_mat(pdhgc_lp* lp, pdhgc_lp::Mat& M, const Csr& C, cudaStream_t st) {
     k_sell_fill<<<grid_for((long long)ns), 256, 0, st>>>(M.smap, M.val, M.sval, (int)ns);
     lp->launches += 2;
     CKL();
+  }
+  return PDHGC_OK;
+}
+
+// uploads the chunked-pass plans of A' for FP64 and FP32 gathered vectors,
+// and lets the chunked kernels use a chunk of dynamic shared memory
+int setup_chunked(pdhgc_lp* lp, const Csr& T, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
+  for (int which = 0; which < 2; ++which) {
+    pdhgc_lp::Chunked& C = which ? lp->ch32 : lp->ch64;
+    ChunkPlan P;
+    plan_chunks(T, which ? kChunkElems32 : kChunkElems64, sms, P);
+    C.nch = P.nch;
+    C.chunk = P.chunk;
+    C.blocks = P.blocks;
+    C.nslots = P.nslots;
+    const size_t ns = (size_t)P.nslots, nu = (size_t)P.nunits;
+    RET(lp->alloc(&C.map, ns + kPad));
+    RET(lp->alloc(&C.idx, ns + kPad));
+    RET(lp->alloc(&C.units, nu + 1));
+    RET(lp->alloc(&C.uc_off, nu * P.nch + 1));
+    RET(lp->alloc(&C.uc_cnt, nu * P.nch + 1));
+    RET(lp->alloc(&C.warp_units, P.warp_units.size() + 1));
+    if (which)
+      RET(lp->alloc(&C.val32, ns + kPad));
+    else
+      RET(lp->alloc(&C.val64, ns + kPad));
+    if (ns) {
+      CK(cudaMemcpyAsync(C.map, P.slot_map.data(), ns * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(C.idx, P.slot_idx.data(), ns * 2, cudaMemcpyHostToDevice, st));
+    }
+    if (nu) {
+      CK(cudaMemcpyAsync(C.units, P.units.data(), nu * sizeof(ChunkUnit), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(C.uc_off, P.uc_off.data(), nu * P.nch * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(C.uc_cnt, P.uc_cnt.data(), nu * P.nch * 4, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(C.warp_units, P.warp_units.data(), P.warp_units.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // P's vectors go out of scope
   }
   return PDHGC_OK;
 }
@@ -1603,6 +1722,7 @@ int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int
   RET(setup_mat(lp.get(), lp->T, P.AT, st));
   lp->ntA = lp->A.nblocks();
   lp->ntT = lp->T.nblocks();
+  RET(setup_chunked(lp.get(), P.AT, st));
   RET(lp->alloc(&lp->err, 1));
   RET(lp->alloc(&lp->b_int, m));
   RET(lp->alloc(&lp->sign, m));
@@ -2136,6 +2256,12 @@ int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t
 
 int64_t pdhgc_kernel_launches(const pdhgc_lp* lp) { return lp ? lp->launches : 0; }
 
+int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked) {
+  if (!lp || (chunked != 0 && chunked != 1)) return set_err(PDHGC_ERR_INVALID_ARG, "chunked must be 0 or 1");
+  lp->chunked_primal = chunked;
+  return PDHGC_OK;
+}
+
 int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out) {
   if (!lp || !out) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
   const pdhgc_lp::Mat* mats[2] = {&lp->A, &lp->T};
@@ -2174,9 +2300,9 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     CK(cudaEventRecord(ev[3 * i], st));
     // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
     if (halpern && fp32)
-      rc = launch_tiles(lp, true, true, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, nullptr, st);
+      rc = launch_primal(lp, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, st, false);
     else if (halpern)
-      rc = launch_tiles(lp, true, true, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, nullptr, st);
+      rc = launch_primal(lp, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, st, false);
     else if (fp32)
       rc = launch_tiles(lp, true, true, PrimalOp32{lp->S, 0, lp->it32.y, md32, it32}, nullptr, st);
     else

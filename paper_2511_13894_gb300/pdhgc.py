@@ -108,6 +108,7 @@ _sig = {
     "pdhgc_get_iterates": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_layout": (C.c_int, [_vp, _vp]),
+    "pdhgc_set_primal_layout": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
     "pdhgc_kkt_eval": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp, C.POINTER(Report), _vp]),
@@ -269,6 +270,10 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    def set_primal_layout(self, chunked: bool):
+        """pdhgc_set_primal_layout: 0 gathers from global memory (default), 1 stages y in shared memory."""
+        _check(lib.pdhgc_set_primal_layout(self._h, int(bool(chunked))), "pdhgc_set_primal_layout")
 
     def get_layout(self):
         """pdhgc_get_layout: SpMV row-segment blocks of A and A'."""

@@ -7,7 +7,10 @@
 //   then f64 lb[n], f64 ub[n], int8 sense[m] when flagged
 // output: int64 rc; int64 detail length; detail bytes; then records
 //   int32 name length, name, int32 type (0 int32, 1 f64, 2 int8), int64 count, data
+// With two more arguments (chunk size, SM count) it also writes the chunked
+// pass's plan of A' (plan_chunks).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -54,7 +57,7 @@ void put_csr(FILE* f, const std::string& p, const pdhgc::Csr& c) {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 3) return 2;
+  if (argc != 3 && argc != 5) return 2;
   FILE* in = std::fopen(argv[1], "rb");
   if (!in) return 3;
   int64_t hdr[4];
@@ -99,6 +102,25 @@ int main(int argc, char** argv) {
     put(out, "norms", 1, norms, 2);
     put_csr(out, "A", P.A);
     put_csr(out, "AT", P.AT);
+    if (argc == 5) {
+      pdhgc::ChunkPlan C;
+      pdhgc::plan_chunks(P.AT, std::atoi(argv[3]), std::atoi(argv[4]), C);
+      const int32_t hdr2[4] = {C.chunk, C.nch, C.blocks, C.nunits};
+      put(out, "ch.hdr", 0, hdr2, 4);
+      std::vector<int32_t> units;
+      for (const pdhgc::ChunkUnit& u : C.units) {
+        units.push_back(u.row0);
+        units.push_back(u.nrows);
+        units.push_back(u.is_long);
+      }
+      put(out, "ch.units", 0, units.data(), (int64_t)units.size());
+      put(out, "ch.uc_off", 0, C.uc_off.data(), (int64_t)C.uc_off.size());
+      put(out, "ch.uc_cnt", 0, C.uc_cnt.data(), (int64_t)C.uc_cnt.size());
+      put(out, "ch.slot_map", 0, C.slot_map.data(), (int64_t)C.slot_map.size());
+      std::vector<int32_t> idx(C.slot_idx.begin(), C.slot_idx.end());
+      put(out, "ch.slot_idx", 0, idx.data(), (int64_t)idx.size());
+      put(out, "ch.warp_units", 0, C.warp_units.data(), (int64_t)C.warp_units.size());
+    }
   }
   std::fclose(out);
   return 0;

@@ -226,6 +226,37 @@ def test_halpern_fp32_bulk_corner_phase(name):
     assert np.all(x >= lp["lb"] - 1e-12 * np.abs(lp["lb"])) and np.all(x <= lp["ub"] + 1e-12 * np.abs(lp["ub"]))
 
 
+@pytest.mark.parametrize("name", ["power_law_skewed", "dense_lines", "bounded_ineq"])
+def test_halpern_primal_layouts_agree(name):
+    # the primal pass over the row segments with global gathers (the
+    # default) and with the gathered y staged in shared memory: the same
+    # iterates up to the summation order, both within 1e-10 of the oracle
+    lp = _lp_cases()[name]()
+    ref = oracle.run_iterations(lp, 100, HP)
+    s = ref["state"]
+    its = []
+    for chunked in (1, 0):
+        g = P.lp_from_dict(lp)
+        g.set_primal_layout(chunked)
+        rep = g.solve(max_iters=100, eps_rel=-1.0, algorithm=P.HALPERN)
+        assert rep["iters"] == 100 and rep["restarts"] == s.restarts
+        it = g.get_iterates()
+        assert rel_err(it["x"], s.x) <= ITER_TOL and rel_err(it["y"], s.y) <= ITER_TOL
+        its.append(it)
+    assert rel_err(its[0]["x"], its[1]["x"]) <= 1e-12 and rel_err(its[0]["y"], its[1]["y"]) <= 1e-12
+    # FP32 bulk: both layouts reach the tolerance in about the same iterations
+    reps = []
+    for chunked in (1, 0):
+        g = P.lp_from_dict(lp)
+        g.set_primal_layout(chunked)
+        reps.append(g.solve(algorithm=P.HALPERN, precision=P.FP32_BULK))
+    for r in reps:
+        assert r["status_name"] == "OPTIMAL" and r["rel_kkt"] <= 1e-6
+    assert abs(reps[0]["iters"] - reps[1]["iters"]) <= max(256, reps[1]["iters"] // 10)
+    with pytest.raises(P.PdhgcError, match="INVALID_ARG"):
+        P._check(P.lib.pdhgc_set_primal_layout(g._h, 2), "pdhgc_set_primal_layout")
+
+
 def test_halpern_profile_iteration_times_its_kernels():
     lp = lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000)
     g = P.lp_from_dict(lp)

@@ -45,7 +45,7 @@ def dump_exe(tmp_path_factory):
     return out
 
 
-def _run(exe, tmp_path, lp):
+def _run(exe, tmp_path, lp, chunk=None, sms=None):
     m, n = lp["m"], lp["n"]
     rp = np.asarray(lp["row_ptr"], dtype=np.int64)
     nnz = int(lp.get("nnz", rp[-1]))
@@ -62,7 +62,8 @@ def _run(exe, tmp_path, lp):
         for key, dt in (("lb", np.float64), ("ub", np.float64), ("sense", np.int8)):
             if lp.get(key) is not None:
                 np.asarray(lp[key], dtype=dt).tofile(f)
-    subprocess.run([exe, path_in, path_out], check=True)
+    extra = [str(chunk), str(sms)] if chunk is not None else []
+    subprocess.run([exe, path_in, path_out, *extra], check=True)
     data = open(path_out, "rb").read()
     rc = int(np.frombuffer(data, np.int64, 1, 0)[0])
     dl = int(np.frombuffer(data, np.int64, 1, 8)[0])
@@ -233,3 +234,109 @@ def test_invalid_inputs_get_their_error_codes(dump_exe, tmp_path, edit, code):
     edit(lp)
     rc, _ = _run(dump_exe, tmp_path, lp)
     assert rc == code
+
+
+def _chunk_constants():
+    src = open(os.path.join(CSRC, "host_prep.h")).read()
+    def get(name):  # an integer literal or a product of two
+        expr = re.search(rf"constexpr int {name} = ([0-9 *]+);", src).group(1)
+        out = 1
+        for f in expr.split("*"):
+            out *= int(f)
+        return out
+    return dict(threads=get("kChunkThreads"), maxu=get("kChunkMaxUnits"), long_len=get("kChunkLongLen"),
+                bytes=get("kChunkBytes"))
+
+
+def test_chunk_plan_matches_its_definition(dump_exe, tmp_path):
+    # the chunked primal pass's plan of A' with a small chunk (many chunks):
+    # every entry of A' sits in exactly one slot of its row's unit and its
+    # chunk, at its index within the chunk; padding slots are marked; every
+    # unit is on exactly one warp, at most kChunkMaxUnits per warp; the grid
+    # is a multiple of the SM count
+    KC = _chunk_constants()
+    lp = _layout_lp(3)
+    chunk, sms = 37, 3
+    rc, a = _run(dump_exe, tmp_path, lp, chunk, sms)
+    assert rc == 0
+    n, m = lp["n"], lp["m"]
+    C, nch, blocks, nunits = (int(v) for v in a["ch.hdr"])
+    assert C == chunk and nch == -(-m // chunk) and blocks % sms == 0
+    rp, col = a["AT.row_ptr"], a["AT.col"]
+    units = a["ch.units"].reshape(-1, 3)
+    assert units.shape[0] == nunits
+    # units cover the rows in order: long rows one each, then slices of 32
+    row = 0
+    for row0, nrows, is_long in units:
+        assert row0 == row
+        ln = rp[row0 + 1] - rp[row0]
+        if is_long:
+            assert nrows == 1 and ln > KC["long_len"]
+        else:
+            assert 1 <= nrows <= 32 and all(rp[r + 1] - rp[r] <= KC["long_len"] for r in range(row0, row0 + nrows))
+        row += nrows
+    assert row == n
+    smap, sidx = a["ch.slot_map"], a["ch.slot_idx"]
+    off = a["ch.uc_off"].reshape(nunits, nch)
+    cnt = a["ch.uc_cnt"].reshape(nunits, nch)
+    seen = np.zeros(len(col), dtype=np.int64)
+    for u, (row0, nrows, is_long) in enumerate(units):
+        for c in range(nch):
+            o, w = off[u, c], cnt[u, c]
+            if is_long:
+                e_in = [e for e in range(rp[row0], rp[row0 + 1]) if col[e] // chunk == c]
+                assert w == len(e_in) and list(smap[o:o + w]) == e_in
+                slots = range(o, o + w)
+            else:
+                widths = [sum(1 for e in range(rp[r], rp[r + 1]) if col[e] // chunk == c)
+                          for r in range(row0, row0 + nrows)]
+                assert w == max(widths)
+                slots = range(o, o + 32 * w)
+                for t in range(32):
+                    es = [smap[o + 32 * j + t] for j in range(w)]
+                    if t < nrows:
+                        want = [e for e in range(rp[row0 + t], rp[row0 + t + 1]) if col[e] // chunk == c]
+                        assert es[:len(want)] == want and all(x == -1 for x in es[len(want):])
+                    else:
+                        assert all(x == -1 for x in es)
+            for sl in slots:
+                e = smap[sl]
+                if e < 0:
+                    assert sidx[sl] == 0xFFFF
+                else:
+                    assert sidx[sl] == col[e] - c * chunk
+                    seen[e] += 1
+    assert np.all(seen == 1)
+    wu = a["ch.warp_units"].reshape(blocks * KC["threads"] // 32, KC["maxu"])
+    listed = wu[wu >= 0]
+    assert sorted(listed.tolist()) == list(range(nunits))
+
+
+def test_column_order_is_chunk_aware(dump_exe, tmp_path):
+    # with more rows than one FP64 chunk, columns of equal length are ordered
+    # by their entry counts in the first three chunks of the (internal) rows
+    rng = np.random.default_rng(7)
+    KC = _chunk_constants()
+    c64 = KC["bytes"] // 8
+    m, n = c64 * 3 + 500, 400
+    counts = rng.integers(1, 6, size=n)
+    rows = np.concatenate([rng.choice(m, size=k, replace=False) for k in counts])
+    cols = np.repeat(np.arange(n), counts)
+    order = np.lexsort((cols, rows))
+    rows, cols = rows[order], cols[order]
+    rp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=rp[1:])
+    lp = dict(m=m, n=n, row_ptr=rp, col_idx=cols.astype(np.int32), val=np.ones(len(cols)), b=np.zeros(m),
+              c=np.ones(n), lb=None, ub=None, sense=None)
+    rc, a = _run(dump_exe, tmp_path, lp)
+    assert rc == 0
+    rlen = np.diff(rp)
+    row_inv = a["row_inv"]
+    q = np.zeros((n, 3), dtype=np.int64)
+    for r, cc in zip(rows, cols):
+        k = row_inv[r] // c64
+        if k < 3:
+            q[cc, k] += 1
+    want = np.lexsort((np.arange(n), -q[:, 2], -q[:, 1], -q[:, 0], -counts))
+    assert np.array_equal(a["col_perm"], want)
+    assert np.array_equal(a["row_perm"], np.argsort(-rlen, kind="stable"))
