@@ -14,4 +14,5 @@ from .pdhg import (  # noqa: F401
     project_box, project_dual_cone, primal_residual, dual_objective, evaluate, kkt_omega,
     pdhg_step, restart_check, initial_omega, setup, solve, run_iterations, unscale,
     splitmix64, splitmix64_uniform, corner_metrics, kkt_report, corner_model, corner_phase,
+    dual_corner_model, dual_corner_phase,
 )

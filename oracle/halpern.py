@@ -57,6 +57,8 @@ def pdhg_map(model, x, y, tau, sigma):
     xbar = 2.0 * xp - x
     yp = y + sigma * (model.bhat - model.Ahat @ xbar)
     yp[model.ge] = np.maximum(yp[model.ge], 0.0)
+    if model.y_zero is not None:
+        yp[model.y_zero] = 0.0
     return xp, yp
 
 
@@ -261,4 +263,51 @@ def corner_phase(phase1, corner_params=None, hold=None):
             s.r_prev = s.r
     return dict(status=status, iters=s.k, restarts=s.restarts, state=s, corner_model=cm,
                 model=model, info=info, x_hat=x_corner, y_hat=y1.copy(),
+                seconds=time.perf_counter() - t0)
+
+
+def dual_corner_phase(phase1, corner_params=None):
+    """The dual corner push (oracle.pdhg.dual_corner_model) with the Halpern
+    loop: a fresh anchor at (proj(0), y1) (y1 = 0 on rows whose dual is
+    fixed), its residual measured, omega_0 from the new b' and the PID state
+    reset; stop once k >= min_iters and the dual residual of the PDHG output
+    of a check meets eps_rel (1 + ||c||) (or the full test with stop_rule
+    "kkt"); on a limit the phase-1 y is kept."""
+    cp = dict(P.CORNER_DEFAULTS)
+    if corner_params:
+        cp.update(corner_params)
+    model = phase1["model"]
+    p = dict(phase1["params"])
+    eta = phase1["eta"]
+    x1, y1 = phase1["x_hat"], phase1["y_hat"]
+    dm, info = P.dual_corner_model(model, x1, y1, cp)
+    y0 = np.where(dm.y_zero, 0.0, y1)
+    s = HState(dm, P.project_box(np.zeros(model.n), dm.lhat, dm.uhat), y0, eta, P.initial_omega(dm))
+    t0 = time.perf_counter()
+    nc = float(np.linalg.norm(model.c_user))
+    status, y_out = None, None
+    while status is None:
+        x_pre, y_pre = halpern_step(dm, s, p["reflection"])
+        at_check = s.k % p["check_period"] == 0
+        at_limit = s.k >= cp["max_iters"]
+        if not (at_check or at_limit):
+            continue
+        ev = P.evaluate(dm, s.xp, s.yp, s.omega)
+        s.r = fixed_point_residual(dm, x_pre, y_pre, s.xp, s.yp, s.tau, s.sigma)
+        if at_check and s.k >= cp["min_iters"]:
+            done = (ev["rel_kkt"] <= cp["eps_rel"] if cp["stop_rule"] == "kkt"
+                    else ev["rD2"] <= cp["eps_rel"] * (1.0 + nc))
+            if done:
+                status, y_out = P.CORNER_DONE, s.yp.copy()
+                break
+        if (at_limit or not (np.isfinite(ev["kkt"]) and np.isfinite(s.r))
+                or time.perf_counter() - t0 > cp["time_limit_s"]):
+            status, y_out = P.CORNER_LIMIT, y1.copy()
+            break
+        if restart_due(s.r, s.r0, s.r_prev, s.t, s.k, p):
+            apply_restart(dm, s, p, s.r)
+        else:
+            s.r_prev = s.r
+    return dict(status=status, iters=s.k, restarts=s.restarts, state=s, dual_model=dm,
+                model=model, info=info, x_hat=x1.copy(), y_hat=y_out,
                 seconds=time.perf_counter() - t0)

@@ -116,6 +116,9 @@ class Model:
         self.set_objective(self.c_user)
         self.lhat = self.l / self.Dc
         self.uhat = self.u / self.Dc
+        # rows whose dual is fixed at 0 (the dual corner model's inactive
+        # inequality rows; None: no such row)
+        self.y_zero = None
 
     def set_objective(self, c_user):
         self.c_cur = np.asarray(c_user, dtype=np.float64)
@@ -226,6 +229,8 @@ def evaluate(model: Model, x, y, omega):
     r_D = r_D_hat / D_c, objectives (scale invariant) and the three ratios."""
     Ax = model.Ahat @ x
     rp = primal_residual(model.bhat, Ax, model.ge)
+    if model.y_zero is not None:
+        rp[model.y_zero] = 0.0  # a row whose dual is fixed at 0 constrains nothing
     lam = model.chat - model.AhatT @ y
     z = project_dual_cone(lam, model.lhat, model.uhat)
     rd = lam - z
@@ -303,6 +308,8 @@ def pdhg_step(model: Model, s: State):
     x_bar = 2.0 * x_new - s.x
     y_new = s.y + s.sigma * (model.bhat - model.Ahat @ x_bar)
     y_new[model.ge] = np.maximum(y_new[model.ge], 0.0)
+    if model.y_zero is not None:
+        y_new[model.y_zero] = 0.0
     s.x, s.y = x_new, y_new
     s.sum_x += x_new
     s.sum_y += y_new
@@ -620,4 +627,110 @@ def corner_phase(phase1, corner_params=None, hold=None):
         restart_check(cm, s, p, ev_cur, ev_avg)
     return dict(status=status, iters=s.k, restarts=s.restarts, state=s, corner_model=cm,
                 model=model, info=info, x_hat=x_corner, y_hat=y1.copy(),
+                seconds=time.perf_counter() - t0)
+
+
+# ---------------------------------------------------------------------------
+# The dual corner push (Section 6, Discussion): Algorithm 1 read for the dual
+# ---------------------------------------------------------------------------
+
+def dual_corner_model(model: Model, x_hat1, y_hat1, cp):
+    """The model whose PDHG run pushes the dual toward a vertex of the dual
+    optimal face, in scaled space.  Section 6 proposes reducing the dual
+    superbasics "with similar techniques" and gives no construction; this is
+    the reading (each step is the dual counterpart of a step of Algorithm 1):
+
+    * Columns (complementary slackness with the phase-1 x, tolerance eps_abs
+      in user space): the lower bound stays where x_j is within eps_abs of a
+      finite l_j, else it is removed (l_j -> -inf); likewise the upper bound.
+      A column strictly inside its bounds becomes free, which forces z_j = 0
+      in the dual (Algorithm 1 fixes primal variables where z_j != 0; this
+      frees them where x_j is off its bounds so that z_j is fixed at 0).
+    * Rows: an inequality row whose slack (A_int x - b_int)_i exceeds eps_abs
+      is inactive at x, so its dual is fixed at 0 (y_zero); every other row
+      keeps its sense.
+    * Objective: the dual objective becomes b' = obj_scale * U[0,1)^m, drawn
+      per user row with SplitMix64 (seed obj_seed), in user space, then
+      negated on '<' rows and scaled by D_r like b (the counterpart of
+      Algorithm 1's random primal objective); c is unchanged.  Rows with a
+      fixed dual get b'_i = 0 (they constrain nothing).
+    On the optimal face every dual-feasible point of this model is dual
+    optimal for the original LP, so maximising the random b' drives the dual
+    to a vertex of the dual optimal face: at least m zero reduced costs."""
+    x1 = model.Dc * x_hat1
+    dm = model.copy()
+    eps = cp["eps_abs"]
+    keep_l = np.isfinite(model.l) & (x1 - model.l <= eps)
+    keep_u = np.isfinite(model.u) & (model.u - x1 <= eps)
+    dm.l = np.where(keep_l, model.l, -np.inf)
+    dm.u = np.where(keep_u, model.u, np.inf)
+    dm.lhat = dm.l / model.Dc
+    dm.uhat = dm.u / model.Dc
+    slack = model.A_int @ x1 - model.b_int
+    y_zero = model.ge & (slack > eps)
+    dm.y_zero = y_zero
+    b_new = cp["obj_scale"] * splitmix64_uniform(cp["obj_seed"], model.m)
+    b_new = np.where(y_zero, 0.0, b_new)
+    dm.b_user = b_new
+    dm.b_int = model.sign * b_new
+    dm.bhat = model.Dr * dm.b_int
+    return dm, dict(freed=int((~keep_l & ~keep_u).sum()), kept_lower=int(keep_l.sum()),
+                    kept_upper=int(keep_u.sum()), rows_zero=int(y_zero.sum()), y_zero=y_zero)
+
+
+def dual_corner_phase(phase1, corner_params=None):
+    """The dual corner push on the phase-1 result: build the model of
+    dual_corner_model, run PDHG from (proj(0), y1) with y1 = 0 on the rows
+    whose dual is fixed (reading: Algorithm 1 keeps the pushed primal point
+    and restarts the dual at 0; here the dual is pushed, so y1 is kept and
+    the primal restarts at proj(0)), the same step size and omega_0 from the
+    new b'; stop once k >= min_iters and the dual residual of the current
+    (else the average) point meets eps_rel (1 + ||c||) on that model,
+    checked every check period (the dual counterpart of Section 3.1's rule;
+    stop_rule "kkt": the full test, for tests); return (x1, y_hat, z_hat) with
+    phase 1's x.  On a limit the phase-1 y is kept.  A phase 1 run with the
+    Halpern loop continues with it (oracle.halpern.dual_corner_phase)."""
+    if phase1["params"].get("algorithm", "averaged") == "halpern":
+        from . import halpern
+        return halpern.dual_corner_phase(phase1, corner_params)
+    cp = dict(CORNER_DEFAULTS)
+    if corner_params:
+        cp.update(corner_params)
+    model = phase1["model"]
+    p = dict(phase1["params"])
+    eta = phase1["eta"]
+    x1, y1 = phase1["x_hat"], phase1["y_hat"]
+    dm, info = dual_corner_model(model, x1, y1, cp)
+    y0 = np.where(dm.y_zero, 0.0, y1)
+    s = State(dm, project_box(np.zeros(model.n), dm.lhat, dm.uhat), y0, eta, initial_omega(dm))
+    t0 = time.perf_counter()
+    nc = float(np.linalg.norm(model.c_user))
+    status, y_out = None, None
+    while status is None:
+        pdhg_step(dm, s)
+        at_check = s.k % p["check_period"] == 0
+        at_limit = s.k >= cp["max_iters"]
+        if not (at_check or at_limit):
+            continue
+        xa, ya = s.average()
+        ev_cur = evaluate(dm, s.x, s.y, s.omega)
+        ev_avg = evaluate(dm, xa, ya, s.omega)
+        if at_check and s.k >= cp["min_iters"] and cp["stop_rule"] == "kkt":
+            if min(ev_cur["rel_kkt"], ev_avg["rel_kkt"]) <= cp["eps_rel"]:
+                status = CORNER_DONE
+                y_out = ya if _pick(ev_cur, ev_avg) == "avg" else s.y.copy()
+                break
+        elif at_check and s.k >= cp["min_iters"]:
+            if ev_cur["rD2"] <= cp["eps_rel"] * (1.0 + nc):
+                status, y_out = CORNER_DONE, s.y.copy()
+                break
+            if ev_avg["rD2"] <= cp["eps_rel"] * (1.0 + nc):
+                status, y_out = CORNER_DONE, ya
+                break
+        if at_limit or time.perf_counter() - t0 > cp["time_limit_s"]:
+            status, y_out = CORNER_LIMIT, y1.copy()   # the phase-1 dual is kept on a limit
+            break
+        restart_check(dm, s, p, ev_cur, ev_avg)
+    return dict(status=status, iters=s.k, restarts=s.restarts, state=s, dual_model=dm,
+                model=model, info=info, x_hat=x1.copy(), y_hat=y_out,
                 seconds=time.perf_counter() - t0)
