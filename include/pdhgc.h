@@ -66,6 +66,7 @@ extern "C" {
 
 #define PDHGC_PHASE1  0
 #define PDHGC_CORNER  1
+#define PDHGC_DUAL_CORNER 2  /* the dual corner push's result (pdhgc_dual_corner_phase) */
 
 /* ---- inner loop (pdhgc_params.algorithm) ---------------------------------
  * PDHGC_ALG_AVERAGED: cuPDLP.jl-style restarted PDHG; restarts compare the
@@ -220,14 +221,18 @@ int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_re
 
 /*
  * pdhgc_kkt_report — residuals, objectives, Section 2 ratios and the
- * Section 2.1 / 4.2 metrics of the PHASE1 or CORNER solution on the
- * original model, computed on the device.
+ * Section 2.1 / 4.2 metrics of the PHASE1, CORNER or DUAL_CORNER solution
+ * on the original model, computed on the device.  Errors: INVALID_ARG,
+ * NO_PHASE1, NO_CORNER (that phase has not run since the last pdhgc_solve).
  */
 int pdhgc_kkt_report(pdhgc_lp* lp, int which, pdhgc_report* out);
 
 /*
- * pdhgc_get_solution — x (n), y (m), z (n) of the PHASE1 or CORNER
- * solution in the user's order and scale.  Any of the three may be NULL.
+ * pdhgc_get_solution — x (n), y (m), z (n) of the PHASE1, CORNER or
+ * DUAL_CORNER solution in the user's order and scale (CORNER: the corner x
+ * with phase 1's y and z; DUAL_CORNER: phase 1's x with the dual corner
+ * phase's y and its z).  Any of the three may be NULL.  Errors as
+ * pdhgc_kkt_report.
  */
 int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z, int on_device);
 
@@ -339,6 +344,37 @@ int pdhgc_kkt_eval_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row
 int pdhgc_uniform(uint64_t seed, int64_t n, double obj_scale, double* out, void* cuda_stream);
 
 /* ---- batched solve: many independent LPs in one persistent launch ------- */
+
+/*
+ * pdhgc_dual_corner_phase — the dual corner push: the dual counterpart of
+ * Algorithm 1 that Section 6 (Discussion) proposes for the dual superbasics
+ * (the paper gives no construction; this is the reading).  From the phase-1
+ * point (x1, y1, z1), complementary slackness decides, in user space: of a
+ * pair (the distance of x_j from a bound, the part of z_j that bound
+ * allows) or (an inequality row's slack, |y_i|) the first is read as
+ * nonzero when it exceeds both eps_abs and the second;
+ *   - a bound is removed where x1 is off it in that sense, so a column
+ *     strictly inside its bounds becomes free, which fixes its reduced cost
+ *     at 0 (the counterpart of fixing x_j where z_j != 0);
+ *   - an inequality row whose slack is nonzero in that sense has its dual
+ *     fixed at 0 (an inactive row);
+ *   - the dual objective becomes b' = obj_scale U[0,1)^m (SplitMix64 of
+ *     obj_seed per user row, negated on '<' rows, scaled like b); c stays.
+ * PDHG then runs from (proj(0), y1) in the phase-1 inner loop and precision,
+ * with omega_0 = ||c_hat|| / ||b_hat'||, and stops at a check once k >=
+ * min_iters and the dual residual of the model meets eps_rel (1 + ||c||)
+ * (stop_rule 0, the counterpart of Section 3.1's primal rule) or the full
+ * Section 2 test holds (stop_rule 1); on a limit y1 is kept
+ * (PDHGC_STATUS_CORNER_LIMIT).  The result is (x1, y, z): phase 1's x with
+ * the new dual, read with which = PDHGC_DUAL_CORNER.  On the optimal face a
+ * converged run ends at a vertex of the dual optimal face (at least m zero
+ * reduced costs, dual push estimate 0); the 1e-6 count of zero reduced costs
+ * registers it only once the phase has converged beyond 1e-6 (eps_rel, e.g.
+ * 1e-9, with stop_rule 1).  Uses corner params eps_abs, eps_rel, min_iters,
+ * max_iters, time_limit_s, obj_seed, obj_scale, stop_rule; row_rule and
+ * omega_rule must be 0.  Errors: NO_PHASE1, INVALID_ARG, CUDA, OOM.
+ */
+int pdhgc_dual_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_report* out);
 
 /*
  * pdhgc_batch_create — `count` LPs, each as for pdhgc_lp_create, given by

@@ -640,15 +640,22 @@ def dual_corner_model(model: Model, x_hat1, y_hat1, cp):
     superbasics "with similar techniques" and gives no construction; this is
     the reading (each step is the dual counterpart of a step of Algorithm 1):
 
-    * Columns (complementary slackness with the phase-1 x, tolerance eps_abs
-      in user space): the lower bound stays where x_j is within eps_abs of a
-      finite l_j, else it is removed (l_j -> -inf); likewise the upper bound.
-      A column strictly inside its bounds becomes free, which forces z_j = 0
-      in the dual (Algorithm 1 fixes primal variables where z_j != 0; this
-      frees them where x_j is off its bounds so that z_j is fixed at 0).
-    * Rows: an inequality row whose slack (A_int x - b_int)_i exceeds eps_abs
-      is inactive at x, so its dual is fixed at 0 (y_zero); every other row
-      keeps its sense.
+    * Complementary slackness with the phase-1 point decides (user space,
+      tolerance eps_abs): of a complementary pair (the distance of x_j from
+      a bound and the part of z_j that bound allows, or an inequality row's
+      slack and |y_i|) the first is read as nonzero when it exceeds both
+      eps_abs and the second.  A phase-1 point meets the tolerances only
+      approximately, and a pair of two small numbers (an active row with a
+      slack of 1.4e-6 and a dual of 0.47, say) must not be read as inactive:
+      that would fix a dual the optimal face needs and leave the model's
+      dual empty.
+    * Columns: a bound is removed (l_j -> -inf, u_j -> +inf) where x_j is
+      off it in that sense, so a column strictly inside its bounds becomes
+      free and its reduced cost is fixed at 0 (Algorithm 1 fixes primal
+      variables where z_j != 0; this frees them where x_j is off its bounds).
+    * Rows: an inequality row whose slack (A_int x - b_int)_i is nonzero in
+      that sense is inactive, and its dual is fixed at 0 (y_zero); every
+      other row keeps its sense.
     * Objective: the dual objective becomes b' = obj_scale * U[0,1)^m, drawn
       per user row with SplitMix64 (seed obj_seed), in user space, then
       negated on '<' rows and scaled by D_r like b (the counterpart of
@@ -657,17 +664,20 @@ def dual_corner_model(model: Model, x_hat1, y_hat1, cp):
     On the optimal face every dual-feasible point of this model is dual
     optimal for the original LP, so maximising the random b' drives the dual
     to a vertex of the dual optimal face: at least m zero reduced costs."""
-    x1 = model.Dc * x_hat1
+    x1, y1, z1 = unscale(model, x_hat1, y_hat1)
     dm = model.copy()
     eps = cp["eps_abs"]
-    keep_l = np.isfinite(model.l) & (x1 - model.l <= eps)
-    keep_u = np.isfinite(model.u) & (model.u - x1 <= eps)
+    dl, du = x1 - model.l, model.u - x1
+    off_l = (dl > eps) & (dl > np.maximum(z1, 0.0))
+    off_u = (du > eps) & (du > np.maximum(-z1, 0.0))
+    keep_l = np.isfinite(model.l) & ~off_l
+    keep_u = np.isfinite(model.u) & ~off_u
     dm.l = np.where(keep_l, model.l, -np.inf)
     dm.u = np.where(keep_u, model.u, np.inf)
     dm.lhat = dm.l / model.Dc
     dm.uhat = dm.u / model.Dc
     slack = model.A_int @ x1 - model.b_int
-    y_zero = model.ge & (slack > eps)
+    y_zero = model.ge & (slack > eps) & (slack > np.abs(y1))
     dm.y_zero = y_zero
     b_new = cp["obj_scale"] * splitmix64_uniform(cp["obj_seed"], model.m)
     b_new = np.where(y_zero, 0.0, b_new)

@@ -9,7 +9,7 @@ before the library exists.
 
 _EXPORTS = {"lp_create", "lp_from_dict", "LP", "Batch", "Guide", "uniform", "probe_gather",
             "default_params", "default_corner_params", "Params", "CornerParams", "Report", "PdhgcError",
-            "FP64", "FP32_BULK", "AVERAGED", "HALPERN", "PHASE1", "CORNER", "STATUS_NAMES", "lib"}
+            "FP64", "FP32_BULK", "AVERAGED", "HALPERN", "PHASE1", "CORNER", "DUAL_CORNER", "STATUS_NAMES", "lib"}
 
 
 def __getattr__(name):

@@ -31,7 +31,7 @@ struct Scalars {
   int check_period, phase, stop_rule, done, status, chosen, restart_to;
   int at_check, at_limit, pi_zero, error;
   // last evaluation of the current (0) and average (1) point
-  double kkt[2], rel_p[2], rel_d[2], rel_gap[2], rel_kkt[2], rP2[2];
+  double kkt[2], rel_p[2], rel_d[2], rel_gap[2], rel_kkt[2], rP2[2], rD2[2];
   // Halpern loop (algorithm == PDHGC_ALG_HALPERN): reflection, PID gains,
   // fixed-point residual of the last check, of the anchor and of the
   // previous check in this epoch, PID integral and last error
@@ -40,6 +40,11 @@ struct Scalars {
   double fpr, fpr0, fpr_prev, pid_int, pid_eprev;
 };
 
+
+// DevModel::ge: 0 for an '=' row, 1 for a '>' row (y >= 0), kRowDualZero for
+// a row whose dual is fixed at 0 (the dual corner push's inactive rows: the
+// projection returns y = 0 and the row's primal residual counts as 0)
+constexpr int8_t kRowDualZero = 2;
 
 struct DevModel {
   const double* chat;
@@ -162,6 +167,7 @@ __device__ inline void decide_step(Scalars* S, const double* q, int mode) {
     gap[w] = pobj - dobj;
     S->kkt[w] = sqrt(om * nrp2[w] + nrd2[w] / om + gap[w] * gap[w]);
     S->rP2[w] = rP2;
+    S->rD2[w] = rD2;
     S->rel_p[w] = rP2 / (1.0 + S->nb);
     S->rel_d[w] = rD2 / (1.0 + S->nc);
     S->rel_gap[w] = fabs(gap[w]) / (1.0 + fabs(pobj) + fabs(dobj));
@@ -191,9 +197,16 @@ __device__ inline void decide_step(Scalars* S, const double* q, int mode) {
       S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 0;
     } else if (S->at_check && S->k >= S->min_iters) {
       const double tol = S->eps_rel * (1.0 + S->nb);
+      const double tol_d = S->eps_rel * (1.0 + S->nc);
       if (S->stop_rule == 1) {
         if (fmin(S->rel_kkt[0], S->rel_kkt[1]) <= S->eps_rel) {
           S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = pick;
+        }
+      } else if (S->stop_rule == 2) {  // the dual corner push: the dual residual regained
+        if (S->rD2[0] <= tol_d) {
+          S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 0;
+        } else if (S->rD2[1] <= tol_d) {
+          S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 1;
         }
       } else if (S->rP2[0] <= tol) {
         S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 0;
@@ -246,6 +259,8 @@ __device__ inline void decide_halpern(Scalars* S, const double* q, int mode) {
   const double pobj = cx, dobj = by + bnd, gap = pobj - dobj;
   S->kkt[0] = sqrt(om * nrp2 + nrd2 / om + gap * gap);
   S->rP2[0] = rP2;
+  S->rD2[0] = rD2;
+  S->rD2[1] = rD2;
   S->rel_p[0] = rP2 / (1.0 + S->nb);
   S->rel_d[0] = rD2 / (1.0 + S->nc);
   S->rel_gap[0] = fabs(gap) / (1.0 + fabs(pobj) + fabs(dobj));
@@ -280,7 +295,9 @@ __device__ inline void decide_halpern(Scalars* S, const double* q, int mode) {
     if (!finite) {
       S->done = 1; S->status = PDHGC_STATUS_CORNER_LIMIT; S->chosen = 2;
     } else if (S->at_check && S->k >= S->min_iters) {
-      const bool met = S->stop_rule == 1 ? S->rel_kkt[0] <= S->eps_rel : rP2 <= S->eps_rel * (1.0 + S->nb);
+      const bool met = S->stop_rule == 1   ? S->rel_kkt[0] <= S->eps_rel
+                       : S->stop_rule == 2 ? rD2 <= S->eps_rel * (1.0 + S->nc)
+                                           : rP2 <= S->eps_rel * (1.0 + S->nb);
       if (met) {
         S->done = 1; S->status = PDHGC_STATUS_CORNER_DONE; S->chosen = 2;
       }
@@ -807,12 +824,13 @@ struct DualOp {
   __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   struct Pre {
     double b, y, sy, sigma;
-    bool ge;
+    int8_t ge;
   };
-  __device__ Pre prefetch(int i) const { return Pre{md.bhat[i], w.y[i], w.sum_y[i], S->sigma, md.ge[i] != 0}; }
+  __device__ Pre prefetch(int i) const { return Pre{md.bhat[i], w.y[i], w.sum_y[i], S->sigma, md.ge[i]}; }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     double yn = p.y + p.sigma * (p.b - a.v[0]);
-    if (p.ge && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
+    // y >= 0 on '>' rows (sign bit test); y = 0 on a row whose dual is fixed
+    if (p.ge && (p.ge == kRowDualZero || __double_as_longlong(yn) < 0)) yn = 0.0;
     w.sum_y[i] = p.sy + yn;
     w.y[i] = yn;
   }
@@ -845,12 +863,12 @@ struct EvalRowsOp {
   __device__ void epilogue(int i, const Acc& a, double* part) const {
     const double inv_t = S->inv_t;
     const double b = md.bhat[i], dr = md.Dr[i];
-    const bool ge = md.ge[i];
+    const int8_t ge = md.ge[i];
 #pragma unroll
     for (int wv = 0; wv < 2; ++wv) {
       const double ax = wv == 0 ? a.v[0] : a.v[1] * inv_t;
       double r = b - ax;
-      if (ge) r = fmax(r, 0.0);
+      if (ge) r = ge == kRowDualZero ? 0.0 : fmax(r, 0.0);
       const double ru = r / dr;
       const double yw = wv == 0 ? y[i] : sum_y[i] * inv_t;
       const double d = yw - y_r[i];
@@ -985,15 +1003,16 @@ struct DualOpH {
   __device__ void accum(Acc& a, double, double v, const GV<double, 1>& g) const { a.v[0] = fma(v, g.v[0], a.v[0]); }
   struct Pre {
     double b, y, y0, sigma, wt, rho;
-    bool ge, last;
+    int8_t ge;
+    bool last;
   };
   __device__ Pre prefetch(int i) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{md.bhat[i], w.y[i], w.y_r[i], S->sigma, h.hw[it], S->rho, md.ge[i] != 0, last};
+    return Pre{md.bhat[i], w.y[i], w.y_r[i], S->sigma, h.hw[it], S->rho, md.ge[i], last};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     double yn = p.y + p.sigma * (p.b - a.v[0]);
-    if (p.ge && __double_as_longlong(yn) < 0) yn = 0.0;  // y >= 0 on '>' rows (sign bit test)
+    if (p.ge && (p.ge == kRowDualZero || __double_as_longlong(yn) < 0)) yn = 0.0;
     if (!probe) {
       const double r = p.rho == 1.0 ? fma(2.0, yn, -p.y) : fma(p.rho, yn - p.y, yn);
       w.y[i] = fma(p.wt, r - p.y0, p.y0);
@@ -1029,7 +1048,7 @@ struct EvalRowsH {
   __device__ void epilogue(int i, const Acc& a, double* part) const {
     const double b = md.bhat[i], dr = md.Dr[i];
     double r = b - a.v[0];
-    if (md.ge[i]) r = fmax(r, 0.0);
+    if (md.ge[i]) r = md.ge[i] == kRowDualZero ? 0.0 : fmax(r, 0.0);
     const double ru = r / dr;
     const double yp = h.yp[i], dy = h.dy[i];
     const double d = yp - y_r[i];
@@ -1473,18 +1492,18 @@ struct DualOp32 {
   __device__ void accum(Acc& a, double, float v, const GV<float, 1>& g) const { ff_fma(a, v, g.v[0]); }
   struct Pre {
     float b, y, yl, sigma;
-    bool ge;
+    int8_t ge;
     float2 sy;
   };
   __device__ Pre prefetch(int i) const {
-    return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, md.ge[i] != 0, w.sum_y[i]};
+    return Pre{md.bhat[i], w.y[i], w.ylo[i], (float)S->sigma, md.ge[i], w.sum_y[i]};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     const float r = (p.b - a.hi[0]) - a.lo[0];
     float yh = p.y, yl = p.yl;
     ff_axpy(yh, yl, p.sigma, r);
-    // y >= 0 on '>' rows: a negative pair projects to (0, 0)
-    if (p.ge && (yh < 0.0f || (yh == 0.0f && yl < 0.0f))) {
+    // y >= 0 on '>' rows: a negative pair projects to (0, 0); y = 0 where fixed
+    if (p.ge && (p.ge == kRowDualZero || yh < 0.0f || (yh == 0.0f && yl < 0.0f))) {
       yh = 0.0f;
       yl = 0.0f;
     }
@@ -1700,18 +1719,20 @@ struct DualOpH32 {
   struct Pre {
     float y, yl, sigma, s, rho;
     float2 r0, y0;
-    bool ge, last;
+    int8_t ge;
+    bool last;
   };
   __device__ Pre prefetch(int i) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{w.y[i], w.ylo[i], (float)S->sigma, h.hs[it], (float)S->rho, w.r0[i], w.ya[i], md.ge[i] != 0, last};
+    return Pre{w.y[i], w.ylo[i], (float)S->sigma, h.hs[it], (float)S->rho, w.r0[i], w.ya[i], md.ge[i], last};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     // r = b_hat - A_hat x_bar = r0 - A_hat gx
     const float r = (p.r0.x - a.hi[0]) + (p.r0.y - a.lo[0]);
     float th = p.y, tl = p.yl;
     ff_axpy(th, tl, p.sigma, r);
-    if (p.ge && (th < 0.0f || (th == 0.0f && tl < 0.0f))) {  // y >= 0 on '>' rows
+    // y >= 0 on '>' rows; y = 0 on a row whose dual is fixed
+    if (p.ge && (p.ge == kRowDualZero || th < 0.0f || (th == 0.0f && tl < 0.0f))) {
       th = 0.0f;
       tl = 0.0f;
     }

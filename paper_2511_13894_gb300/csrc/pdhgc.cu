@@ -175,7 +175,8 @@ struct Iter32 {
   float2* r0;
 };
 
-__global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32) {
+__global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const double* x_start, Iter32 w32,
+                                const double* y_start = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double x0 = x_start ? x_start[i] : fmin(fmax(0.0, md.lhat[i]), md.uhat[i]);
@@ -193,15 +194,17 @@ __global__ void k_init_iterates(int n, int m, DevModel md, DevIter w, const doub
     }
   }
   if (i < m) {
-    w.y[i] = 0.0;
-    w.y_r[i] = 0.0;
+    const double y0 = y_start ? y_start[i] : 0.0;
+    w.y[i] = y0;
+    w.y_r[i] = y0;
     w.sum_y[i] = 0.0;
     if (w32.y) {
-      w32.y[i] = 0.0f;
-      w32.ylo[i] = 0.0f;
+      const float h = (float)y0, lo = (float)(y0 - (double)h);
+      w32.y[i] = h;
+      w32.ylo[i] = lo;
       w32.sy[i] = make_float2(0.f, 0.f);
-      w32.ya[i] = make_float2(0.f, 0.f);
-      w32.gy[i] = 0.0f;
+      w32.ya[i] = make_float2(h, lo);
+      w32.gy[i] = 0.0f;  // y = y_0
     }
   }
 }
@@ -236,6 +239,7 @@ struct PhaseInit {
   long long max_iters, min_iters;
   int check_period, phase, stop_rule;
   int use_cc2;  // corner: primal weight from ||c_hat'|| (cc2[0]) and ||c'|| (cc2[1])
+  int use_bb2;  // dual corner: primal weight from ||b_hat'|| (cc2[2])
   int algorithm;  // PDHGC_ALG_*
   double rho, pid_kp, pid_ki, pid_kd;  // Halpern loop
   double omega0;  // > 0: the starting primal weight (corner omega_rule 1); else from ||c_hat|| / ||b_hat||
@@ -252,12 +256,13 @@ __global__ void k_init_scalars(Scalars* S, PhaseInit pi, const double* cc2) {
   S->nb = pi.nb;
   S->nc = pi.use_cc2 ? sqrt(cc2[1]) : pi.nc;
   const double nch = pi.use_cc2 ? sqrt(cc2[0]) : S->nc_hat;
+  const double nbh = pi.use_bb2 ? sqrt(cc2[2]) : S->nb_hat;
   S->max_iters = pi.max_iters;
   S->min_iters = pi.min_iters;
   S->check_period = pi.check_period;
   S->phase = pi.phase;
   S->stop_rule = pi.stop_rule;
-  S->omega = pi.omega0 > 0.0 ? pi.omega0 : ((nch > 1e-10 && S->nb_hat > 1e-10) ? nch / S->nb_hat : 1.0);
+  S->omega = pi.omega0 > 0.0 ? pi.omega0 : ((nch > 1e-10 && nbh > 1e-10) ? nch / nbh : 1.0);
   S->tau = S->eta / S->omega;
   S->sigma = S->eta * S->omega;
   S->k = 0;
@@ -475,7 +480,7 @@ __global__ void k_ring_init(int n, const double* __restrict__ x, RingRec rr) {
 // (chosen 2, Halpern loop: the PDHG output T(z) of the last check)
 __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo, double* yo,
                            const double* x_fallback, const double* __restrict__ lhat,
-                           const double* __restrict__ uhat, DevHalpern hz) {
+                           const double* __restrict__ uhat, DevHalpern hz, const double* y_fallback = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool out = S->chosen == 2;
   const bool avg = S->chosen == 1 && S->t > 0;
@@ -485,7 +490,10 @@ __global__ void k_finalize(const Scalars* S, int n, int m, DevIter w, double* xo
     const double xv = out ? hz.xp[i] : (avg ? w.sum_x[i] * inv_t : w.x[i]);
     xo[i] = fallback ? x_fallback[i] : fmin(fmax(xv, lhat[i]), uhat[i]);
   }
-  if (yo && i < m) yo[i] = out ? hz.yp[i] : (avg ? w.sum_y[i] * inv_t : w.y[i]);
+  if (yo && i < m) {
+    const bool yfb = y_fallback && S->status == PDHGC_STATUS_CORNER_LIMIT;
+    yo[i] = yfb ? y_fallback[i] : (out ? hz.yp[i] : (avg ? w.sum_y[i] * inv_t : w.y[i]));
+  }
 }
 
 // Section 3: a '>' row whose dual is non-trivial becomes '='.  ax (optional,
@@ -673,6 +681,12 @@ struct pdhgc_lp {
   float *chat32 = nullptr, *lhat32 = nullptr, *uhat32 = nullptr, *bhat32 = nullptr;
   float *chat_c32 = nullptr, *lhat_c32 = nullptr, *uhat_c32 = nullptr;
   double *x1 = nullptr, *y1 = nullptr, *xc = nullptr;
+  // the dual corner push: its model (allocated on first use) and its y
+  bool have_dual_bufs = false, have_dual = false;
+  double *lhat_d = nullptr, *uhat_d = nullptr, *bhat_d = nullptr, *yd = nullptr;
+  int8_t* ge_d = nullptr;
+  float *lhat_d32 = nullptr, *uhat_d32 = nullptr, *bhat_d32 = nullptr;
+  pdhgc_report repd{};
   double *chat_c = nullptr, *lhat_c = nullptr, *uhat_c = nullptr;
   int8_t* ge_c = nullptr;
   // phase-1 restart history for the guidance features: 8 slots x n
@@ -1076,7 +1090,8 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
 
 // Runs one phase: init, the device-driven loop graph, finalize.
 int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi,
-              const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback) {
+              const double* x_start, const double* cc2, double* xo, double* yo, const double* x_fallback,
+              const double* y_start = nullptr, const double* y_fallback = nullptr) {
   cudaStream_t st = lp->stream;
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
@@ -1087,7 +1102,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const Iter32 w32 = fp32 ? lp->it32 : Iter32{};
   const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
                        lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
-  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32);
+  k_init_iterates<<<gnm, 256, 0, st>>>(n, m, md, lp->it, x_start, w32, y_start);
   k_init_scalars<<<1, 32, 0, st>>>(lp->S, pi, cc2);
   lp->launches += 2;
   CKL();
@@ -1125,7 +1140,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   long long chunks = 0;
   CK(cudaMemcpy(&chunks, &lp->S->chunks, sizeof(chunks), cudaMemcpyDeviceToHost));
   lp->launches += chunks * per_body;
-  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat, hz);
+  k_finalize<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it, xo, yo, x_fallback, md.lhat, md.uhat, hz, y_fallback);
   lp->launches++;
   if (fp32 && halpern) {
     k_h32_to64<<<gnm, 256, 0, st>>>(lp->S, n, m, lp->it32.x, lp->it32.xlo, lp->it32.y, lp->it32.ylo, lp->it.x,
@@ -1369,6 +1384,155 @@ int corner_run(pdhgc_lp* lp, const pdhgc_corner_params& cp, const double* x_star
   *r = pdhgc_report{};
   RET(fill_phase_report(lp, r));
   RET(run_report(lp, lp->xc, lp->y1, r));
+  return PDHGC_OK;
+}
+
+// ---- the dual corner push (the dual counterpart of Algorithm 1) ----------
+
+// Complementary slackness with the phase-1 point decides the model (user
+// space, tolerance eps_abs): a pair (distance of x_j from a bound, the part
+// of z_j that bound allows) or (slack of an inequality row, |y_i|) is read as
+// "the first is nonzero" when it exceeds both eps_abs and the second.
+// Columns: a bound stays unless x_j is off it in that sense, so a column
+// strictly inside its bounds becomes free (its reduced cost is fixed at 0).
+// z: the phase-1 reduced costs, unscaled (internal order).
+__global__ void k_dual_cols(int n, const double* __restrict__ x1, const double* __restrict__ z,
+                            const double* __restrict__ Dc, const double* __restrict__ l,
+                            const double* __restrict__ u, const double* __restrict__ lhat,
+                            const double* __restrict__ uhat, double eps_abs, double* __restrict__ lhat_d,
+                            double* __restrict__ uhat_d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = Dc[j] * x1[j];
+  const double dl = x - l[j], du = u[j] - x;
+  const bool off_l = dl > eps_abs && dl > fmax(z[j], 0.0);
+  const bool off_u = du > eps_abs && du > fmax(-z[j], 0.0);
+  lhat_d[j] = (l[j] != -INFINITY && !off_l) ? lhat[j] : -INFINITY;
+  uhat_d[j] = (u[j] != INFINITY && !off_u) ? uhat[j] : INFINITY;
+}
+
+// Rows: an inequality row whose slack exceeds eps_abs and |y_i| is inactive,
+// and its dual is fixed at 0 (ge_d = kRowDualZero, b_hat' = 0); the other
+// rows keep their sense and get the new objective b' = obj_scale U[0,1) per
+// user row, negated on '<' rows and scaled by D_r.  part: per-block sums of
+// b_hat'^2
+__global__ void k_dual_rows(int m, const int8_t* __restrict__ ge, const double* __restrict__ Dr,
+                            const double* __restrict__ sign, const double* __restrict__ b_int,
+                            const int* __restrict__ row_perm, const double* __restrict__ ax,
+                            const double* __restrict__ y1, double eps_abs, unsigned long long seed, double scale,
+                            int8_t* __restrict__ ge_d, double* __restrict__ bhat_d, double* __restrict__ part) {
+  __shared__ double s_red[8];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (i < m) {
+    const double slack = ax[i] / Dr[i] - b_int[i];
+    const bool zero = ge[i] && slack > eps_abs && slack > fabs(Dr[i] * y1[i]);
+    ge_d[i] = zero ? kRowDualZero : ge[i];
+    const double bh = zero ? 0.0 : Dr[i] * (sign[i] * (scale * splitmix_uniform(seed, (unsigned long long)row_perm[i])));
+    bhat_d[i] = bh;
+    sq = bh * bh;
+  }
+  for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// the start dual: y1, with 0 on the rows whose dual is fixed
+__global__ void k_dual_start(int m, const double* __restrict__ y1, const int8_t* __restrict__ ge_d,
+                             double* __restrict__ y0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) y0[i] = ge_d[i] == kRowDualZero ? 0.0 : y1[i];
+}
+
+__global__ void k_fold_into(const double* __restrict__ p, int nt, double* out) {
+  __shared__ double s_tmp[32];
+  const double v = block_fold(p, nt, false, s_tmp);
+  if (threadIdx.x == 0) *out = v;
+}
+
+DevModel model_dual(const pdhgc_lp* lp) {
+  return DevModel{lp->chat, lp->lhat_d, lp->uhat_d, lp->bhat_d, lp->Dr, lp->Dc, lp->ge_d};
+}
+DevModel32 model32_dual(const pdhgc_lp* lp) {
+  return DevModel32{lp->chat32, lp->lhat_d32, lp->uhat_d32, lp->bhat_d32, lp->ge_d};
+}
+
+int ensure_dual(pdhgc_lp* lp) {
+  if (!lp->have_dual_bufs) {
+    RET(lp->alloc(&lp->lhat_d, (size_t)lp->n));
+    RET(lp->alloc(&lp->uhat_d, (size_t)lp->n));
+    RET(lp->alloc(&lp->bhat_d, (size_t)lp->m));
+    RET(lp->alloc(&lp->yd, (size_t)lp->m));
+    RET(lp->alloc(&lp->ge_d, (size_t)lp->m));
+    lp->have_dual_bufs = true;
+  }
+  if (lp->params.precision == PDHGC_FP32_BULK && !lp->lhat_d32) {
+    RET(lp->alloc(&lp->lhat_d32, (size_t)lp->n));
+    RET(lp->alloc(&lp->uhat_d32, (size_t)lp->n));
+    RET(lp->alloc(&lp->bhat_d32, (size_t)lp->m));
+  }
+  return PDHGC_OK;
+}
+
+// builds the dual corner model from the phase-1 point and runs its phase
+int dual_corner_run(pdhgc_lp* lp, const pdhgc_corner_params& cp, pdhgc_report* r) {
+  cudaStream_t st = lp->stream;
+  const int m = lp->m, n = lp->n;
+  RET(ensure_dual(lp));
+  // the phase-1 reduced costs (unscaled) for the column rule
+  RET(launch_tiles(lp, true, true, ZOp{lp->y1, model_orig(lp), lp->pi_w}, nullptr, st));
+  k_dual_cols<<<grid_for(n), 256, 0, st>>>(n, lp->x1, lp->pi_w, lp->Dc, lp->l, lp->u, lp->lhat, lp->uhat,
+                                           cp.eps_abs, lp->lhat_d, lp->uhat_d);
+  k_fill<<<grid_for(m), 256, 0, st>>>(lp->tmp_m, m, 0.0);  // A = 0 leaves the pass empty
+  lp->launches += 2;
+  CKL();
+  CK(cudaMemsetAsync(&lp->S->pi_zero, 0, sizeof(int), st));
+  RET(launch_tiles(lp, false, true, SpmvOp<false>{lp->S, lp->x1, lp->tmp_m}, nullptr, st));
+  const int gm = grid_for(m);
+  k_dual_rows<<<gm, 256, 0, st>>>(m, lp->ge, lp->Dr, lp->sign, lp->b_int, lp->row_perm, lp->tmp_m, lp->y1,
+                                  cp.eps_abs, (unsigned long long)cp.obj_seed, cp.obj_scale, lp->ge_d, lp->bhat_d,
+                                  lp->pA);
+  k_fold_into<<<1, 256, 0, st>>>(lp->pA, gm, lp->scratch + 10);  // pA holds >= ceil(m / 256) entries
+  k_dual_start<<<gm, 256, 0, st>>>(m, lp->y1, lp->ge_d, lp->yd);
+  lp->launches += 3;
+  CKL();
+  const pdhgc_params& p = lp->params;
+  if (p.precision == PDHGC_FP32_BULK) {
+    RET(to32(lp, lp->lhat_d, lp->lhat_d32, n, st));
+    RET(to32(lp, lp->uhat_d, lp->uhat_d32, n, st));
+    RET(to32(lp, lp->bhat_d, lp->bhat_d32, m, st));
+  }
+  PhaseInit pi{};
+  pi.eps_rel = cp.eps_rel;
+  pi.beta_suff = p.beta_suff;
+  pi.beta_nec = p.beta_nec;
+  pi.beta_art = p.beta_art;
+  pi.theta = p.theta;
+  pi.time_limit_s = cp.time_limit_s;
+  pi.nb = lp->b_norm;
+  pi.nc = lp->c_norm;
+  pi.max_iters = cp.max_iters;
+  pi.min_iters = cp.min_iters;
+  pi.check_period = p.check_period;
+  pi.phase = 1;
+  pi.stop_rule = cp.stop_rule == 1 ? 1 : 2;
+  pi.use_bb2 = 1;
+  pi.algorithm = p.algorithm;
+  pi.rho = p.reflection;
+  pi.pid_kp = p.pid_kp;
+  pi.pid_ki = p.pid_ki;
+  pi.pid_kd = p.pid_kd;
+  // x starts at proj(0) of the dual corner model's box, y at y1 (0 on fixed rows)
+  RET(run_phase(lp, model_dual(lp), model32_dual(lp), pi, nullptr, lp->scratch + 8, lp->tmp_n, lp->yd, nullptr,
+                lp->yd, lp->y1));
+  *r = pdhgc_report{};
+  RET(fill_phase_report(lp, r));
+  RET(run_report(lp, lp->x1, lp->yd, r));
   return PDHGC_OK;
 }
 
@@ -1792,6 +1956,7 @@ int pdhgc_solve(pdhgc_lp* lp, const pdhgc_params* params, pdhgc_report* out) {
   lp->params = p;
   lp->have_phase1 = false;
   lp->have_corner = false;
+  lp->have_dual = false;
   RET(setup_scaling(lp, p));
   if (p.precision == PDHGC_FP32_BULK) {
     RET(ensure_fp32(lp));
@@ -1840,6 +2005,23 @@ int pdhgc_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_re
   lp->repc = r;
   lp->have_corner = true;
   lp->cp_last = cp;
+  if (out) *out = r;
+  return PDHGC_OK;
+}
+
+int pdhgc_dual_corner_phase(pdhgc_lp* lp, const pdhgc_corner_params* params, pdhgc_report* out) {
+  if (!lp) return set_err(PDHGC_ERR_INVALID_ARG, "lp is NULL");
+  if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run on this handle");
+  pdhgc_corner_params cp;
+  if (params) cp = *params; else pdhgc_default_corner_params(&cp);
+  RET(check_corner_params(cp));
+  if (cp.row_rule != 0 || cp.omega_rule != 0)
+    return set_err(PDHGC_ERR_INVALID_ARG, "the dual corner phase takes row_rule 0 and omega_rule 0");
+  lp->have_dual = false;
+  pdhgc_report r{};
+  RET(dual_corner_run(lp, cp, &r));
+  lp->repd = r;
+  lp->have_dual = true;
   if (out) *out = r;
   return PDHGC_OK;
 }
@@ -2081,12 +2263,13 @@ int pdhgc_set_state(pdhgc_lp* lp, const void* buf, size_t bytes) {
 }
 
 int pdhgc_kkt_report(pdhgc_lp* lp, int which, pdhgc_report* out) {
-  if (!lp || !out || (which != PDHGC_PHASE1 && which != PDHGC_CORNER))
+  if (!lp || !out || (which != PDHGC_PHASE1 && which != PDHGC_CORNER && which != PDHGC_DUAL_CORNER))
     return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
   if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
   if (which == PDHGC_CORNER && !lp->have_corner) return set_err(PDHGC_ERR_NO_CORNER, "no corner result");
-  pdhgc_report r = which == PDHGC_PHASE1 ? lp->rep1 : lp->repc;
-  RET(run_report(lp, which == PDHGC_PHASE1 ? lp->x1 : lp->xc, lp->y1, &r));
+  if (which == PDHGC_DUAL_CORNER && !lp->have_dual) return set_err(PDHGC_ERR_NO_CORNER, "no dual corner result");
+  pdhgc_report r = which == PDHGC_PHASE1 ? lp->rep1 : (which == PDHGC_CORNER ? lp->repc : lp->repd);
+  RET(run_report(lp, which == PDHGC_CORNER ? lp->xc : lp->x1, which == PDHGC_DUAL_CORNER ? lp->yd : lp->y1, &r));
   *out = r;
   return PDHGC_OK;
 }
@@ -2098,28 +2281,31 @@ static int copy_out(pdhgc_lp* lp, double* dst, const double* dev_user, size_t co
 }
 
 int pdhgc_get_solution(pdhgc_lp* lp, int which, double* x, double* y, double* z, int on_device) {
-  if (!lp || (which != PDHGC_PHASE1 && which != PDHGC_CORNER) || (on_device != 0 && on_device != 1))
+  if (!lp || (which != PDHGC_PHASE1 && which != PDHGC_CORNER && which != PDHGC_DUAL_CORNER) ||
+      (on_device != 0 && on_device != 1))
     return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
   if (!lp->have_phase1) return set_err(PDHGC_ERR_NO_PHASE1, "pdhgc_solve has not run");
   if (which == PDHGC_CORNER && !lp->have_corner) return set_err(PDHGC_ERR_NO_CORNER, "no corner result");
+  if (which == PDHGC_DUAL_CORNER && !lp->have_dual) return set_err(PDHGC_ERR_NO_CORNER, "no dual corner result");
   cudaStream_t st = lp->stream;
   const int m = lp->m, n = lp->n;
+  const double* ysrc = which == PDHGC_DUAL_CORNER ? lp->yd : lp->y1;
   if (x) {
-    k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, which == PDHGC_PHASE1 ? lp->x1 : lp->xc, lp->Dc,
+    k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, which == PDHGC_CORNER ? lp->xc : lp->x1, lp->Dc,
                                             nullptr, lp->tmp_n);
     lp->launches++;
     CKL();
     RET(copy_out(lp, x, lp->tmp_n, n, on_device));
   }
   if (y) {
-    k_unpermute<<<grid_for(m), 256, 0, st>>>(m, lp->row_perm, lp->y1, lp->Dr, lp->sign, lp->tmp_m);
+    k_unpermute<<<grid_for(m), 256, 0, st>>>(m, lp->row_perm, ysrc, lp->Dr, lp->sign, lp->tmp_m);
     lp->launches++;
     CKL();
     RET(copy_out(lp, y, lp->tmp_m, m, on_device));
   }
   if (z) {
     // the unpermute below reads pi_w; the stream orders it after the ZOp pass
-    RET(launch_tiles(lp, true, true, ZOp{lp->y1, model_orig(lp), lp->pi_w}, nullptr, st));
+    RET(launch_tiles(lp, true, true, ZOp{ysrc, model_orig(lp), lp->pi_w}, nullptr, st));
     k_unpermute<<<grid_for(n), 256, 0, st>>>(n, lp->col_perm, lp->pi_w, nullptr, nullptr, lp->tmp_n);
     lp->launches++;
     CKL();

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "NONE", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "TIME_LIMIT", 4: "N
                 5: "CORNER_DONE", 6: "CORNER_LIMIT", 7: "GUIDE_FALLBACK"}
 GUIDE_FEATURES, GUIDE_FEAT_STRIDE, GUIDE_PARAMS = 18, 32, 5441
 FP64, FP32_BULK = 0, 1
-PHASE1, CORNER = 0, 1
+PHASE1, CORNER, DUAL_CORNER = 0, 1, 2
 AVERAGED, HALPERN = 0, 1  # pdhgc_params.algorithm (PDHGC_ALG_*)
 
 
@@ -103,6 +103,7 @@ _sig = {
                                   _vp, _vp, _vp, C.c_int, _vp]),
     "pdhgc_solve": (C.c_int, [_vp, C.POINTER(Params), C.POINTER(Report)]),
     "pdhgc_corner_phase": (C.c_int, [_vp, C.POINTER(CornerParams), C.POINTER(Report)]),
+    "pdhgc_dual_corner_phase": (C.c_int, [_vp, C.POINTER(CornerParams), C.POINTER(Report)]),
     "pdhgc_kkt_report": (C.c_int, [_vp, C.c_int, C.POINTER(Report)]),
     "pdhgc_get_solution": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_iterates": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
@@ -230,6 +231,13 @@ class LP:
         p = params if params is not None else default_corner_params(**kw)
         r = Report()
         _check(lib.pdhgc_corner_phase(self._h, C.byref(p), C.byref(r)), "pdhgc_corner_phase")
+        return r.as_dict()
+
+    def dual_corner_phase(self, params: CornerParams | None = None, **kw) -> dict:
+        """pdhgc_dual_corner_phase: the dual corner push from the phase-1 point."""
+        p = params if params is not None else default_corner_params(**kw)
+        r = Report()
+        _check(lib.pdhgc_dual_corner_phase(self._h, C.byref(p), C.byref(r)), "pdhgc_dual_corner_phase")
         return r.as_dict()
 
     def kkt_report(self, which: int = PHASE1) -> dict:

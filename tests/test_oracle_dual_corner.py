@@ -28,11 +28,12 @@ def test_dual_corner_model_follows_its_definition():
     model = r1["model"]
     cp = dict(oracle.CORNER_DEFAULTS, obj_seed=9, obj_scale=0.5)
     dm, info = oracle.dual_corner_model(model, r1["x_hat"], r1["y_hat"], cp)
-    x = model.Dc * r1["x_hat"]
+    x, y, z = oracle.unscale(model, r1["x_hat"], r1["y_hat"])
     eps = cp["eps_abs"]
-    # a bound stays exactly where x sits on it (within eps_abs), else it is removed
-    at_l = np.isfinite(model.l) & (x - model.l <= eps)
-    at_u = np.isfinite(model.u) & (model.u - x <= eps)
+    # a bound stays unless x is off it: the distance exceeds eps_abs and the
+    # part of z that bound allows (complementary slackness read at x)
+    at_l = np.isfinite(model.l) & ~((x - model.l > eps) & (x - model.l > np.maximum(z, 0)))
+    at_u = np.isfinite(model.u) & ~((model.u - x > eps) & (model.u - x > np.maximum(-z, 0)))
     assert np.array_equal(np.isfinite(dm.l), at_l) and np.array_equal(dm.l[at_l], model.l[at_l])
     assert np.array_equal(np.isfinite(dm.u), at_u) and np.array_equal(dm.u[at_u], model.u[at_u])
     # the constructed optimum: columns of S free, the others at a bound
@@ -40,9 +41,9 @@ def test_dual_corner_model_follows_its_definition():
     S[lp["support"]] = True
     assert not np.any(np.isfinite(dm.l[S]) | np.isfinite(dm.u[S]))
     assert np.all(np.isfinite(dm.l[~S]) | np.isfinite(dm.u[~S]))
-    # inactive inequality rows (slack > eps_abs at x) get a dual fixed at 0
+    # inactive inequality rows (slack above eps_abs and |y| at x) get a dual fixed at 0
     slack = model.A_int @ x - model.b_int
-    assert np.array_equal(dm.y_zero, model.ge & (slack > eps))
+    assert np.array_equal(dm.y_zero, model.ge & (slack > eps) & (slack > np.abs(y)))
     ineq_inactive = (np.asarray(lp["sense"]) != oracle.EQ) & (np.abs(lp["y_star"]) == 0.0) & \
         (np.abs(lp["b"] - ve.dense(lp) @ lp["x_star"]) > 0.05)
     assert np.array_equal(dm.y_zero, ineq_inactive)
@@ -150,3 +151,22 @@ def test_dual_corner_fixed_rows_and_limit(alg):
     assert ev["rD2"] <= 1e-6 * (1 + np.linalg.norm(lp["c"]))
     lim = oracle.dual_corner_phase(r1, dict(obj_seed=5, max_iters=64))
     assert lim["status"] == oracle.CORNER_LIMIT and np.array_equal(lim["y_hat"], r1["y_hat"])
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_dual_corner_reads_near_threshold_pairs_by_complementarity(alg):
+    # at a 1e-6 phase-1 point an active row can show a slack just above
+    # eps_abs (1.4e-6 here) beside a dual of order 1: it keeps its dual, the
+    # model's dual stays non-empty, and the phase regains dual feasibility
+    lp = lpgen.with_bounds_and_inequalities(lpgen.random_face_lp(200, 500, 150, seed=3), 3)
+    r1 = _phase1(lp, alg, 1e-6)
+    model = r1["model"]
+    x, y, _ = oracle.unscale(model, r1["x_hat"], r1["y_hat"])
+    slack = model.A_int @ x - model.b_int
+    near = model.ge & (slack > 1e-6) & (slack < 1e-5) & (np.abs(y) > 1e-2)
+    assert near.any()
+    rd = oracle.dual_corner_phase(r1, dict(obj_seed=5, max_iters=200_000))
+    assert not rd["dual_model"].y_zero[near].any()
+    assert rd["status"] == oracle.CORNER_DONE
+    rep = oracle.kkt_report(model, rd["x_hat"], rd["y_hat"])
+    assert rep["rel_d"] <= 1e-6 and rep["rel_kkt"] <= 1e-5
