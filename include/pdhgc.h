@@ -45,7 +45,8 @@ extern "C" {
 #define PDHGC_ERR_OOM           -6  /* device or pinned-host allocation failed */
 #define PDHGC_ERR_NO_PHASE1     -7  /* corner phase or PHASE1 report requested before pdhgc_solve */
 #define PDHGC_ERR_NO_CORNER     -8  /* CORNER report / solution requested before pdhgc_corner_phase */
-#define PDHGC_ERR_TOO_LARGE     -9  /* nnz >= 2^31 or a dimension >= 2^31 */
+#define PDHGC_ERR_TOO_LARGE     -9  /* nnz >= 2^31 or a dimension >= 2^31, or n above the
+                                       limit of a fixed-capacity entry point (pdhgc_kkt_eval_noalloc) */
 #define PDHGC_ERR_DEVICE        -10 /* a device-side check failed (error word set by a kernel) */
 #define PDHGC_ERR_BUFFER        -11 /* a caller buffer is too small (size written back) */
 
@@ -313,8 +314,9 @@ int pdhgc_kkt_eval(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
  * applications whose device memory is owned by a pool or framework allocator
  * that must account for every byte, and code paths where the implicit
  * synchronisation of cudaMalloc / cudaFree is not acceptable.  (The paper
- * has no counterpart; this is a library convenience.)  Same arguments,
- * results and errors as pdhgc_kkt_eval, plus:
+ * has no counterpart; this is a library convenience.)  Same arguments and
+ * results as pdhgc_kkt_eval.  Errors: INVALID_ARG (as pdhgc_kkt_eval),
+ * TOO_LARGE (below), CUDA; never OOM.  Further:
  *  - n must be <= 262,144 (1 << 18); a larger n returns PDHGC_ERR_TOO_LARGE
  *    without touching the device.
  *  - The scratch is a file-scope device array of 2,203,776 bytes ((1 << 18)
@@ -323,7 +325,10 @@ int pdhgc_kkt_eval(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
  *    no cudaMalloc, cudaFree or allocating library routine.
  *  - The first call on a device (the current device of the calling thread)
  *    looks up that array's device address with cudaGetSymbolAddress; make
- *    that first call before any stream capture begins.
+ *    that first call before any stream capture begins.  Later calls check
+ *    with cudaPointerGetAttributes that the address still belongs to the
+ *    device's current context (after cudaDeviceReset it does not) and look
+ *    it up again when it does not.
  *  - All calls on a device share the array and it keeps the last call's
  *    contents; every call clears the part that must start at zero.  Calls
  *    that overlap on the GPU (different streams, or different host threads

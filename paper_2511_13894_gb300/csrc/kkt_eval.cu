@@ -272,8 +272,21 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
+// true when p is device memory of device `dev` in the current context (a
+// cached address stays valid until cudaDeviceReset replaces the context)
+bool still_device_memory(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not a pointer of this context: clear the error it set
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 // device address of g_kkt_eval_scratch for the current device, looked up
-// once per device with that device current
+// with that device current on its first call, and again whenever the cached
+// address no longer belongs to the device's current context
 int scratch_for_current_device(double** out, std::string& detail) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -286,7 +299,7 @@ int scratch_for_current_device(double** out, std::string& detail) {
     return PDHGC_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !still_device_memory(g_scratch_ptr[dev], dev)) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_kkt_eval_scratch);
     if (e != cudaSuccess || !p) {

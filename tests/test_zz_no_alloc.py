@@ -78,3 +78,52 @@ def test_noalloc_rejects_n_above_its_capacity():
     rc, _ = _call(_noalloc, lp, t, n_override=NOALLOC_MAX_N + 1)
     assert rc == -9  # PDHGC_ERR_TOO_LARGE, before any device work
     assert b"static scratch capacity" in P.lib.pdhgc_last_error_detail()
+
+
+def _cudart():
+    """The CUDA runtime, for the device's default memory pool (the pool
+    cudaMallocAsync draws from)."""
+    import ctypes.util
+    import glob
+    import os
+    names = [ctypes.util.find_library("cudart")] + sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so*"))
+    for nm in names:
+        if nm and (os.path.exists(nm) or "/" not in nm):
+            try:
+                return C.CDLL(nm)
+            except OSError:
+                continue
+    pytest.skip("libcudart not found")
+
+
+def test_noalloc_allocates_no_device_memory():
+    # the default pool's high-water mark of used memory, reset before each
+    # call, moves for the allocating entry point (its cudaMallocAsync
+    # scratch) and stays put for the no-allocation one; torch's allocator
+    # sees no change either
+    rt = _cudart()
+    USED_HIGH = 8  # cudaMemPoolAttrUsedMemHigh
+    dev = C.c_int(0)
+    assert rt.cudaGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+
+    def used_high_after(fn, lp, t):
+        torch.cuda.synchronize()
+        zero = C.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, USED_HIGH, C.byref(zero)) == 0
+        before = torch.cuda.memory_allocated()
+        rc, _ = _call(fn, lp, t)
+        torch.cuda.synchronize()
+        assert rc == 0
+        v = C.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, USED_HIGH, C.byref(v)) == 0
+        return v.value, torch.cuda.memory_allocated() - before
+
+    lp = lpgen.power_law_lp(3000, 12000, 500, seed=5, kmax=2000)
+    x, y = _point(lp, 3)
+    t = P._device_lp_args(lp, x, y)
+    high_ref, torch_ref = used_high_after(P.lib.pdhgc_kkt_eval, lp, t)
+    high, torch_delta = used_high_after(_noalloc, lp, t)
+    assert high_ref > 0          # the control: the allocating entry point used the pool
+    assert high == 0 and torch_delta == 0 and torch_ref == 0
