@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -91,6 +92,12 @@ def parse():
     ap.add_argument("--obj-scale-sweep", type=str, default=None,
                     help="comma-separated corner objective scales (Section 5's study): one phase 1 with the "
                          "headline loop, then one timed corner phase per scale; prints its own JSON line")
+    ap.add_argument("--guidance-study", type=str, default=None,
+                    help="TRAIN,TEST: the learned-guidance study on 20k x 80k power-law LPs (the guidance "
+                         "configuration's size): corners of TRAIN seed-generated LPs (Halpern loop) label "
+                         "the training rows, the network trains on the GPU, and TEST held-out LPs compare "
+                         "the guided corner phase with the plain one; prints its own JSON line")
+    ap.add_argument("--guidance-steps", type=int, default=3000, help="training steps of --guidance-study")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-iters", type=int, default=50)
     ap.add_argument("--cpu-iters", type=int, default=640,
@@ -736,6 +743,54 @@ def run_obj_scale_sweep(args, g, P, torch, stream):
                       "runs": rows}), flush=True)
 
 
+def run_guidance_study(args, torch, P):
+    """The learned-guidance study at 20k x 80k (m, n of the guidance
+    configuration; power-law construction, |S| = m + 1000).  Training rows
+    come from the plain corner phases of `train` LPs (seeds 0..train-1, each
+    with the Halpern loop's phase 1 and Algorithm 1 under Section 3's row
+    rule); the network trains with the library's kernels; each of `test`
+    held-out LPs (seeds 1000..) runs phase 1 once, then the plain and the
+    guided corner phase from it.  Reports the dataset, the loss against the
+    label entropy, and per held-out LP the two corner phases' iterations,
+    seconds and status, the holds and their precision as the plain corner
+    judges them, and the plain/guided time ratio."""
+    from paper_2511_13894_gb300 import guide as G
+    n_train, n_test = (int(v) for v in args.guidance_study.split(","))
+    p1 = P.default_params(max_iters=args.phase1_max_iters, algorithm=P.HALPERN)
+    t0 = time.perf_counter()
+    train_lps = [lpgen.guidance_lp(s) for s in range(n_train)]
+    t_gen = time.perf_counter() - t0
+    data = G.build_dataset(train_lps, [s + 1 for s in range(n_train)], corner_max_iters=args.corner_max_iters,
+                           phase1_params=p1)
+    del train_lps
+    rows = int(data["rows"])
+    pos = float(data["labels"][:rows].float().mean().item()) if rows else 0.0
+    entropy = -(pos * math.log(pos) + (1 - pos) * math.log(1 - pos)) if 0 < pos < 1 else 0.0
+    net = P.Guide(seed=0)
+    t0 = time.perf_counter()
+    losses = G.train(net, data, steps=args.guidance_steps, batch=4096, lr=1e-3, seed=5) if rows else []
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    tests = []
+    for s in range(1000, 1000 + n_test):
+        r = G.compare(net, lpgen.guidance_lp(s), s + 1, threshold=0.9, corner_max_iters=args.corner_max_iters,
+                      guided_max_iters=2 * 64 * 1024, phase1_params=p1)
+        r["seed"] = s
+        tests.append(r)
+    done = [r for r in tests if r["plain_status"] == "CORNER_DONE" and r["final_status"] == "CORNER_DONE"]
+    print(json.dumps({
+        "mode": "guidance_study", "workload": "power_law_m20k_n80k", "algorithm": "halpern",
+        "train_lps": n_train, "test_lps": n_test, "generate_seconds": t_gen,
+        "dataset": {"rows": rows, "positive_frac": pos, "seconds": data["seconds"], "records": data["records"]},
+        "training": {"steps": args.guidance_steps, "seconds": t_train, "label_entropy": entropy,
+                     "loss_first50": float(np.mean(losses[:50])) if len(losses) else None,
+                     "loss_last50": float(np.mean(losses[-50:])) if len(losses) else None},
+        "held_out": tests,
+        "time_ratio_plain_over_guided": [r["speedup"] for r in done],
+        "data": "synthetic (seeded power-law LPs; the paper's models are not available)",
+    }), flush=True)
+
+
 def corner_speedup(base, other):
     """Time-to-corner speedup of `other` over `base` (ratio of their step
     times), reported only when every timed step of both arms ended its
@@ -768,6 +823,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.guidance_study:
+        if rank == 0:
+            run_guidance_study(args, torch, P)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch_512" and args.mode == "kernels":
         # --profile-iters iterations of every LP in one batched launch (FP32 bulk), for ncu
         B = P.Batch(lpgen.batch_lps(512), stream=torch.cuda.current_stream().cuda_stream)

@@ -419,6 +419,11 @@ using SpmvMat = SpmvMatT<double>;
 #ifndef PDHGC_MIN_BLOCKS
 #define PDHGC_MIN_BLOCKS 4
 #endif
+// 1: the SELL-32 loop requests the next batch's matrix entries before it
+// consumes the current batch's gathers
+#ifndef PDHGC_SELL_PIPE
+#define PDHGC_SELL_PIPE 0
+#endif
 constexpr int kBatch = PDHGC_GATHER_BATCH;
 
 // acc += sum over k = k0, k0+step, ... < k1 of val[k] * gathered(col[k]), in
@@ -597,6 +602,36 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
     typename Op::Acc acc;
     acc.zero();
     const double rc = r >= 0 ? op.row_ctx(r) : 0.0;
+#if PDHGC_SELL_PIPE
+    // software-pipelined: the next batch's values and indices are requested
+    // while this batch's gathers are in flight, so that a step waits for the
+    // slower of the two loads instead of their sum
+    for (int j = jb; j < je; j += kBatch) {
+      GV<GT, NG> g[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < jend)
+#pragma unroll
+          for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+      VT vn[kBatch];
+      int cn[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (j + kBatch + u < jend) {
+          vn[u] = ld_stream(M.sval + base + (j + kBatch + u) * kSellH + lane);
+          cn[u] = ld_stream(M.scol + base + (j + kBatch + u) * kSellH + lane);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (j + u < jend) op.accum(acc, rc, v[u], g[u]);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        v[u] = vn[u];
+        c[u] = cn[u];
+      }
+    }
+#else
     for (int j = jb; j < je; j += kBatch) {
       if (j > jb) {
 #pragma unroll
@@ -617,6 +652,7 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
       for (int u = 0; u < kBatch; ++u)
         if (j + u < jend) op.accum(acc, rc, v[u], g[u]);
     }
+#endif
     if constexpr (kPdl) grid_dep_launch();
     if (K > 1) {  // uniform over the block
       __shared__ typename Op::Acc s_part[kWarpsPerBlock][kSellH];
