@@ -106,9 +106,11 @@ def parse():
     ap.add_argument("--batch-sample", type=int, default=16,
                     help="batch_512: LPs solved one by one with the single-LP FP64 path for the "
                          "sequential reference time (every count/sample-th LP by size)")
-    ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "kernels", "stream"], default="bench",
                     help="kernels: short solve, then --profile-iters replays of the two iteration "
-                         "kernels as plain launches inside the NVTX range 'pdhg_kernels' (for ncu)")
+                         "kernels as plain launches inside the NVTX range 'pdhg_kernels' (for ncu); "
+                         "stream: phase 1 of the headline loop for --profile-iters iterations (rounded up to "
+                         "check periods) with every kernel a plain stream launch (for ncu's launch list)")
     return ap.parse_args()
 
 
@@ -753,7 +755,9 @@ def run_guidance_study(args, torch, P):
     guided corner phase from it.  Reports the dataset, the loss against the
     label entropy, and per held-out LP the two corner phases' iterations,
     seconds and status, the holds and their precision as the plain corner
-    judges them, and the plain/guided time ratio."""
+    judges them, and the plain/guided time ratio; beside them the guided
+    run at higher thresholds (no fallback) and a perfect predictor that
+    holds exactly the columns the plain corner left at their hold bound."""
     from paper_2511_13894_gb300 import guide as G
     n_train, n_test = (int(v) for v in args.guidance_study.split(","))
     p1 = P.default_params(max_iters=args.phase1_max_iters, algorithm=P.HALPERN)
@@ -774,7 +778,8 @@ def run_guidance_study(args, torch, P):
     tests = []
     for s in range(1000, 1000 + n_test):
         r = G.compare(net, lpgen.guidance_lp(s), s + 1, threshold=0.9, corner_max_iters=args.corner_max_iters,
-                      guided_max_iters=2 * 64 * 1024, phase1_params=p1)
+                      guided_max_iters=2 * 64 * 1024, phase1_params=p1, upper_bound=True,
+                      extra_thresholds=(0.97, 0.995))
         r["seed"] = s
         tests.append(r)
     done = [r for r in tests if r["plain_status"] == "CORNER_DONE" and r["final_status"] == "CORNER_DONE"]
@@ -787,6 +792,14 @@ def run_guidance_study(args, torch, P):
                      "loss_last50": float(np.mean(losses[-50:])) if len(losses) else None},
         "held_out": tests,
         "time_ratio_plain_over_guided": [r["speedup"] for r in done],
+        "time_ratio_plain_over_perfect_predictor": [r["perfect_predictor"]["speedup"] for r in done
+                                                    if r["perfect_predictor"]["status"] == "CORNER_DONE"],
+        "by_threshold": [{"threshold": t["threshold"],
+                          "corner_done": sum(r["thresholds"][k]["status"] == "CORNER_DONE" for r in tests),
+                          "mean_wrong_holds": float(np.mean([r["thresholds"][k]["wrong_holds"] for r in tests])),
+                          "time_ratio_plain_over_guided": [r["thresholds"][k]["speedup"] for r in tests
+                                                           if r["plain_status"] == "CORNER_DONE"]}
+                         for k, t in enumerate(tests[0]["thresholds"])] if tests else [],
         "data": "synthetic (seeded power-law LPs; the paper's models are not available)",
     }), flush=True)
 
@@ -862,6 +875,18 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"mode": "kernels", "workload": args.workload, "primal_ms": ms[0], "dual_ms": ms[1]}))
+        return
+    if args.mode == "stream":
+        iters = max(64, -(-args.profile_iters // 64) * 64)
+        g.set_launch_mode(P.LAUNCH_STREAM)
+        l0 = g.kernel_launches()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = g.solve(max_iters=iters, eps_rel=-1.0, precision=P.FP32_BULK if args.precision == "fp32" else P.FP64,
+                      algorithm=P.AVERAGED if args.algorithm == "averaged" else P.HALPERN)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "stream", "workload": args.workload, "iters": rep["iters"],
+                          "launches": g.kernel_launches() - l0, "seconds": time.perf_counter() - t0}))
         return
     if args.obj_scale_sweep:
         run_obj_scale_sweep(args, g, P, torch, stream)

@@ -49,6 +49,7 @@ extern "C" {
                                        limit of a fixed-capacity entry point (pdhgc_kkt_eval_noalloc) */
 #define PDHGC_ERR_DEVICE        -10 /* a device-side check failed (error word set by a kernel) */
 #define PDHGC_ERR_BUFFER        -11 /* a caller buffer is too small (size written back) */
+#define PDHGC_ERR_IO            -12 /* a file could not be opened, read or written, or is not in the expected format */
 
 /* ---- solver outcome (pdhgc_report.status) -------------------------------- */
 #define PDHGC_STATUS_NONE          0
@@ -285,6 +286,27 @@ int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out);
  * Errors: INVALID_ARG.
  */
 int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked);
+
+/*
+ * pdhgc_set_launch_mode — how pdhgc_solve, pdhgc_corner_phase and the dual
+ * corner push drive their restarted loop (Section 2's iteration with a check
+ * every check_period steps):
+ *   PDHGC_LAUNCH_GRAPH (0, the default): one CUDA graph per phase whose
+ *     conditional WHILE node repeats the body (check_period iterations, the
+ *     check, the decision, the restart) until the device decision sets the
+ *     phase's done flag: no host round trip inside the loop;
+ *   PDHGC_LAUNCH_STREAM (1): the same kernels, enqueued as plain launches on
+ *     the handle's stream, one body at a time; the host reads the done flag
+ *     back after each body.  Every kernel is then a separate launch that a
+ *     profiler's launch list shows (kernel nodes inside a conditional graph
+ *     body are not listed separately).
+ * Both modes make the same decisions and give bitwise-equal results.  Takes
+ * effect at the next call.  A launch choice (the paper has no counterpart).
+ * Errors: INVALID_ARG.
+ */
+#define PDHGC_LAUNCH_GRAPH  0
+#define PDHGC_LAUNCH_STREAM 1
+int pdhgc_set_launch_mode(pdhgc_lp* lp, int32_t mode);
 
 /*
  * pdhgc_kkt_eval — the Section 2 residuals, objectives and relative ratios,
@@ -548,6 +570,19 @@ void pdhgc_guide_destroy(pdhgc_guide* g);
  * Errors: INVALID_ARG, NONFINITE (set). */
 int pdhgc_guide_set_weights(pdhgc_guide* g, const float* w);
 int pdhgc_guide_get_weights(pdhgc_guide* g, float* w);
+
+/*
+ * pdhgc_guide_save / pdhgc_guide_load — the network's FP32 parameter vector
+ * in a file: the 8 bytes "PDHGCGW1", PDHGC_GUIDE_PARAMS as a little-endian
+ * int32, a zero int32, the parameters as little-endian IEEE FP32 in the
+ * parameter-vector layout, then the 64-bit FNV-1a hash of those parameter
+ * bytes (little-endian).  load checks the header, size and hash, rejects
+ * non-finite weights, and resets Adam's moments as set_weights does.
+ * Errors: INVALID_ARG (NULL), IO (open / read / write failure, wrong header,
+ * size or hash), NONFINITE (load), CUDA.
+ */
+int pdhgc_guide_save(pdhgc_guide* g, const char* path);
+int pdhgc_guide_load(pdhgc_guide* g, const char* path);
 
 /*
  * pdhgc_guide_infer — probabilities p[r] for `rows` feature rows; feat and p

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -933,6 +934,73 @@ int pdhgc_guide_get_weights(pdhgc_guide* g, float* w) {
   GK(cudaMemcpyAsync(w, g->w, sizeof(float) * kGParams, cudaMemcpyDeviceToHost, g->stream));
   GK(cudaStreamSynchronize(g->stream));
   return PDHGC_OK;
+}
+
+namespace {
+constexpr char kGuideMagic[8] = {'P', 'D', 'H', 'G', 'C', 'G', 'W', '1'};
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+void put_le(unsigned char* d, uint64_t v, int bytes) {
+  for (int i = 0; i < bytes; ++i) d[i] = (unsigned char)(v >> (8 * i));
+}
+
+uint64_t get_le(const unsigned char* d, int bytes) {
+  uint64_t v = 0;
+  for (int i = 0; i < bytes; ++i) v |= (uint64_t)d[i] << (8 * i);
+  return v;
+}
+}  // namespace
+
+int pdhgc_guide_save(pdhgc_guide* g, const char* path) {
+  if (!g || !path) return set_error_detail(PDHGC_ERR_INVALID_ARG, "NULL argument");
+  std::vector<float> w(kGParams);
+  int rc = pdhgc_guide_get_weights(g, w.data());
+  if (rc != PDHGC_OK) return rc;
+  std::vector<unsigned char> buf(16 + 4 * (size_t)kGParams + 8);
+  std::memcpy(buf.data(), kGuideMagic, 8);
+  put_le(buf.data() + 8, (uint64_t)kGParams, 4);
+  put_le(buf.data() + 12, 0, 4);
+  for (int i = 0; i < kGParams; ++i) {
+    uint32_t bits;
+    std::memcpy(&bits, &w[i], 4);
+    put_le(buf.data() + 16 + 4 * (size_t)i, bits, 4);
+  }
+  put_le(buf.data() + 16 + 4 * (size_t)kGParams, fnv1a(buf.data() + 16, 4 * (size_t)kGParams), 8);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error_detail(PDHGC_ERR_IO, std::string("cannot open for writing: ") + path);
+  const size_t wrote = std::fwrite(buf.data(), 1, buf.size(), f);
+  const int closed = std::fclose(f);
+  if (wrote != buf.size() || closed != 0) return set_error_detail(PDHGC_ERR_IO, std::string("write failed: ") + path);
+  return PDHGC_OK;
+}
+
+int pdhgc_guide_load(pdhgc_guide* g, const char* path) {
+  if (!g || !path) return set_error_detail(PDHGC_ERR_INVALID_ARG, "NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error_detail(PDHGC_ERR_IO, std::string("cannot open: ") + path);
+  std::vector<unsigned char> buf(16 + 4 * (size_t)kGParams + 8 + 1);
+  const size_t got = std::fread(buf.data(), 1, buf.size(), f);
+  std::fclose(f);
+  if (got != buf.size() - 1) return set_error_detail(PDHGC_ERR_IO, "not a guide weight file (size)");
+  if (std::memcmp(buf.data(), kGuideMagic, 8) != 0 || get_le(buf.data() + 8, 4) != (uint64_t)kGParams ||
+      get_le(buf.data() + 12, 4) != 0)
+    return set_error_detail(PDHGC_ERR_IO, "not a guide weight file (header)");
+  if (get_le(buf.data() + 16 + 4 * (size_t)kGParams, 8) != fnv1a(buf.data() + 16, 4 * (size_t)kGParams))
+    return set_error_detail(PDHGC_ERR_IO, "guide weight file is corrupt (hash)");
+  std::vector<float> w(kGParams);
+  for (int i = 0; i < kGParams; ++i) {
+    const uint32_t bits = (uint32_t)get_le(buf.data() + 16 + 4 * (size_t)i, 4);
+    std::memcpy(&w[i], &bits, 4);
+  }
+  return pdhgc_guide_set_weights(g, w.data());
 }
 
 int pdhgc_guide_infer(pdhgc_guide* g, const uint16_t* feat, int64_t rows, float* p) {

@@ -664,6 +664,7 @@ struct pdhgc_lp {
     float* val32 = nullptr;
   } ch64, ch32;
   int chunked_primal = 0;  // 1: the Halpern loop's primal pass runs chunked (pdhgc_set_primal_layout)
+  int launch_mode = PDHGC_LAUNCH_GRAPH;  // pdhgc_set_launch_mode
   // vectors (internal order)
   double *b_int = nullptr, *sign = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
   int8_t* ge = nullptr;
@@ -997,13 +998,12 @@ int launch_anchor(pdhgc_lp* lp, const DevModel& md, int force, cudaStream_t st) 
   return PDHGC_OK;
 }
 
-// Builds and launches the loop graph of a phase on the handle's stream:
-// while (!done) { P iterations; pre-check; eval; decide; restart; weights }.
-// fp32 selects the FP32-bulk iteration kernels; the evaluation and the
-// decisions are FP64 in both.  Adds the kernels of the executed bodies to
-// lp->launches once the graph has finished (the caller synchronises).
-int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi, bool fp32,
-                bool ring, const RingRec& rr, int64_t* per_body_out) {
+// Enqueues one loop body on `cs`: P iterations; pre-check; eval; decide;
+// restart; weights.  fp32 selects the FP32-bulk iteration kernels; the
+// evaluation and the decisions are FP64 in both.  use_handle: the decision
+// kernel sets the graph's WHILE condition (`handle`) from S->done.
+int enqueue_body(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi, bool fp32,
+                 bool ring, const RingRec& rr, cudaStream_t cs, cudaGraphConditionalHandle handle, int use_handle) {
   const int n = lp->n, m = lp->m;
   const int gnm = grid_for(n > m ? n : m);
   const bool halpern = pi.algorithm == PDHGC_ALG_HALPERN;
@@ -1011,23 +1011,6 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
   const Iter32 w32 = fp32 ? lp->it32 : Iter32{};
   const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
                        lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaGraphCreate(&graph, 0));
-  std::unique_ptr<CUgraph_st, void (*)(cudaGraph_t)> g_guard(graph, [](cudaGraph_t g) { cudaGraphDestroy(g); });
-  cudaGraphConditionalHandle handle;
-  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = handle;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cnode;
-  CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaStream_t cs = lp->cap_stream;
-  CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  const int64_t before = lp->launches;
   int rc = PDHGC_OK;
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
     if (halpern && fp32) {
@@ -1063,9 +1046,9 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
   }
   if (rc == PDHGC_OK) {
     if (halpern)
-      k_decide_h<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
+      k_decide_h<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
     else
-      k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, 1);
+      k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
     k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr, hz);
     lp->launches += 2;
     if (halpern && fp32) rc = launch_anchor(lp, md, 0, cs);  // a restart moved the anchor
@@ -1074,6 +1057,48 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
       lp->launches++;
     }
   }
+  return rc;
+}
+
+// Runs the loop of a phase on the handle's stream until S->done.  Graph mode
+// (the default) builds one graph whose conditional WHILE node repeats the
+// body with no host round trip, and adds the kernels of the executed bodies
+// to lp->launches once the graph has finished (*per_body_out per body; the
+// caller multiplies by S->chunks).  Stream mode (pdhgc_set_launch_mode)
+// enqueues each body as plain launches and reads S->done back after it, so
+// that every kernel is a separate launch a profiler can see; the launches are
+// counted as they are made (*per_body_out = 0).
+int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const PhaseInit& pi, bool fp32,
+                bool ring, const RingRec& rr, int64_t* per_body_out) {
+  if (lp->launch_mode == PDHGC_LAUNCH_STREAM) {
+    *per_body_out = 0;
+    for (;;) {
+      RET(enqueue_body(lp, md, md32, pi, fp32, ring, rr, lp->stream, cudaGraphConditionalHandle{}, 0));
+      int done = 0;
+      CK(cudaMemcpyAsync(&done, &lp->S->done, sizeof(int), cudaMemcpyDeviceToHost, lp->stream));
+      CK(cudaStreamSynchronize(lp->stream));
+      if (done) break;
+    }
+    return PDHGC_OK;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  std::unique_ptr<CUgraph_st, void (*)(cudaGraph_t)> g_guard(graph, [](cudaGraph_t g) { cudaGraphDestroy(g); });
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = lp->cap_stream;
+  CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = lp->launches;
+  const int rc = enqueue_body(lp, md, md32, pi, fp32, ring, rr, cs, handle, 1);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &captured);
   *per_body_out = lp->launches - before;
@@ -2448,6 +2473,13 @@ int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked) {
   return PDHGC_OK;
 }
 
+int pdhgc_set_launch_mode(pdhgc_lp* lp, int32_t mode) {
+  if (!lp || (mode != PDHGC_LAUNCH_GRAPH && mode != PDHGC_LAUNCH_STREAM))
+    return set_err(PDHGC_ERR_INVALID_ARG, "mode must be PDHGC_LAUNCH_GRAPH or PDHGC_LAUNCH_STREAM");
+  lp->launch_mode = mode;
+  return PDHGC_OK;
+}
+
 int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out) {
   if (!lp || !out) return set_err(PDHGC_ERR_INVALID_ARG, "bad argument");
   const pdhgc_lp::Mat* mats[2] = {&lp->A, &lp->T};
@@ -2544,6 +2576,7 @@ const char* pdhgc_strerror(int code) {
     case PDHGC_ERR_TOO_LARGE: return "problem too large";
     case PDHGC_ERR_DEVICE: return "device-side check failed";
     case PDHGC_ERR_BUFFER: return "buffer too small";
+    case PDHGC_ERR_IO: return "file input/output error";
     default: return "unknown error";
   }
 }

@@ -58,11 +58,16 @@ def _nearest(x, lb, ub):
 
 
 def compare(net, lp, corner_seed, threshold=0.9, corner_max_iters=300_000, guided_max_iters=0,
-            phase1_params=None):
+            phase1_params=None, upper_bound=False, extra_thresholds=()):
     """Plain corner phase versus the guided one on the same phase-1 result.
     The plain run judges the network: a held column is wrong when the plain
     corner did not leave it at the bound it was held at.  `phase1_params`
-    (a Params, as for build_dataset) selects e.g. the Halpern loop."""
+    (a Params, as for build_dataset) selects e.g. the Halpern loop.  With
+    `upper_bound`, a third corner phase holds exactly the eligible columns
+    the plain corner left at their hold bound (a perfect predictor, no
+    fallback): the most any hold decision can gain on this LP.  Each of
+    `extra_thresholds` adds a guided run without fallback at that threshold
+    (its holds, wrong holds, status, iterations and seconds)."""
     import torch
     g = P.lp_from_dict(lp)
     r1 = g.solve(phase1_params) if phase1_params is not None else g.solve()
@@ -82,6 +87,32 @@ def compare(net, lp, corner_seed, threshold=0.9, corner_max_iters=300_000, guide
                                    obj_seed=int(corner_seed), max_iters=int(corner_max_iters))
     torch.cuda.synchronize()
     t_guided = time.perf_counter() - t0
+    bound = None
+    if upper_bound:
+        perfect = at_hold_bound & (elig.cpu().numpy() > 0)
+        t0 = time.perf_counter()
+        ru, gu = g.corner_phase_guided(hold=perfect, fallback=False, guided_max_iters=guided_max_iters,
+                                       obj_seed=int(corner_seed), max_iters=int(corner_max_iters))
+        torch.cuda.synchronize()
+        t_perfect = time.perf_counter() - t0
+        bound = dict(held=gu["held"], status=ru["status_name"], iters=ru["iters"], seconds=t_perfect,
+                     corner_measure=ru["corner_measure"], rel_kkt=ru["rel_kkt"],
+                     speedup=t_plain / t_perfect if t_perfect > 0 else None,
+                     iters_ratio=rp["iters"] / ru["iters"] if ru["iters"] else None)
+    sweep = []
+    probs = net.infer(feat) if extra_thresholds else None
+    for th in extra_thresholds:
+        h_th = ((probs >= th) & (elig > 0)).cpu().numpy()
+        t0 = time.perf_counter()
+        rt, gt = g.corner_phase_guided(guide=net, threshold=float(th), fallback=False,
+                                       guided_max_iters=guided_max_iters, obj_seed=int(corner_seed),
+                                       max_iters=int(corner_max_iters))
+        torch.cuda.synchronize()
+        t_th = time.perf_counter() - t0
+        sweep.append(dict(threshold=float(th), held=gt["held"], wrong_holds=int((h_th & ~at_hold_bound).sum()),
+                          status=rt["status_name"], iters=rt["iters"], seconds=t_th,
+                          corner_measure=rt["corner_measure"],
+                          speedup=t_plain / t_th if rt["status_name"] == "CORNER_DONE" and t_th > 0 else None))
     g.close()
     held = int(hold.sum())
     wrong = int((hold & ~at_hold_bound).sum())
@@ -93,4 +124,5 @@ def compare(net, lp, corner_seed, threshold=0.9, corner_max_iters=300_000, guide
                 guided_status=gr["status_name"], guided_iters=gr["guided_iters"], fell_back=bool(gr["fell_back"]),
                 final_status=rg["status_name"], final_iters=rg["iters"], final_corner_measure=rg["corner_measure"],
                 final_rel_kkt=rg["rel_kkt"], guided_seconds=t_guided,
-                speedup=t_plain / t_guided if t_guided > 0 else None)
+                speedup=t_plain / t_guided if t_guided > 0 else None, perfect_predictor=bound,
+                thresholds=sweep)

@@ -30,13 +30,14 @@ lib = C.CDLL(LIB_PATH)
 # ---- constants (include/pdhgc.h) -------------------------------------------
 OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "INVALID_CSR", -3: "NONFINITE", -4: "BOUNDS", -5: "CUDA", -6: "OOM",
-             -7: "NO_PHASE1", -8: "NO_CORNER", -9: "TOO_LARGE", -10: "DEVICE", -11: "BUFFER"}
+             -7: "NO_PHASE1", -8: "NO_CORNER", -9: "TOO_LARGE", -10: "DEVICE", -11: "BUFFER", -12: "IO"}
 STATUS_NAMES = {0: "NONE", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "TIME_LIMIT", 4: "NUMERICAL",
                 5: "CORNER_DONE", 6: "CORNER_LIMIT", 7: "GUIDE_FALLBACK"}
 GUIDE_FEATURES, GUIDE_FEAT_STRIDE, GUIDE_PARAMS = 18, 32, 5441
 FP64, FP32_BULK = 0, 1
 PHASE1, CORNER, DUAL_CORNER = 0, 1, 2
 AVERAGED, HALPERN = 0, 1  # pdhgc_params.algorithm (PDHGC_ALG_*)
+LAUNCH_GRAPH, LAUNCH_STREAM = 0, 1  # pdhgc_set_launch_mode
 
 
 class PdhgcError(RuntimeError):
@@ -110,6 +111,7 @@ _sig = {
     "pdhgc_get_scaling": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
     "pdhgc_get_layout": (C.c_int, [_vp, _vp]),
     "pdhgc_set_primal_layout": (C.c_int, [_vp, C.c_int32]),
+    "pdhgc_set_launch_mode": (C.c_int, [_vp, C.c_int32]),
     "pdhgc_uniform": (C.c_int, [C.c_uint64, C.c_int64, C.c_double, _vp, _vp]),
     "pdhgc_kkt_eval": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp, C.POINTER(Report), _vp]),
@@ -138,6 +140,8 @@ _sig = {
     "pdhgc_guide_destroy": (None, [_vp]),
     "pdhgc_guide_set_weights": (C.c_int, [_vp, _vp]),
     "pdhgc_guide_get_weights": (C.c_int, [_vp, _vp]),
+    "pdhgc_guide_save": (C.c_int, [_vp, C.c_char_p]),
+    "pdhgc_guide_load": (C.c_int, [_vp, C.c_char_p]),
     "pdhgc_guide_infer": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
     "pdhgc_guide_grad": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp, _vp]),
     "pdhgc_guide_train": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int64, C.c_float, C.c_uint64, _vp]),
@@ -278,6 +282,11 @@ class LP:
 
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_kernel_launches(self._h))
+
+    def set_launch_mode(self, mode: int):
+        """pdhgc_set_launch_mode: LAUNCH_GRAPH (default, one conditional graph
+        per phase) or LAUNCH_STREAM (plain launches, one body at a time)."""
+        _check(lib.pdhgc_set_launch_mode(self._h, int(mode)), "pdhgc_set_launch_mode")
 
     def set_primal_layout(self, chunked: bool):
         """pdhgc_set_primal_layout: 0 gathers from global memory (default), 1 stages y in shared memory."""
@@ -550,10 +559,13 @@ class Guide:
         return w
 
     def save(self, path):
-        np.save(path, self.get_weights())
+        """pdhgc_guide_save: the parameter vector to a file."""
+        _check(lib.pdhgc_guide_save(self._h, os.fsencode(path)), "pdhgc_guide_save")
 
     def load(self, path):
-        self.set_weights(np.load(path))
+        """pdhgc_guide_load: the parameter vector from a file written by save
+        (Adam's moments reset)."""
+        _check(lib.pdhgc_guide_load(self._h, os.fsencode(path)), "pdhgc_guide_load")
 
     def infer(self, feat):
         torch = _torch()

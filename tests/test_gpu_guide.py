@@ -393,3 +393,32 @@ def test_free_columns_are_never_eligible():
     assert np.all(np.abs(got - F) <= BF16_REL * np.abs(F) + 1e-30)
     assert np.array_equal(elig.cpu().numpy().astype(bool), E)
     assert not E[free].any()
+
+
+def test_weights_survive_save_and_load(tmp_path):
+    # a file written by pdhgc_guide_save restores the same parameters (and the
+    # same probabilities) in another network; a damaged or foreign file is
+    # refused with IO and leaves the network unchanged
+    w = rounded_weights(4)
+    a = P.Guide(seed=0)
+    a.set_weights(pack(w))
+    path = tmp_path / "net.pdhgcgw"
+    a.save(str(path))
+    b = P.Guide(seed=7)
+    before = b.get_weights()
+    b.load(str(path))
+    assert np.array_equal(b.get_weights(), a.get_weights())
+    F, _ = _random_inputs(500, 2)
+    feat, _ = feat_tensor(F)
+    assert torch.equal(a.infer(feat), b.infer(feat))
+    raw = bytearray(path.read_bytes())
+    assert raw[:8] == b"PDHGCGW1" and len(raw) == 16 + 4 * P.GUIDE_PARAMS + 8
+    raw[100] ^= 0x01
+    bad = tmp_path / "bad.pdhgcgw"
+    bad.write_bytes(bytes(raw))
+    c = P.Guide(seed=7)
+    with pytest.raises(RuntimeError, match="IO"):
+        c.load(str(bad))
+    with pytest.raises(RuntimeError, match="IO"):
+        c.load(str(tmp_path / "missing.pdhgcgw"))
+    assert np.array_equal(c.get_weights(), before)
