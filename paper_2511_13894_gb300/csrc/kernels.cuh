@@ -452,12 +452,27 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) op.accum(acc, rc, v[u], g[u]);
   }
-  for (; k < k1; k += step) {
-    GV<GT, NG> g;
-    const int c = ld_stream(col + k);
+  // the ragged tail (fewer than kBatch entries left) as one predicated batch:
+  // its loads and gathers are in flight together, in the same summation order
+  if (k < k1) {
+    VT v[kBatch];
+    int c[kBatch];
+    GV<GT, NG> g[kBatch];
 #pragma unroll
-    for (int i = 0; i < NG; ++i) g.v[i] = __ldg(op.gsrc(i) + c);
-    op.accum(acc, rc, ld_stream(val + k), g);
+    for (int u = 0; u < kBatch; ++u) {
+      if (k + u * step < k1) {
+        v[u] = ld_stream(val + k + u * step);
+        c[u] = ld_stream(col + k + u * step);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (k + u * step < k1)
+#pragma unroll
+        for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (k + u * step < k1) op.accum(acc, rc, v[u], g[u]);
   }
 }
 
@@ -978,7 +993,11 @@ struct EvalColsOp {
 // step (the last of a chunk, or of the phase) also stores T(z) and z - T(z)
 // for the evaluation; `probe` forms T(z) of the start point only, leaving z.
 // ---------------------------------------------------------------------------
-struct PrimalOpH {
+// kUnitRho: the reflection is known to be 1 when the kernel is launched, so
+// the reflected point is x_bar with no run-time test (the general operator
+// makes the same choice from S->rho; both give the same bits at rho = 1)
+template <bool kUnitRho>
+struct PrimalOpHT {
   using Acc = SumD<1>;
   static constexpr int NQ = 0;
   static constexpr unsigned kMaxMask = 0;
@@ -1001,7 +1020,7 @@ struct PrimalOpH {
   };
   __device__ Pre prefetch(int j) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.x_r[j], S->tau, h.hw[it], S->rho, last};
+    return Pre{md.chat[j], md.lhat[j], md.uhat[j], w.x[j], w.x_r[j], S->tau, h.hw[it], kUnitRho ? 1.0 : S->rho, last};
   }
   __device__ void epilogue_pre(int j, const Acc& a, const Pre& p, double*) const {
     const double g = p.c - a.v[0];
@@ -1010,7 +1029,7 @@ struct PrimalOpH {
     w.xbar[j] = xb;
     if (!probe) {
       // the reflected point x+ + rho (x+ - x); with rho = 1 it is x_bar itself
-      const double r = p.rho == 1.0 ? xb : fma(p.rho, xn - p.x, xn);
+      const double r = (kUnitRho || p.rho == 1.0) ? xb : fma(p.rho, xn - p.x, xn);
       w.x[j] = fma(p.wt, r - p.x0, p.x0);
     }
     if (p.last) {
@@ -1019,8 +1038,10 @@ struct PrimalOpH {
     }
   }
 };
+using PrimalOpH = PrimalOpHT<false>;
 
-struct DualOpH {
+template <bool kUnitRho>
+struct DualOpHT {
   using Acc = SumD<1>;
   static constexpr int NQ = 0;
   static constexpr unsigned kMaxMask = 0;
@@ -1044,13 +1065,13 @@ struct DualOpH {
   };
   __device__ Pre prefetch(int i) const {
     const bool last = probe || it == last_it || S->k + it + 1 == S->max_iters;
-    return Pre{md.bhat[i], w.y[i], w.y_r[i], S->sigma, h.hw[it], S->rho, md.ge[i], last};
+    return Pre{md.bhat[i], w.y[i], w.y_r[i], S->sigma, h.hw[it], kUnitRho ? 1.0 : S->rho, md.ge[i], last};
   }
   __device__ void epilogue_pre(int i, const Acc& a, const Pre& p, double*) const {
     double yn = p.y + p.sigma * (p.b - a.v[0]);
     if (p.ge && (p.ge == kRowDualZero || __double_as_longlong(yn) < 0)) yn = 0.0;
     if (!probe) {
-      const double r = p.rho == 1.0 ? fma(2.0, yn, -p.y) : fma(p.rho, yn - p.y, yn);
+      const double r = (kUnitRho || p.rho == 1.0) ? fma(2.0, yn, -p.y) : fma(p.rho, yn - p.y, yn);
       w.y[i] = fma(p.wt, r - p.y0, p.y0);
     }
     if (p.last) {
@@ -1059,6 +1080,7 @@ struct DualOpH {
     }
   }
 };
+using DualOpH = DualOpHT<false>;
 
 // Halpern check, rows: r_hat = b_hat - A_hat x+ (max(., 0) on '>' rows),
 //   r_hat^2, (r_hat/D_r)^2, max |r_hat/D_r|, b_hat y+, (y+ - y_0)^2,

@@ -1018,6 +1018,12 @@ int enqueue_body(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const
       rc = launch_primal(lp, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, cs, true);
       if (rc == PDHGC_OK)
         rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
+    } else if (halpern && pi.rho == 1.0) {  // the default reflection: the reflected point is x_bar
+      const int last = pi.check_period - 1;
+      rc = launch_primal(lp, PrimalOpHT<true>{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, cs, true);
+      if (rc == PDHGC_OK)
+        rc = launch_tiles(lp, false, true, DualOpHT<true>{lp->S, i, last, 0, lp->it.xbar, md, lp->it, hz}, nullptr,
+                          cs, true);
     } else if (halpern) {
       const int last = pi.check_period - 1;
       rc = launch_primal(lp, PrimalOpH{lp->S, i, last, 0, lp->it.y, md, lp->it, hz}, cs, true);
@@ -1301,6 +1307,10 @@ int setup_chunked(pdhgc_lp* lp, const Csr& T, cudaStream_t st) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkBytes));
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpHT<true>, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpHT<true>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           kChunkBytes));
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2499,6 +2509,7 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
   const DevModel md = lp->have_corner ? model_corner(lp) : model_orig(lp);
   const bool fp32 = lp->params.precision == PDHGC_FP32_BULK;
   const bool halpern = lp->params.algorithm == PDHGC_ALG_HALPERN && lp->have_h;
+  const bool unit_rho = lp->params.reflection == 1.0;  // the operator the loop launches
   const DevModel32 md32 = lp->have_corner ? model32_corner(lp) : model32_orig(lp);
   const DevIter32 it32{lp->it32.x,  lp->it32.y,   lp->it32.xbar, lp->it32.sx, lp->it32.sy,
                        lp->it32.xlo, lp->it32.ylo, lp->it32.xa,   lp->it32.ya};
@@ -2519,6 +2530,8 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
     if (halpern && fp32)
       rc = launch_primal(lp, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, st, false);
+    else if (halpern && unit_rho)
+      rc = launch_primal(lp, PrimalOpHT<true>{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, st, false);
     else if (halpern)
       rc = launch_primal(lp, PrimalOpH{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, st, false);
     else if (fp32)
@@ -2529,6 +2542,9 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     CK(cudaEventRecord(ev[3 * i + 1], st));
     if (halpern && fp32)
       rc = launch_tiles(lp, false, true, DualOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, nullptr, st);
+    else if (halpern && unit_rho)
+      rc = launch_tiles(lp, false, true, DualOpHT<true>{lp->S, 0, 1, 0, lp->it.xbar, md, lp->it, lp->hz}, nullptr,
+                        st);
     else if (halpern)
       rc = launch_tiles(lp, false, true, DualOpH{lp->S, 0, 1, 0, lp->it.xbar, md, lp->it, lp->hz}, nullptr, st);
     else if (fp32)
