@@ -339,10 +339,11 @@ def kernel_roofline(m, n, nnz, fp32, halpern, ms_primal, ms_dual, peak, peak_kin
     dom = "primal" if ms_primal >= ms_dual else "dual"
     ms_dom, b_dom, f_dom = (ms_primal, b_primal, f_primal) if dom == "primal" else (ms_dual, b_dual, f_dual)
     achieved = b_dom / (ms_dom * 1e-3) / 1e9
-    key = ("halpern_" if halpern else "") + "dram_bytes_per_launch_" + dom
+    key = ("halpern32_" if halpern and fp32 else "halpern_" if halpern else "fp32_" if fp32 else "") \
+        + "dram_bytes_per_launch_" + dom
     roofline = {
-        # the record holds the FP64 kernels' counters only
-        "traffic": float(traffic_rec[key]) if traffic_rec and not fp32 and key in traffic_rec else None,
+        # the record holds the counters of the kernels it names (null for others)
+        "traffic": float(traffic_rec[key]) if traffic_rec and key in traffic_rec else None,
         "kernel": ("spmv<PrimalOp" if dom == "primal" else "spmv<DualOp")
                   + ("H32>" if halpern and fp32 else "H>" if halpern else "32>" if fp32 else ">")
                   + f" ({dom} step)",
@@ -689,6 +690,11 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
             "corner": {"done": cdone, "lps": len(rc), "iters_sum": sum(r["iters"] for r in rc),
                        "iters_max": max(r["iters"] for r in rc),
                        "corner_measure_sum": sum(r["corner_measure"] for r in rc)},
+            "lp_seconds": {"note": "each LP's own phase-1 + corner device time (its slowest LP bounds the step)",
+                           "max": max(a["seconds"] + b["seconds"] for a, b in zip(r1, rc)),
+                           "p50": float(np.median([a["seconds"] + b["seconds"] for a, b in zip(r1, rc)])),
+                           "p90": float(np.percentile([a["seconds"] + b["seconds"] for a, b in zip(r1, rc)], 90)),
+                           "sum": sum(a["seconds"] + b["seconds"] for a, b in zip(r1, rc))},
             "sequential_fp64": seq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_batch (whole step)",
@@ -959,7 +965,8 @@ def main():
         roofline["gather"] = {"gathers_per_launch": nz, "vector_elems": g_len, "elem_bytes": g_bytes,
                               "ceiling_ms": ms_g, "ceiling_gathers_per_s": nz / (ms_g * 1e-3),
                               "achieved_gathers_per_s": nz / (ms_dom * 1e-3), "frac": ms_g / ms_dom,
-                              "note": "pdhgc_probe_gather: the same count of random loads alone"}
+                              "note": "pdhgc_probe_gather: the same count of random loads alone, at the "
+                                      "steady-state rate of a launch of 16 times as many"}
         roofline["step"] = step_roofline(b_primal + b_dual, total_ms, total_iters, peak)
         r1, rc = reps[-1]
         return dict(value=value, total_ms=total_ms, steps=steps, warmup=warmup, total_iters=total_iters,

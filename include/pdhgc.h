@@ -260,8 +260,8 @@ int pdhgc_get_scaling(pdhgc_lp* lp, double* d_row, double* d_col, double* scalar
  * pdhgc_get_layout — how the matrix passes split the rows of A (out[0..3])
  * and of A' (out[4..7]) over the SpMV's row segments, as planned at
  * lp_create: the number of blocks that each own one row longer than 4096
- * nonzeros (one CTA per row), of blocks of warp-per-row rows (129..4096
- * nonzeros), of SELL-32 blocks (rows of at most 128 nonzeros), and the
+ * nonzeros (one CTA per row), of blocks of warp-per-row rows (257..4096
+ * nonzeros), of SELL-32 blocks (rows of at most 256 nonzeros), and the
  * number of rows in the CTA segment.  `out` is a host array of 8 int64.
  * (The Halpern loop's primal pass can instead run a chunked layout; see
  * pdhgc_set_primal_layout.)
@@ -688,10 +688,13 @@ int64_t pdhgc_kernel_launches(const pdhgc_lp* lp);
 /*
  * pdhgc_probe_gather — the random-gather ceiling the SpMV passes run against
  * (a measurement utility; the paper has no counterpart).  Times `reps`
- * launches of a kernel that makes `count` loads of elem_bytes (4 or 8) at
- * hashed uniform positions of a device vector of n_vec elements (resident in
- * L2 after a warm launch), 8 independent loads in flight per thread, and
- * writes the mean milliseconds per launch.  Allocates and frees the vector.
+ * launches of a kernel that makes 16 * `count` loads of elem_bytes (4 or 8)
+ * at hashed uniform positions of a device vector of n_vec elements (resident
+ * in L2 after a warm launch), 8 independent loads in flight per thread, and
+ * writes the mean milliseconds per `count` loads (a launch's time / 16: the
+ * steady-state rate, without the launch latency and the grid's tail that a
+ * launch of only `count` loads would include).  Allocates and frees the
+ * vector.
  * Errors: INVALID_ARG, CUDA, OOM.
  */
 int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t reps, double* ms_out,

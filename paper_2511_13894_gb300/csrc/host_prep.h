@@ -30,8 +30,8 @@ namespace pdhgc {
 constexpr int kBlock = 256;          // threads per CTA of the SpMV kernel
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kSellH = 32;           // rows per slice (one warp)
-constexpr int kColsPerWarp = 16;     // SELL columns one warp takes
-constexpr int kSellMaxLen = kColsPerWarp * kWarpsPerBlock;  // longest row kept in SELL (128)
+constexpr int kColsPerWarp = 32;     // SELL columns one warp takes (16 measured 1.5-2 us slower per pass)
+constexpr int kSellMaxLen = kColsPerWarp * kWarpsPerBlock;  // longest row kept in SELL (256)
 constexpr int kWarpMaxLen = 4096;    // longest row given to a single warp
 constexpr int kPad = 8;              // trailing padding elements of every device array
 

@@ -389,6 +389,31 @@ __device__ __forceinline__ int ld_stream(const int* p) {
 #endif
 }
 
+// Gathers of the iterate vector (random entries, reused across the pass):
+// read-only path, L1 allocation as usual; PDHGC_GATHER_HINT = 1 asks L1 to
+// keep them over other lines (evict_last)
+#ifndef PDHGC_GATHER_HINT
+#define PDHGC_GATHER_HINT 0
+#endif
+__device__ __forceinline__ double ld_gather(const double* p) {
+#if PDHGC_GATHER_HINT
+  double v;
+  asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ float ld_gather(const float* p) {
+#if PDHGC_GATHER_HINT
+  float v;
+  asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+
 template <class T, int NG>
 struct GV {
   T v[NG];
@@ -448,7 +473,7 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
 #pragma unroll
     for (int u = 0; u < kBatch; ++u)
 #pragma unroll
-      for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+      for (int i = 0; i < NG; ++i) g[u].v[i] = ld_gather(op.gsrc(i) + c[u]);
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) op.accum(acc, rc, v[u], g[u]);
   }
@@ -469,7 +494,7 @@ __device__ __forceinline__ void row_dot_global(const Op& op, typename Op::Acc& a
     for (int u = 0; u < kBatch; ++u)
       if (k + u * step < k1)
 #pragma unroll
-        for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+        for (int i = 0; i < NG; ++i) g[u].v[i] = ld_gather(op.gsrc(i) + c[u]);
 #pragma unroll
     for (int u = 0; u < kBatch; ++u)
       if (k + u * step < k1) op.accum(acc, rc, v[u], g[u]);
@@ -627,7 +652,7 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
       for (int u = 0; u < kBatch; ++u)
         if (j + u < jend)
 #pragma unroll
-          for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+          for (int i = 0; i < NG; ++i) g[u].v[i] = ld_gather(op.gsrc(i) + c[u]);
       VT vn[kBatch];
       int cn[kBatch];
 #pragma unroll
@@ -662,7 +687,7 @@ __global__ void __launch_bounds__(kBlock, PDHGC_MIN_BLOCKS)
       for (int u = 0; u < kBatch; ++u)
         if (j + u < jend)
 #pragma unroll
-          for (int i = 0; i < NG; ++i) g[u].v[i] = __ldg(op.gsrc(i) + c[u]);
+          for (int i = 0; i < NG; ++i) g[u].v[i] = ld_gather(op.gsrc(i) + c[u]);
 #pragma unroll
       for (int u = 0; u < kBatch; ++u)
         if (j + u < jend) op.accum(acc, rc, v[u], g[u]);

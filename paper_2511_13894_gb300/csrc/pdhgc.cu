@@ -573,10 +573,13 @@ __global__ void k_unpermute(int len, const int* perm, const double* a, const dou
   out[perm[i]] = v;
 }
 
-// random-gather ceiling: count loads of v[h(i)] with h a multiplicative
+// random-gather ceiling: `count` loads of v[h(i)] with h a multiplicative
 // hash onto [0, n_vec), kGatherProbeBatch independent loads in flight per
-// thread (as the SpMV keeps them); the sum is kept live through `sink`
+// thread; the sum is kept live through `sink`.  A launch makes
+// kGatherProbeScale times more loads than it is charged for, so that the
+// launch latency and the grid's ramp and tail do not set the rate
 constexpr int kGatherProbeBatch = 8;
+constexpr int kGatherProbeScale = 16;
 template <class T>
 __global__ void k_gather_probe(const T* __restrict__ v, long long n_vec, long long count, double* sink) {
   const long long stride = (long long)gridDim.x * blockDim.x * kGatherProbeBatch;
@@ -2448,14 +2451,15 @@ int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long loads = count * kGatherProbeScale;
   const long long per_block = 256LL * kGatherProbeBatch;
-  long long grid = (count + per_block - 1) / per_block;
+  long long grid = (loads + per_block - 1) / per_block;
   if (grid > (long long)sms * 8) grid = (long long)sms * 8;
   auto launch = [&]() {
     if (elem_bytes == 8)
-      k_gather_probe<double><<<(unsigned)grid, 256, 0, st>>>(static_cast<const double*>(vec), n_vec, count, sink);
+      k_gather_probe<double><<<(unsigned)grid, 256, 0, st>>>(static_cast<const double*>(vec), n_vec, loads, sink);
     else
-      k_gather_probe<float><<<(unsigned)grid, 256, 0, st>>>(static_cast<const float*>(vec), n_vec, count, sink);
+      k_gather_probe<float><<<(unsigned)grid, 256, 0, st>>>(static_cast<const float*>(vec), n_vec, loads, sink);
   };
   launch();  // warm: the vector into L2
   CKL();
@@ -2471,7 +2475,7 @@ int pdhgc_probe_gather(int64_t n_vec, int64_t count, int32_t elem_bytes, int32_t
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CKL();
-  *ms_out = (double)ms / reps;
+  *ms_out = (double)ms / reps / kGatherProbeScale;
   return PDHGC_OK;
 }
 

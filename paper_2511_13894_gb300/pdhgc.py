@@ -642,8 +642,8 @@ def uniform(seed: int, n: int, obj_scale: float = 1.0):
 
 
 def probe_gather(n_vec: int, count: int, elem_bytes: int = 8, reps: int = 20) -> float:
-    """pdhgc_probe_gather: mean ms per launch of `count` random loads from an
-    L2-resident vector of n_vec elements."""
+    """pdhgc_probe_gather: ms per `count` random loads from an L2-resident
+    vector of n_vec elements, at the steady-state rate of long launches."""
     out = np.zeros(1)
     _check(lib.pdhgc_probe_gather(int(n_vec), int(count), int(elem_bytes), int(reps), out.ctypes.data,
                                   _current_stream()), "pdhgc_probe_gather")

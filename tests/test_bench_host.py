@@ -78,12 +78,13 @@ def test_headline_bound_follows_the_larger_fraction():
 def test_kernel_roofline(fp32, halpern, ms, alg_bytes, kernel):
     # the 100k x 400k workload with the replayed durations of the default bench
     m, n, nnz = 100000, 400000, 3206827
-    rec = {"dram_bytes_per_launch_primal": "57635840", "halpern_dram_bytes_per_launch_primal": "57580032"}
+    rec = {"halpern_dram_bytes_per_launch_primal": "57401600", "halpern32_dram_bytes_per_launch_primal": "40662784"}
     r = bench.kernel_roofline(m, n, nnz, fp32, halpern, ms[0], ms[1], 6789.6, "measured", rec)
     assert r["kernel"] == kernel and r["algorithmic_bytes_per_launch"] == alg_bytes
     assert r["hbm"]["achieved"] == pytest.approx(alg_bytes / (ms[0] * 1e-3) / 1e9)
-    assert r["traffic"] == (None if fp32 else float(rec[("halpern_" if halpern else "") +
-                                                       "dram_bytes_per_launch_primal"]))
+    # the record's counters for the kernel it names, null for kernels it does not hold
+    want = {(False, True): 57401600.0, (True, True): 40662784.0}.get((fp32, halpern))
+    assert r["traffic"] == want
     assert r["bound"] in ("hbm", "alu")
     top = r["fp64"] if r["bound"] == "alu" else r["hbm"]
     assert r["frac"] == top["frac"] and r["frac"] >= min(r["hbm"]["frac"], r["fp64"]["frac"])

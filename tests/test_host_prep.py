@@ -83,13 +83,13 @@ def _run(exe, tmp_path, lp, chunk=None, sms=None):
 
 
 def _layout_lp(seed=0):
-    """300 x 6000: one row of 5000 nonzeros (a CTA row), rows of 200-1000 (warp
+    """300 x 6000: one row of 5000 nonzeros (a CTA row), rows of 300-1000 (warp
     rows), short rows of 0-60 with many ties (SELL-32, empty rows), column 0 in
     every row (a warp row of A'); entries of a row in random column order."""
     rng = np.random.default_rng(seed)
     m, n = 300, 6000
     lens = rng.integers(1, 61, size=m)
-    lens[[3, 50, 77, 120, 200, 250]] = rng.integers(200, 1001, size=6)  # warp rows
+    lens[[3, 50, 77, 120, 200, 250]] = rng.integers(300, 1001, size=6)  # warp rows
     lens[17] = 5000                                                     # a CTA row
     lens[[8, 9, 60, 61, 130, 131, 210, 211, 280, 299]] = 0              # empty rows
     cols, rp = [], [0]
