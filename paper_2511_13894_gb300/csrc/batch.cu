@@ -12,7 +12,9 @@
 // graph (queue reset + the persistent kernel).  Tail handoff: once the queue
 // is empty and only a few LPs still run, a long-running LP stops at its next
 // check and the host finishes it on the single-LP path (whole-GPU graph
-// loop), several concurrently on their own streams.
+// loop), several concurrently on their own streams; the host watches the
+// running kernel's report statuses and starts each handed-off LP at once,
+// while the kernel finishes its other LPs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,10 +90,19 @@ struct pdhgc_batch {
   long long handoff_min_iters = 8192;
   std::vector<pdhgc_report> ext_rep1, ext_repc;  // reports of handed-off LPs
   std::vector<char> ext1, extc;                  // 1: that phase's result came from the single-LP path
+  // watching the running batched kernel for handoffs: a stream for the status
+  // copies, pinned host statuses (2 x count), events around the kernel
+  cudaStream_t poll_stream = nullptr;
+  int32_t* h_stat = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   ~pdhgc_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     for (void* q : allocs) cudaFree(q);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (poll_stream) cudaStreamDestroy(poll_stream);
+    if (h_stat) cudaFreeHost(h_stat);
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_done) cudaEventDestroy(ev_done);
   }
 };
 
@@ -287,48 +298,103 @@ int finish_on_single_path(pdhgc_batch* B, int k, int mode, const pdhgc_params& p
   return rc;
 }
 
-// the LPs a batched phase handed off, finished concurrently.  phase 0 or 1:
-// that phase's handoffs; 2 (the fused call): an LP handed off in phase 1
-// runs both phases on the single-LP path, one handed off in its corner phase
-// runs the corner phase there (mode 1)
-int run_handoffs(pdhgc_batch* B, int phase, const pdhgc_params& p, const pdhgc_corner_params* cp) {
+// Runs a batched phase and finishes the LPs it hands off on the single-LP
+// path, each from its own host thread and stream.  While the batched kernel
+// runs, the host copies the LPs' statuses (a strided copy of the status
+// field of the device reports, on a stream of its own) every few hundred
+// microseconds and starts a worker as soon as an LP shows the handoff
+// status, so that the handed-off LPs run while the batched kernel finishes
+// its other LPs, on the SMs its exited CTAs leave free.  phase 0 or 1: that
+// phase's handoffs; 2 (the fused call): an LP handed off in phase 1 runs
+// both phases on the single-LP path, one handed off in its corner phase runs
+// the corner phase there (mode 1).  The reports are copied to h_rep1 /
+// h_repc when the kernel has finished.
+int run_batch_and_handoffs(pdhgc_batch* B, const BatchParams& bp, int phase, cudaStream_t st, const pdhgc_params& p,
+                           const pdhgc_corner_params* cp) {
+  const int count = B->count;
+  if (!B->poll_stream) BCK(cudaStreamCreateWithFlags(&B->poll_stream, cudaStreamNonBlocking));
+  if (!B->h_stat) BCK(cudaMallocHost(&B->h_stat, 2 * (size_t)count * sizeof(int32_t)));
+  if (!B->ev_start) BCK(cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming));
+  if (!B->ev_done) BCK(cudaEventCreateWithFlags(&B->ev_done, cudaEventDisableTiming));
+  // statuses start at 0 (NONE): a report of an earlier call never reads as a handoff
+  BCK(cudaMemsetAsync(B->d_rep, 0, count * sizeof(BatchReport), st));
+  BCK(cudaMemsetAsync(B->d_rep2, 0, count * sizeof(BatchReport), st));
+  BCK(cudaEventRecord(B->ev_start, st));
+  RET(run_batch(B, bp, phase, st));
+  BCK(cudaEventRecord(B->ev_done, st));
+  BCK(cudaStreamWaitEvent(B->poll_stream, B->ev_start, 0));
   std::vector<int> ks, modes;
-  for (int k = 0; k < B->count; ++k) {
-    if (phase == 2) {
-      if (B->h_rep1[k].status == kStatusHandoff) {
-        ks.push_back(k);
-        modes.push_back(2);
-      } else if (B->h_repc[k].status == kStatusHandoff) {
-        ks.push_back(k);
-        modes.push_back(1);
-      }
-    } else if ((phase ? B->h_repc : B->h_rep1)[k].status == kStatusHandoff) {
-      ks.push_back(k);
-      modes.push_back(phase);
+  std::vector<char> started(count, 0);
+  std::vector<int> rcs(count, PDHGC_OK);
+  std::vector<std::string> errs(count);
+  std::vector<int64_t> lcount(count, 0);
+  std::vector<std::thread> th;
+  int rc = PDHGC_OK;
+  // the handoff mode of LP k from the statuses s1 (phase 1 or the phase run)
+  // and s2 (corner, fused call), or -1
+  auto mode_of = [&](int32_t s1, int32_t s2) {
+    if (phase != 2) return s1 == kStatusHandoff ? phase : -1;
+    if (s1 == kStatusHandoff) return 2;
+    if (s2 == kStatusHandoff && s1 != 0) return 1;  // phase 1 finished in the batch
+    return -1;
+  };
+  auto start = [&](int k, int mode) {
+    started[k] = 1;
+    ks.push_back(k);
+    modes.push_back(mode);
+    try {
+      th.emplace_back([&, k, mode] { rcs[k] = finish_on_single_path(B, k, mode, p, cp, errs[k], lcount[k]); });
+    } catch (...) {
+      rcs[k] = finish_on_single_path(B, k, mode, p, cp, errs[k], lcount[k]);  // no thread: finish it here
+    }
+  };
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(B->ev_done);
+    if (q != cudaSuccess && q != cudaErrorNotReady) {
+      rc = set_berr(PDHGC_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(q));
+      break;
+    }
+    if (q == cudaSuccess) break;
+    cudaError_t e = cudaMemcpy2DAsync(B->h_stat, sizeof(int32_t), B->d_rep, sizeof(BatchReport), sizeof(int32_t),
+                                      count, cudaMemcpyDeviceToHost, B->poll_stream);
+    if (e == cudaSuccess && phase == 2)
+      e = cudaMemcpy2DAsync(B->h_stat + count, sizeof(int32_t), B->d_rep2, sizeof(BatchReport), sizeof(int32_t),
+                            count, cudaMemcpyDeviceToHost, B->poll_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->poll_stream);
+    if (e != cudaSuccess) {
+      rc = set_berr(PDHGC_ERR_CUDA, std::string("handoff status copy: ") + cudaGetErrorString(e));
+      break;
+    }
+    for (int k = 0; k < count; ++k) {
+      if (started[k]) continue;
+      const int mode = mode_of(B->h_stat[k], phase == 2 ? B->h_stat[count + k] : 0);
+      if (mode >= 0) start(k, mode);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(300));
+  }
+  // the kernel has finished (or failed): the final reports, and any handoff
+  // the last status copy had not seen yet
+  if (rc == PDHGC_OK) {
+    cudaError_t e = cudaMemcpyAsync((phase == 1 ? B->h_repc : B->h_rep1).data(), B->d_rep,
+                                    count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && phase == 2)
+      e = cudaMemcpyAsync(B->h_repc.data(), B->d_rep2, count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = set_berr(PDHGC_ERR_CUDA, std::string("report copy: ") + cudaGetErrorString(e));
+  }
+  if (rc == PDHGC_OK) {
+    const std::vector<BatchReport>& r1 = phase == 1 ? B->h_repc : B->h_rep1;
+    for (int k = 0; k < count; ++k) {
+      if (started[k]) continue;
+      const int mode = mode_of(r1[k].status, phase == 2 ? B->h_repc[k].status : 0);
+      if (mode >= 0) start(k, mode);
     }
   }
-  if (ks.empty()) return PDHGC_OK;
-  // each worker writes only its LP's slots (result buffers, report, flag)
-  std::vector<int> rcs(ks.size(), PDHGC_OK);
-  std::vector<std::string> errs(ks.size());
-  std::vector<int64_t> lcount(ks.size(), 0);
-  std::vector<std::thread> th;
-  size_t started = 0;
-  try {
-    for (; started < ks.size(); ++started)
-      th.emplace_back([&, started] {
-        rcs[started] = finish_on_single_path(B, ks[started], modes[started], p, cp, errs[started],
-                                             lcount[started]);
-      });
-  } catch (...) {
-    // no more threads: finish the rest on this one
-  }
-  for (size_t i = started; i < ks.size(); ++i)
-    rcs[i] = finish_on_single_path(B, ks[i], modes[i], p, cp, errs[i], lcount[i]);
   for (auto& t : th) t.join();
-  for (size_t i = 0; i < ks.size(); ++i) B->launches += lcount[i];
-  for (size_t i = 0; i < ks.size(); ++i)
-    if (rcs[i] != PDHGC_OK) return set_berr(rcs[i], errs[i]);
+  for (int k : ks) B->launches += lcount[k];
+  if (rc != PDHGC_OK) return rc;
+  for (int k : ks)
+    if (rcs[k] != PDHGC_OK) return set_berr(rcs[k], errs[k]);
   return PDHGC_OK;
 }
 
@@ -646,10 +712,7 @@ int pdhgc_batch_solve(pdhgc_batch* B, const pdhgc_params* params, pdhgc_report* 
   BatchParams bp = make_params(p, nullptr);
   bp.handoff_running = B->handoff_running;
   bp.handoff_min_iters = B->handoff_min_iters;
-  RET(run_batch(B, bp, 0, st));
-  BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  RET(run_handoffs(B, 0, p, nullptr));
+  RET(run_batch_and_handoffs(B, bp, 0, st, p, nullptr));
   fill_reports(B, 0, reports);
   B->have_phase1 = 1;
   return PDHGC_OK;
@@ -666,10 +729,7 @@ int pdhgc_batch_corner_phase(pdhgc_batch* B, const pdhgc_corner_params* params, 
   BatchParams bp = make_params(B->params, &cp);
   bp.handoff_running = B->handoff_running;
   bp.handoff_min_iters = B->handoff_min_iters;
-  RET(run_batch(B, bp, 1, st));
-  BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  RET(run_handoffs(B, 1, B->params, &cp));
+  RET(run_batch_and_handoffs(B, bp, 1, st, B->params, &cp));
   fill_reports(B, 1, reports);
   B->have_corner = 1;
   return PDHGC_OK;
@@ -694,11 +754,7 @@ int pdhgc_batch_solve_corner(pdhgc_batch* B, const pdhgc_params* params, const p
   BatchParams bp = make_params(p, &cp);
   bp.handoff_running = B->handoff_running;
   bp.handoff_min_iters = B->handoff_min_iters;
-  RET(run_batch(B, bp, 2, st));
-  BCK(cudaMemcpyAsync(B->h_rep1.data(), B->d_rep, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
-  BCK(cudaMemcpyAsync(B->h_repc.data(), B->d_rep2, B->count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  RET(run_handoffs(B, 2, p, &cp));
+  RET(run_batch_and_handoffs(B, bp, 2, st, p, &cp));
   fill_reports(B, 0, reports1);
   fill_reports(B, 1, reports_c);
   B->have_phase1 = 1;

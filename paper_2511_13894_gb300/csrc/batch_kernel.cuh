@@ -63,8 +63,27 @@ struct BMat {
   const VT* sval;
 };
 
+// asks L2 to fetch [p, p + bytes) from DRAM ahead of its use (a hint: no
+// data moves into the SM and nothing waits on it); p 16-byte aligned, bytes a
+// multiple of 16
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  if (bytes != 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (bytes & 15) == 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// lane 0 of the warp prefetches slice s's values and indices into L2
+template <class VT>
+__device__ __forceinline__ void prefetch_slice(const BMat<VT>& M, int s) {
+  const int base = M.sptr[s], w = M.sw[s];
+  prefetch_l2(M.sval + base, (unsigned)(w * kSellH * sizeof(VT)));
+  prefetch_l2(M.scol + base, (unsigned)(w * kSellH * sizeof(int)));
+}
+
 // one pass: long rows with a warp each (CSR), then SELL-32 slices with a lane
-// per row and kBatch coalesced loads in flight, slices round-robin over warps
+// per row and kBatch coalesced loads in flight, slices round-robin over warps.
+// Each warp asks L2 for its next slice's values and indices while it works on
+// the current one: one CTA streams its LP's matrix alone, and without the
+// look-ahead every batch of loads waits a full DRAM latency.
 template <int BT, class Op>
 __device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* part) {
   using PF = Prefetcher<Op>;
@@ -73,8 +92,10 @@ __device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* p
   constexpr int NG = Op::NG;
   constexpr int W = BT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0 && warp < M.nslices) prefetch_slice(M, warp);
   if (M.long_rows > 0) cta_rows<BT>(M.rp, M.col, M.val, M.long_rows, 32, op, part);
   for (int s = warp; s < M.nslices; s += W) {
+    if (lane == 0 && s + W < M.nslices) prefetch_slice(M, s + W);
     const int base = M.sptr[s], w = M.sw[s];
     const int r = M.long_rows + s * kSellH + lane;
     const bool has = r < M.rows;
@@ -692,12 +713,16 @@ struct LpSolver {
     __syncthreads();
   }
 
+  // the host watches the reports while the kernel runs and starts a handed-off
+  // LP on the single-LP path as soon as its status shows: every earlier write
+  // of the CTA is made visible before the status is
   __device__ bool handed_off(BatchReport* out) {
     if (S->status != kStatusHandoff) return false;
     if (threadIdx.x == 0) {
       BatchReport r{};
       r.status = kStatusHandoff;
       r.iters = S->k;
+      __threadfence_system();
       *out = r;
     }
     __syncthreads();
@@ -762,8 +787,23 @@ struct LpSolver {
   }
 };
 
+// resident CTAs per SM the register allocation of k_batch must allow (0: the
+// compiler's choice under the thread count alone).  1: the compiler may give
+// a thread 65536 / BT registers; with the thread count alone it held the
+// 1024-thread kernel to 32 registers and spilled 34 KB of state, and the
+// batch_512 step took 13.5 s against 9.2 s with one CTA per SM and 64
+// registers.
+#ifndef PDHGC_BATCH_MIN_BLOCKS
+#define PDHGC_BATCH_MIN_BLOCKS 1
+#endif
+#if PDHGC_BATCH_MIN_BLOCKS > 0
+#define PDHGC_BATCH_BOUNDS(bt) __launch_bounds__(bt, PDHGC_BATCH_MIN_BLOCKS)
+#else
+#define PDHGC_BATCH_BOUNDS(bt) __launch_bounds__(bt)
+#endif
+
 template <class VT, int BT>
-__global__ void __launch_bounds__(BT) k_batch(const LpDesc* __restrict__ descs, const int* __restrict__ order,
+__global__ void PDHGC_BATCH_BOUNDS(BT) k_batch(const LpDesc* __restrict__ descs, const int* __restrict__ order,
                                               int count, int* queue, BatchParams bp, int phase,
                                               BatchReport* reps, BatchReport* reps2) {
   extern __shared__ __align__(16) unsigned char s_vec[];
