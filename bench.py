@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="halpern",
                     help="inner loop of the headline: halpern (the default; FP64 headline plus an FP32-bulk "
                          "block), averaged, or both (the Halpern headline plus the averaged loop's arms)")
-    ap.add_argument("--blocks", type=str, default="transport",
+    ap.add_argument("--blocks", type=str, default="transport,batch",
                     help="comma-separated extra workloads measured after the headline (Halpern loop only): "
                          "transport (transportation_1000x2000, FP64 and FP32 bulk), batch (batch_512); "
                          "'' for none")
@@ -682,7 +682,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"lpt-split x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
             "tail_handoff": {"phase1_lps": h1, "corner_lps": hc,
-                             "rule": "once the queue is empty and <= 8 LPs run, an LP past 8192 iterations "
+                             "rule": "once the queue is empty and <= 16 LPs run, an LP past 8192 iterations "
                                      "of its phase finishes on the single-LP path, concurrently"},
             "phase1": {"optimal": done, "lps": len(r1), "iters_sum": sum(r["iters"] for r in r1),
                        "iters_max": max(r["iters"] for r in r1),
