@@ -81,10 +81,13 @@ def parse():
     ap.add_argument("--algorithm", choices=["averaged", "halpern", "both"], default="halpern",
                     help="inner loop of the headline: halpern (the default; FP64 headline plus an FP32-bulk "
                          "block), averaged, or both (the Halpern headline plus the averaged loop's arms)")
-    ap.add_argument("--blocks", type=str, default="transport,batch",
+    ap.add_argument("--blocks", type=str, default="transport,small,batch",
                     help="comma-separated extra workloads measured after the headline (Halpern loop only): "
-                         "transport (transportation_1000x2000, FP64 and FP32 bulk), batch (batch_512); "
-                         "'' for none")
+                         "transport (transportation_1000x2000, FP64 and FP32 bulk), small (random_face_m200_n500, "
+                         "FP64), batch (batch_512); '' for none")
+    ap.add_argument("--batch-handoff", type=str, default=None,
+                    help="R,MIN: the batched solver's tail handoff (at most R LPs running, MIN iterations; "
+                         "default: the library's)")
     ap.add_argument("--block-warmup", type=int, default=1, help="untimed steps of each extra block")
     ap.add_argument("--block-steps", type=int, default=2, help="timed steps of each extra block")
     ap.add_argument("--cpu-threads", type=int, default=0,
@@ -566,6 +569,8 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     B = P.Batch(lps, stream=stream.cuda_stream)
     params = P.default_params(precision=P.FP32_BULK, max_iters=args.phase1_max_iters, algorithm=algorithm)
     tuned = B.tune(256, params)  # schedule autotuner (untimed setup)
+    if args.batch_handoff:
+        B.set_handoff(*(int(v) for v in args.batch_handoff.split(",")))
     cparams = P.default_corner_params(max_iters=args.corner_max_iters, obj_seed=args.corner_seed)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -639,6 +644,8 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
     Be.set_block(tuned["threads"])
     Be.set_layout(tuned["sell"])
     Be.set_lanes(tuned["lanes_a"], tuned["lanes_t"])
+    if args.batch_handoff:
+        Be.set_handoff(*(int(v) for v in args.batch_handoff.split(",")))
     a1, a2 = Be.solve_corner(params, cparams)
     d2h = 0
     for k in range(len(lps)):
@@ -682,7 +689,7 @@ def run_batch_workload(args, rank, world, local, torch, P, dist, barrier):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"lpt-split x{world}"},
             "time_to_corner_s": total_ms / args.steps * 1e-3,
             "tail_handoff": {"phase1_lps": h1, "corner_lps": hc,
-                             "rule": "once the queue is empty and <= 16 LPs run, an LP past 8192 iterations "
+                             "rule": "once the queue is empty and <= 8 LPs run, an LP past 8192 iterations "
                                      "of its phase finishes on the single-LP path, concurrently"},
             "phase1": {"optimal": done, "lps": len(r1), "iters_sum": sum(r["iters"] for r in r1),
                        "iters_max": max(r["iters"] for r in r1),
@@ -1040,6 +1047,22 @@ def main():
             "fp64": block(t64, "Halpern loop, FP64", "f64"),
             "fp32_bulk": block(t32, "Halpern loop, FP32 bulk", f32_dtype),
             "speedup_fp32_vs_fp64_time_to_corner": corner_speedup(t64, t32),
+        }
+    if head_alg == "halpern" and args.workload != "random_face_m200_n500" and "small" in args.blocks:
+        # the 200 x 500 face LP: launch- and latency-bound, not a roofline case
+        # (its iteration touches about 0.1 MB); phase 1 + corner phase per step
+        ls = lpgen.small_face_lp(0)
+        ds = (ls["m"], ls["n"], int(ls["row_ptr"][-1]))
+        gs = P.lp_from_dict(ls, stream=stream.cuda_stream)
+        s64 = run_arm(gs, ds, P.FP64, warmup=3, steps=10)
+        gs.close()
+        sb = block(s64, "Halpern loop, FP64; latency-bound (about 0.1 MB per iteration): iterations/s and "
+                        "microseconds per iteration, not a roofline case", "f64")
+        sb.pop("roofline")
+        extra["random_face_m200_n500"] = {
+            "config": {"workload": "random_face_m200_n500", "m": ds[0], "n": ds[1], "nnz": ds[2],
+                       "algorithm": "halpern", "corner_rows": args.corner_rows},
+            "fp64": sb,
         }
     if head_alg == "halpern" and "batch" in args.blocks and world == 1:
         bargs = argparse.Namespace(**vars(args))

@@ -489,9 +489,10 @@ int pdhgc_batch_tune(pdhgc_batch* batch, const pdhgc_params* params, int32_t tun
  * its handoff status while the batched kernel still runs.  A handed-off LP
  * restarts its phase from the phase's start point on that path; a corner
  * phase handed off there starts from that path's own phase 1 of the LP.  Its
- * report and result are the single-LP path's.  Defaults: 16, 8192
- * (measured on 512 LPs: 8.6 s per step against 9.3 s at 8, 23 s at 32 and
- * 17 s with no handoff); max_running = 0 disables.
+ * report and result are the single-LP path's.  Defaults: 8, 8192 (measured
+ * on 512 LPs: 9.3-9.9 s per step at 8; 8.6 s at 16 alone but 14.2 s at 16
+ * while another process polled the GPU through NVML; 23 s at 32; 17 s with
+ * no handoff); max_running = 0 disables.
  */
 int pdhgc_batch_set_handoff(pdhgc_batch* batch, int32_t max_running, int64_t min_iters);
 

@@ -86,7 +86,7 @@ struct pdhgc_batch {
     std::vector<int8_t> sense;
   };
   std::vector<HostLp> host;
-  int handoff_running = 16;
+  int handoff_running = 8;
   long long handoff_min_iters = 8192;
   std::vector<pdhgc_report> ext_rep1, ext_repc;  // reports of handed-off LPs
   std::vector<char> ext1, extc;                  // 1: that phase's result came from the single-LP path

@@ -668,6 +668,7 @@ struct pdhgc_lp {
   } ch64, ch32;
   int chunked_primal = 0;  // 1: the Halpern loop's primal pass runs chunked (pdhgc_set_primal_layout)
   int launch_mode = PDHGC_LAUNCH_GRAPH;  // pdhgc_set_launch_mode
+  cudaEvent_t loop_done = nullptr;       // blocking-sync event the host waits on for a phase's loop
   // vectors (internal order)
   double *b_int = nullptr, *sign = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
   int8_t* ge = nullptr;
@@ -730,6 +731,7 @@ struct pdhgc_lp {
   ~pdhgc_lp() {
     for (void* q : allocs) cudaFree(q);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (loop_done) cudaEventDestroy(loop_done);
   }
 };
 
@@ -1118,7 +1120,12 @@ int launch_loop(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const 
   std::unique_ptr<CUgraphExec_st, void (*)(cudaGraphExec_t)> e_guard(exec,
                                                                     [](cudaGraphExec_t e) { cudaGraphExecDestroy(e); });
   CK(cudaGraphLaunch(exec, lp->stream));
-  CK(cudaStreamSynchronize(lp->stream));  // the executable graph is destroyed on return
+  // the loop runs for up to seconds: wait on an event with blocking sync, so
+  // that the calling thread sleeps instead of spinning on a core (the batched
+  // solver finishes several handed-off LPs at once, a host thread each)
+  if (!lp->loop_done) CK(cudaEventCreateWithFlags(&lp->loop_done, cudaEventBlockingSync | cudaEventDisableTiming));
+  CK(cudaEventRecord(lp->loop_done, lp->stream));
+  CK(cudaEventSynchronize(lp->loop_done));  // the executable graph is destroyed on return
   return PDHGC_OK;
 }
 

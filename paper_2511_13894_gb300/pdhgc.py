@@ -499,7 +499,7 @@ class Batch:
     def kernel_launches(self) -> int:
         return int(lib.pdhgc_batch_kernel_launches(self._h))
 
-    def set_handoff(self, max_running: int = 16, min_iters: int = 8192):
+    def set_handoff(self, max_running: int = 8, min_iters: int = 8192):
         """pdhgc_batch_set_handoff (max_running = 0 disables the tail handoff)."""
         _check(lib.pdhgc_batch_set_handoff(self._h, int(max_running), int(min_iters)), "pdhgc_batch_set_handoff")
 
