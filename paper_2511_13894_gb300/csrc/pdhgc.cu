@@ -328,27 +328,67 @@ __global__ void k_pre_check(Scalars* S) {
   if (S->chunks > S->max_chunks) S->at_limit = 1;
 }
 
+// The fold of block_fold (256 threads) for several quantities at once: a CTA
+// of kFoldGroups x 256 threads, where group g folds quantities g, g + 4, ...
+// with exactly block_fold's arithmetic (thread t of the group sums entries
+// t, t + 256, ... in order, a shuffle tree per warp, then the 8 warp totals
+// in warp order), so each result is bit for bit block_fold's.  part(qi, &p,
+// &n) names quantity qi's partials; bit qi of max_mask makes it a maximum.
+constexpr int kFoldGroups = 4;
+constexpr int kFoldThreads = 256 * kFoldGroups;
+template <class Parts>
+__device__ inline void group_fold(const Parts& part, int nq, unsigned max_mask, double* q_out,
+                                  double (*s_grp)[8]) {
+  const int g = threadIdx.x >> 8, t = threadIdx.x & 255;
+  const int lane = t & 31, w = t >> 5;
+  for (int r = 0; r * kFoldGroups < nq; ++r) {
+    const int qi = r * kFoldGroups + g;
+    const bool is_max = qi < nq && ((max_mask >> qi) & 1u);
+    double v = 0.0;
+    if (qi < nq) {
+      const double* p = nullptr;
+      int n = 0;
+      part(qi, p, n);
+      for (int k = t; k < n; k += 256) v = is_max ? fmax(v, p[k]) : v + p[k];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = is_max ? fmax(v, o) : v + o;
+    }
+    __syncthreads();
+    if (lane == 0) s_grp[g][w] = v;
+    __syncthreads();
+    if (qi < nq && t == 0) {
+      double tot = s_grp[g][0];
+      for (int w2 = 1; w2 < 8; ++w2) tot = is_max ? fmax(tot, s_grp[g][w2]) : tot + s_grp[g][w2];
+      q_out[qi] = tot;
+    }
+  }
+  __syncthreads();
+}
+
 // Fold the KKT partials, then: termination (Section 2 test, or the Section
 // 3.1 rule in the corner phase), limits, and the adaptive restart with the
 // primal-weight update.  mode 0: initial restart point only.
 __global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, const double* __restrict__ pT,
                          int ntT, int mode, cudaGraphConditionalHandle h, int use_handle) {
-  __shared__ double s_tmp[32];
+  __shared__ double s_grp[kFoldGroups][8];
   __shared__ double q[22];
   if (S->done) {
     if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, 0u);
     return;
   }
-  for (int qi = 0; qi < 10; ++qi) {
-    const double v = block_fold(pA + (size_t)qi * ntA, ntA, qi == 2 || qi == 7, s_tmp);
-    if (threadIdx.x == 0) q[qi] = v;
-    __syncthreads();
-  }
-  for (int qi = 0; qi < 12; ++qi) {
-    const double v = block_fold(pT + (size_t)qi * ntT, ntT, qi == 2 || qi == 8, s_tmp);
-    if (threadIdx.x == 0) q[10 + qi] = v;
-    __syncthreads();
-  }
+  // rows: quantities 0..9 of pA (2 and 7 maxima); columns: 10..21 of pT (2 and 8)
+  auto parts = [&](int qi, const double*& p, int& n) {
+    if (qi < 10) {
+      p = pA + (size_t)qi * ntA;
+      n = ntA;
+    } else {
+      p = pT + (size_t)(qi - 10) * ntT;
+      n = ntT;
+    }
+  };
+  group_fold(parts, 22, (1u << 2) | (1u << 7) | (1u << 12) | (1u << 18), q, s_grp);
   if (threadIdx.x != 0) return;
   if (mode == 0) {
     decide_step(S, q, 0);
@@ -362,22 +402,23 @@ __global__ void k_decide(Scalars* S, const double* __restrict__ pA, int ntA, con
 // Fold the 7 + 7 Halpern check quantities, then decide_halpern.
 __global__ void k_decide_h(Scalars* S, const double* __restrict__ pA, int ntA, const double* __restrict__ pT,
                            int ntT, int mode, cudaGraphConditionalHandle h, int use_handle) {
-  __shared__ double s_tmp[32];
+  __shared__ double s_grp[kFoldGroups][8];
   __shared__ double q[14];
   if (S->done) {
     if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, 0u);
     return;
   }
-  for (int qi = 0; qi < 7; ++qi) {
-    const double v = block_fold(pA + (size_t)qi * ntA, ntA, qi == 2, s_tmp);
-    if (threadIdx.x == 0) q[qi] = v;
-    __syncthreads();
-  }
-  for (int qi = 0; qi < 7; ++qi) {
-    const double v = block_fold(pT + (size_t)qi * ntT, ntT, qi == 2, s_tmp);
-    if (threadIdx.x == 0) q[7 + qi] = v;
-    __syncthreads();
-  }
+  // rows: quantities 0..6 of pA; columns: 7..13 of pT (2 and 9 maxima)
+  auto parts = [&](int qi, const double*& p, int& n) {
+    if (qi < 7) {
+      p = pA + (size_t)qi * ntA;
+      n = ntA;
+    } else {
+      p = pT + (size_t)(qi - 7) * ntT;
+      n = ntT;
+    }
+  };
+  group_fold(parts, 14, (1u << 2) | (1u << 9), q, s_grp);
   if (threadIdx.x != 0) return;
   decide_halpern(S, q, mode);
   if (mode != 0 && use_handle) cudaGraphSetConditional(h, S->done ? 0u : 1u);
@@ -1057,9 +1098,9 @@ int enqueue_body(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const
   }
   if (rc == PDHGC_OK) {
     if (halpern)
-      k_decide_h<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
+      k_decide_h<<<1, kFoldThreads, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
     else
-      k_decide<<<1, 256, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
+      k_decide<<<1, kFoldThreads, 0, cs>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 1, handle, use_handle);
     k_restart_apply<<<gnm, 256, 0, cs>>>(lp->S, n, m, lp->it, w32, rr, hz);
     lp->launches += 2;
     if (halpern && fp32) rc = launch_anchor(lp, md, 0, cs);  // a restart moved the anchor
@@ -1151,7 +1192,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
   const bool ring = pi.phase == 0;
   const RingRec rr = ring ? RingRec{lp->ring_x, lp->ring_z, lp->z_cur, lp->z_avg} : RingRec{};
   RET(launch_eval(lp, md, st, ring));
-  k_decide<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+  k_decide<<<1, kFoldThreads, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
   lp->launches++;
   CKL();
   if (ring) {
@@ -1171,7 +1212,7 @@ int run_phase(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const Ph
       RET(launch_tiles(lp, false, true, DualOpH{lp->S, 0, 0, 1, lp->it.xbar, md, lp->it, hz}, nullptr, st));
     }
     RET(launch_eval_h(lp, md, st, false));
-    k_decide_h<<<1, 256, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
+    k_decide_h<<<1, kFoldThreads, 0, st>>>(lp->S, lp->pA, lp->ntA, lp->pT, lp->ntT, 0, cudaGraphConditionalHandle{}, 0);
     k_halpern_weights<<<1, 256, 0, st>>>(lp->S, hz.hw, hz.hs, pi.check_period);
     lp->launches += 2;
     CKL();
