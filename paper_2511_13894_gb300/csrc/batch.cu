@@ -373,7 +373,9 @@ int run_batch_and_handoffs(pdhgc_batch* B, const BatchParams& bp, int phase, cud
     std::this_thread::sleep_for(std::chrono::microseconds(300));
   }
   // the kernel has finished (or failed): the final reports, and any handoff
-  // the last status copy had not seen yet
+  // the last status copy had not seen yet.  After a failed status copy the
+  // batch's stream is still drained, so that no kernel of this call outlives it.
+  if (rc != PDHGC_OK) cudaStreamSynchronize(st);
   if (rc == PDHGC_OK) {
     cudaError_t e = cudaMemcpyAsync((phase == 1 ? B->h_repc : B->h_rep1).data(), B->d_rep,
                                     count * sizeof(BatchReport), cudaMemcpyDeviceToHost, st);
