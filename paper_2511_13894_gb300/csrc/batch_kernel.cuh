@@ -71,6 +71,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// matrix entries in flight per lane in the batched SELL pass, and how many of
+// its own slices ahead a warp asks L2 for (tuning knobs)
+#ifndef PDHGC_BATCH_KBATCH
+#define PDHGC_BATCH_KBATCH 4
+#endif
+#ifndef PDHGC_BATCH_AHEAD
+#define PDHGC_BATCH_AHEAD 1
+#endif
+constexpr int kBatchB = PDHGC_BATCH_KBATCH;
+
 // lane 0 of the warp prefetches slice s's values and indices into L2
 template <class VT>
 __device__ __forceinline__ void prefetch_slice(const BMat<VT>& M, int s) {
@@ -95,7 +105,7 @@ __device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* p
   if (lane == 0 && warp < M.nslices) prefetch_slice(M, warp);
   if (M.long_rows > 0) cta_rows<BT>(M.rp, M.col, M.val, M.long_rows, 32, op, part);
   for (int s = warp; s < M.nslices; s += W) {
-    if (lane == 0 && s + W < M.nslices) prefetch_slice(M, s + W);
+    if (lane == 0 && s + PDHGC_BATCH_AHEAD * W < M.nslices) prefetch_slice(M, s + PDHGC_BATCH_AHEAD * W);
     const int base = M.sptr[s], w = M.sw[s];
     const int r = M.long_rows + s * kSellH + lane;
     const bool has = r < M.rows;
@@ -105,23 +115,23 @@ __device__ void cta_pass(const BMat<typename Op::VT>& M, const Op& op, double* p
     const double rc = has ? op.row_ctx(r) : 0.0;
     typename Op::Acc acc;
     acc.zero();
-    for (int j = 0; j < w; j += kBatch) {
-      VT v[kBatch];
-      int c[kBatch];
+    for (int j = 0; j < w; j += kBatchB) {
+      VT v[kBatchB];
+      int c[kBatchB];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u)
+      for (int u = 0; u < kBatchB; ++u)
         if (j + u < len) {
           v[u] = ld_stream(M.sval + base + (j + u) * kSellH + lane);
           c[u] = ld_stream(M.scol + base + (j + u) * kSellH + lane);
         }
-      GV<GT, NG> g[kBatch];
+      GV<GT, NG> g[kBatchB];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u)
+      for (int u = 0; u < kBatchB; ++u)
         if (j + u < len)
 #pragma unroll
           for (int i = 0; i < NG; ++i) g[u].v[i] = op.gsrc(i)[c[u]];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u)
+      for (int u = 0; u < kBatchB; ++u)
         if (j + u < len) op.accum(acc, rc, v[u], g[u]);
     }
     if (has) PF::epilogue(op, r, acc, pre, part);
