@@ -1726,7 +1726,10 @@ __device__ __forceinline__ void ff_sum(float ah, float al, float bh, float bl, f
   ff_sub(ah, al, -bh, -bl, h, l);
 }
 
-struct PrimalOpH32 {
+// kUnitRho: the reflection is 1, so the reflected point T + (T - z) is the
+// x_bar pair the epilogue already forms (the general operator recomputes it)
+template <bool kUnitRho>
+struct PrimalOpH32T {
   using Acc = SumFF;
   static constexpr int NQ = 0;
   static constexpr unsigned kMaxMask = 0;
@@ -1772,7 +1775,16 @@ struct PrimalOpH32 {
     w.gx[j] = eh + el;
     if (!probe) {
       float oh, ol;
-      ff_halpern(th, tl, p.x, p.xl, p.x0, p.rho, p.s, oh, ol);
+      if constexpr (kUnitRho) {
+        // z <- r + s (z_0 - r) with r = x_bar = (bh, bl), and z_0 - r =
+        // -(eh, el) exactly (TwoSum differences are odd in their arguments)
+        float rh = bh, rl = bl;
+        ff_axpy_ff(rh, rl, p.s, -eh, -el);
+        oh = rh;
+        ol = rl;
+      } else {
+        ff_halpern(th, tl, p.x, p.xl, p.x0, p.rho, p.s, oh, ol);
+      }
       w.x[j] = oh;
       w.xlo[j] = ol;
     }
@@ -1782,6 +1794,7 @@ struct PrimalOpH32 {
     }
   }
 };
+using PrimalOpH32 = PrimalOpH32T<false>;
 
 struct DualOpH32 {
   using Acc = SumFF;

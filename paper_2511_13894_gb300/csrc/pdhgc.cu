@@ -1061,7 +1061,8 @@ int enqueue_body(pdhgc_lp* lp, const DevModel& md, const DevModel32& md32, const
   for (int i = 0; i < pi.check_period && rc == PDHGC_OK; ++i) {
     if (halpern && fp32) {
       const int last = pi.check_period - 1;
-      rc = launch_primal(lp, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, cs, true);
+      rc = pi.rho == 1.0 ? launch_primal(lp, PrimalOpH32T<true>{lp->S, i, last, 0, md32, h32_of(lp), hz}, cs, true)
+                         : launch_primal(lp, PrimalOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, cs, true);
       if (rc == PDHGC_OK)
         rc = launch_tiles(lp, false, true, DualOpH32{lp->S, i, last, 0, md32, h32_of(lp), hz}, nullptr, cs, true);
     } else if (halpern && pi.rho == 1.0) {  // the default reflection: the reflected point is x_bar
@@ -1365,6 +1366,10 @@ int setup_chunked(pdhgc_lp* lp, const Csr& T, cudaStream_t st) {
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           kChunkBytes));
   CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32T<true>, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kChunkBytes));
+  CK(cudaFuncSetAttribute(spmv_chunked<PrimalOpH32T<true>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           kChunkBytes));
   for (int which = 0; which < 2; ++which) {
     pdhgc_lp::Chunked& C = which ? lp->ch32 : lp->ch64;
@@ -2581,7 +2586,8 @@ int pdhgc_profile_iteration(pdhgc_lp* lp, int32_t iters, double* ms_out) {
     CK(cudaEventRecord(ev[3 * i], st));
     // the Halpern loop's kernels as a step inside a chunk (it 0, not a check step)
     if (halpern && fp32)
-      rc = launch_primal(lp, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, st, false);
+      rc = unit_rho ? launch_primal(lp, PrimalOpH32T<true>{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, st, false)
+                    : launch_primal(lp, PrimalOpH32{lp->S, 0, 1, 0, md32, h32_of(lp), lp->hz}, st, false);
     else if (halpern && unit_rho)
       rc = launch_primal(lp, PrimalOpHT<true>{lp->S, 0, 1, 0, lp->it.y, md, lp->it, lp->hz}, st, false);
     else if (halpern)
