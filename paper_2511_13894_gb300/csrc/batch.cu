@@ -418,11 +418,14 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
   int64_t sm = 0, sn = 0, snz = 0;
   BCK(cudaGetDevice(&B->device));
   B->host.resize(count);
-  for (int k = 0; k < count; ++k) {
-    std::string detail;
-    const int rc = prepare_lp(P[k], m[k], n[k], nnz[k], row_ptr[k], col_idx[k], val[k], b[k], c[k],
-                              lb ? lb[k] : nullptr, ub ? ub[k] : nullptr, sense ? sense[k] : nullptr, detail);
-    if (rc != PDHGC_OK) return set_berr(rc, "LP " + std::to_string(k) + ": " + detail);
+  // the LPs are independent: validated and laid out on several host threads
+  // (each writes only its LPs' slots), errors reported for the first bad LP
+  std::vector<int> prc(count, PDHGC_OK);
+  std::vector<std::string> pdetail(count);
+  auto prepare_one = [&](int k) {
+    prc[k] = prepare_lp(P[k], m[k], n[k], nnz[k], row_ptr[k], col_idx[k], val[k], b[k], c[k], lb ? lb[k] : nullptr,
+                        ub ? ub[k] : nullptr, sense ? sense[k] : nullptr, pdetail[k]);
+    if (prc[k] != PDHGC_OK) return;
     auto& h = B->host[k];
     h.m = m[k];
     h.n = n[k];
@@ -434,6 +437,27 @@ int pdhgc_batch_create(pdhgc_batch** out, int32_t count, const int32_t* m, const
     if (lb && lb[k]) h.lb.assign(lb[k], lb[k] + n[k]);
     if (ub && ub[k]) h.ub.assign(ub[k], ub[k] + n[k]);
     if (sense && sense[k]) h.sense.assign(sense[k], sense[k] + m[k]);
+  };
+  {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = std::max(1, std::min(count, (int)std::min(hw == 0 ? 1u : hw, 16u)));
+    std::vector<std::thread> pth;
+    int started = 0;
+    try {
+      for (; started < nt - 1; ++started)
+        pth.emplace_back([&, started] {
+          for (int k = started + 1; k < count; k += nt) prepare_one(k);
+        });
+    } catch (...) {
+      // no more threads: this thread takes the remaining strides
+    }
+    for (int t = started + 1; t < nt; ++t)
+      for (int k = t; k < count; k += nt) prepare_one(k);
+    for (int k = 0; k < count; k += nt) prepare_one(k);
+    for (auto& t : pth) t.join();
+  }
+  for (int k = 0; k < count; ++k) {
+    if (prc[k] != PDHGC_OK) return set_berr(prc[k], "LP " + std::to_string(k) + ": " + pdetail[k]);
     sm += m[k];
     sn += n[k];
     snz += nnz[k];
