@@ -276,14 +276,15 @@ int pdhgc_get_layout(const pdhgc_lp* lp, int64_t* out);
  * chunked = 0 (the default) uses the row segments of pdhgc_get_layout with
  * gathers from global memory; chunked = 1 stages the gathered vector y in
  * shared memory, 200 KB at a time, with one CTA per SM whose warps gather
- * from shared memory (the layout is planned at lp_create: work units of one
- * long column or 32 short ones, their entries grouped by chunk).  On the
+ * from shared memory (the layout is planned by the first call that selects
+ * it, from A' as laid out on the device: work units of one long column or
+ * 32 short ones, their entries grouped by chunk).  On the
  * 100k x 400k LP the chunked pass measured 2-2.5 times slower (each warp
  * runs its units' short per-chunk segments one after another), so it is
  * not the default.  The results differ only by the summation order of the
  * row sums.  Takes effect at the next pdhgc_solve or pdhgc_corner_phase.  A
  * layout choice for measurement and tests (the paper has no counterpart).
- * Errors: INVALID_ARG.
+ * Errors: INVALID_ARG; on the first selection also CUDA, OOM.
  */
 int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked);
 

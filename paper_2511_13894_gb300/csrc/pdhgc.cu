@@ -708,6 +708,7 @@ struct pdhgc_lp {
     float* val32 = nullptr;
   } ch64, ch32;
   int chunked_primal = 0;  // 1: the Halpern loop's primal pass runs chunked (pdhgc_set_primal_layout)
+  bool chunk_ready = false;  // the chunk plans are built on the first request for the chunked layout
   int launch_mode = PDHGC_LAUNCH_GRAPH;  // pdhgc_set_launch_mode
   cudaEvent_t loop_done = nullptr;       // blocking-sync event the host waits on for a phase's loop
   // vectors (internal order)
@@ -1977,7 +1978,6 @@ int pdhgc_lp_create(pdhgc_lp** out, int32_t m, int32_t n, int64_t nnz, const int
   RET(setup_mat(lp.get(), lp->T, P.AT, st));
   lp->ntA = lp->A.nblocks();
   lp->ntT = lp->T.nblocks();
-  RET(setup_chunked(lp.get(), P.AT, st));
   RET(lp->alloc(&lp->err, 1));
   RET(lp->alloc(&lp->b_int, m));
   RET(lp->alloc(&lp->sign, m));
@@ -2536,6 +2536,36 @@ int64_t pdhgc_kernel_launches(const pdhgc_lp* lp) { return lp ? lp->launches : 0
 
 int pdhgc_set_primal_layout(pdhgc_lp* lp, int32_t chunked) {
   if (!lp || (chunked != 0 && chunked != 1)) return set_err(PDHGC_ERR_INVALID_ARG, "chunked must be 0 or 1");
+  if (chunked && !lp->chunk_ready) {
+    // the chunk plan is built on first use (lp_create leaves it out): from
+    // A' as laid out on the device, then the slots take the scaled values the
+    // last scaling left (each solve's scaling refills them)
+    cudaStream_t st = lp->stream;
+    Csr T;
+    T.rows = lp->T.rows;
+    T.cols = lp->m;
+    T.nnz = lp->nnz;
+    T.row_ptr.resize((size_t)T.rows + 1);
+    T.col.resize((size_t)lp->nnz);
+    CK(cudaMemcpyAsync(T.row_ptr.data(), lp->T.rp, T.row_ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (lp->nnz > 0)
+      CK(cudaMemcpyAsync(T.col.data(), lp->T.col, T.col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    RET(setup_chunked(lp, T, st));
+    if (lp->ch64.nslots > 0) {
+      k_sell_fill<<<grid_for(lp->ch64.nslots), 256, 0, st>>>(lp->ch64.map, lp->T.hat, lp->ch64.val64,
+                                                            (int)lp->ch64.nslots);
+      lp->launches++;
+    }
+    if (lp->have32 && lp->ch32.nslots > 0) {
+      k_sell_fill<<<grid_for(lp->ch32.nslots), 256, 0, st>>>(lp->ch32.map, lp->T.hat32, lp->ch32.val32,
+                                                            (int)lp->ch32.nslots);
+      lp->launches++;
+    }
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    lp->chunk_ready = true;
+  }
   lp->chunked_primal = chunked;
   return PDHGC_OK;
 }
