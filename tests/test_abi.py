@@ -135,3 +135,33 @@ def test_package_exports_exist(lib):
     import paper_2511_13894_gb300 as pkg
     for name in pkg._EXPORTS:
         assert getattr(pkg, name) is not None, name
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "pdhgc.h")).read()
+    return {k: int(v) for k, v in re.findall(r"^#define (PDHGC_[A-Z0-9_]+)\s+(-?\d+)", src, flags=re.M)}
+
+
+def test_binding_constants_match_the_header(lib):
+    # every error code, status, precision, result selector, inner loop, launch
+    # mode and guidance size the binding names has the header's value
+    from paper_2511_13894_gb300 import pdhgc as P
+    d = _header_defines()
+    errs = {v: k[len("PDHGC_ERR_"):] for k, v in d.items() if k.startswith("PDHGC_ERR_")}
+    assert errs == P.ERR_NAMES
+    stats = {v: k[len("PDHGC_STATUS_"):] for k, v in d.items() if k.startswith("PDHGC_STATUS_")}
+    assert stats == P.STATUS_NAMES
+    pairs = {"PDHGC_OK": P.OK, "PDHGC_FP64": P.FP64, "PDHGC_FP32_BULK": P.FP32_BULK, "PDHGC_PHASE1": P.PHASE1,
+             "PDHGC_CORNER": P.CORNER, "PDHGC_DUAL_CORNER": P.DUAL_CORNER, "PDHGC_ALG_AVERAGED": P.AVERAGED,
+             "PDHGC_ALG_HALPERN": P.HALPERN, "PDHGC_LAUNCH_GRAPH": P.LAUNCH_GRAPH,
+             "PDHGC_LAUNCH_STREAM": P.LAUNCH_STREAM, "PDHGC_GUIDE_FEATURES": P.GUIDE_FEATURES,
+             "PDHGC_GUIDE_FEAT_STRIDE": P.GUIDE_FEAT_STRIDE, "PDHGC_GUIDE_PARAMS": P.GUIDE_PARAMS}
+    for name, value in pairs.items():
+        assert d[name] == value, name
+
+
+def test_every_error_code_has_a_message(lib):
+    from paper_2511_13894_gb300 import pdhgc as P
+    for code in P.ERR_NAMES:
+        msg = P.lib.pdhgc_strerror(code).decode()
+        assert msg and "unknown" not in msg.lower(), (code, msg)
