@@ -4,12 +4,53 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 #include "../../include/pdhgc.h"
 
 namespace pdhgc {
 
 namespace {
+
+// Runs body(t) for t in [0, parts) on up to `parts` threads (the calling
+// thread takes part 0 and any part whose thread could not start).  Each part
+// writes only its own outputs, so the result does not depend on the threads.
+template <class F>
+void run_parts(int parts, const F& body) {
+  std::vector<std::thread> th;
+  int started = 1;
+  try {
+    for (; started < parts; ++started) th.emplace_back([&body, started] { body(started); });
+  } catch (...) {
+  }
+  for (int t = started; t < parts; ++t) body(t);
+  body(0);
+  for (auto& x : th) x.join();
+}
+
+// threads for a pass over nnz entries: one per 64k entries, at most 16 and at
+// most the machine's
+int parts_for(int64_t nnz) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t cap = std::min<int64_t>(16, hw == 0 ? 1 : (int64_t)hw);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(cap, nnz / 65536));
+}
+
+// splits [0, rows) into `parts` ranges of about equal entry counts (row_ptr
+// prefix sums); bounds has parts + 1 entries
+template <class RP>
+std::vector<int32_t> split_rows(const RP& row_ptr, int32_t rows, int parts) {
+  std::vector<int32_t> bounds(parts + 1, rows);
+  bounds[0] = 0;
+  const int64_t total = (int64_t)row_ptr[rows];
+  int32_t r = 0;
+  for (int t = 1; t < parts; ++t) {
+    const int64_t target = total * t / parts;
+    while (r < rows && (int64_t)row_ptr[r] < target) ++r;
+    bounds[t] = r;
+  }
+  return bounds;
+}
 
 std::vector<int32_t> order_by_decreasing(const std::vector<int64_t>& len) {
   std::vector<int32_t> idx(len.size());
@@ -21,8 +62,32 @@ std::vector<int32_t> order_by_decreasing(const std::vector<int64_t>& len) {
 
 // columns by decreasing length, then by decreasing chunk counts q[.][0..2]
 std::vector<int32_t> order_columns(const std::vector<int64_t>& len, const std::vector<int32_t>& q) {
-  std::vector<int32_t> idx(len.size());
+  const size_t n = len.size();
+  std::vector<int32_t> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
+  // when every length and chunk count fits in 16 bits, the order is that of
+  // the 64-bit key (len, q0, q1, q2) descending, stable: a 4-pass LSD radix
+  // sort of the indices on the complemented key gives it in linear time
+  bool small = true;
+  for (size_t j = 0; j < n && small; ++j)
+    small = len[j] < 65536 && q[3 * j] < 65536 && q[3 * j + 1] < 65536 && q[3 * j + 2] < 65536;
+  if (small) {
+    std::vector<uint64_t> key(n);
+    for (size_t j = 0; j < n; ++j)
+      key[j] = ~(((uint64_t)len[j] << 48) | ((uint64_t)q[3 * j] << 32) | ((uint64_t)q[3 * j + 1] << 16) |
+                 (uint64_t)q[3 * j + 2]);
+    std::vector<int32_t> tmp(n);
+    std::vector<size_t> cnt(65537);
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 16 * pass;
+      std::fill(cnt.begin(), cnt.end(), 0);
+      for (size_t t = 0; t < n; ++t) cnt[((key[idx[t]] >> shift) & 0xffff) + 1]++;
+      for (size_t d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+      for (size_t t = 0; t < n; ++t) tmp[cnt[(key[idx[t]] >> shift) & 0xffff]++] = idx[t];
+      idx.swap(tmp);
+    }
+    return idx;
+  }
   std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
     if (len[a] != len[b]) return len[a] > len[b];
     for (int k = 0; k < 3; ++k)
@@ -279,21 +344,30 @@ int prepare_lp(Prepared& P, int32_t m, int32_t n, int64_t nnz, const int64_t* ro
   double bn = 0.0;
   for (int32_t i = 0; i < m; ++i) bn += b[i] * b[i];
   P.b_norm = std::sqrt(bn);
-  int64_t pos = 0;
+  // row pointers first (a prefix sum of the internal rows' lengths), then the
+  // rows' entries in parallel: each part fills its own rows' slots
   for (int32_t r = 0; r < m; ++r) {
     const int32_t i = P.row_perm[r];
-    const char s = sense ? char(sense[i]) : '=';
-    const double sg = (s == '<') ? -1.0 : 1.0;
-    P.sign[r] = sg;
-    P.ge[r] = (s != '=') ? 1 : 0;
-    P.b_int[r] = sg * b[i];
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      A.col[pos] = P.col_inv[col_idx[e]];
-      A.val[pos] = sg * val[e];
-      ++pos;
-    }
-    A.row_ptr[r + 1] = int32_t(pos);
+    A.row_ptr[r + 1] = A.row_ptr[r] + int32_t(row_ptr[i + 1] - row_ptr[i]);
   }
+  const int parts = parts_for(nnz);
+  const std::vector<int32_t> rb = split_rows(A.row_ptr, m, parts);
+  run_parts(parts, [&](int t) {
+    for (int32_t r = rb[t]; r < rb[t + 1]; ++r) {
+      const int32_t i = P.row_perm[r];
+      const char s = sense ? char(sense[i]) : '=';
+      const double sg = (s == '<') ? -1.0 : 1.0;
+      P.sign[r] = sg;
+      P.ge[r] = (s != '=') ? 1 : 0;
+      P.b_int[r] = sg * b[i];
+      int64_t pos = A.row_ptr[r];
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        A.col[pos] = P.col_inv[col_idx[e]];
+        A.val[pos] = sg * val[e];
+        ++pos;
+      }
+    }
+  });
 
   // internal A': stable counting sort of A's entries by internal column
   Csr& T = P.AT;
@@ -306,14 +380,23 @@ int prepare_lp(Prepared& P, int32_t m, int32_t n, int64_t nnz, const int64_t* ro
   std::vector<int32_t> next(T.row_ptr.begin(), T.row_ptr.end() - 1);
   T.col.resize(nnz);
   T.val.resize(nnz);
-  for (int32_t r = 0; r < m; ++r) {
-    for (int32_t e = A.row_ptr[r]; e < A.row_ptr[r + 1]; ++e) {
-      const int32_t j = A.col[e];
-      const int32_t q = next[j]++;
-      T.col[q] = r;
-      T.val[q] = A.val[e];
+  // each part owns a range of columns (of about equal entry counts) and scans
+  // all of A in row order, placing only its columns' entries: every column's
+  // entries land in increasing row order, as one sequential pass places them
+  const std::vector<int32_t> cb = split_rows(T.row_ptr, n, parts);
+  run_parts(parts, [&](int t) {
+    const int32_t j0 = cb[t], j1 = cb[t + 1];
+    if (j0 >= j1) return;
+    for (int32_t r = 0; r < m; ++r) {
+      for (int32_t e = A.row_ptr[r]; e < A.row_ptr[r + 1]; ++e) {
+        const int32_t j = A.col[e];
+        if (j < j0 || j >= j1) continue;
+        const int32_t q = next[j]++;
+        T.col[q] = r;
+        T.val[q] = A.val[e];
+      }
     }
-  }
+  });
 
   P.c.resize(n);
   P.l.resize(n);

@@ -340,3 +340,51 @@ def test_column_order_is_chunk_aware(dump_exe, tmp_path):
     want = np.lexsort((np.arange(n), -q[:, 2], -q[:, 1], -q[:, 0], -counts))
     assert np.array_equal(a["col_perm"], want)
     assert np.array_equal(a["row_perm"], np.argsort(-rlen, kind="stable"))
+
+
+def test_large_layout_matches_its_definition(dump_exe, tmp_path):
+    # an LP large enough that the layout is built on several host threads (one
+    # per 64k entries) and that rows reach the second staged chunk: the same
+    # definition, checked with sparse arithmetic
+    import scipy.sparse as sp
+    import lpgen
+    lp = lpgen.power_law_lp(30000, 60000, 2000, 7, kmax=3000)
+    rc, a = _run(dump_exe, tmp_path, lp)
+    assert rc == 0
+    m, n = lp["m"], lp["n"]
+    rp = np.asarray(lp["row_ptr"])
+    col = np.asarray(lp["col_idx"])
+    val = np.asarray(lp["val"])
+    nnz = int(rp[-1])
+    assert nnz > 4 * 65536
+    rlen = np.diff(rp)
+    clen = np.bincount(col, minlength=n)
+    assert np.array_equal(a["row_perm"], np.argsort(-rlen, kind="stable"))
+    row_inv = a["row_inv"]
+    assert np.array_equal(row_inv[a["row_perm"]], np.arange(m))
+    # columns: decreasing length, then decreasing counts in the row chunks
+    # [0, C), [C, 2C), [2C, 3C) of the internal row numbering, stable
+    C = int(re.search(r"kChunkBytes = (\d+) \* 1024", open(os.path.join(CSRC, "host_prep.h")).read()).group(1)) * 1024 // 8
+    chunk_of_entry = row_inv[np.repeat(np.arange(m), rlen)] // C
+    q = np.zeros((n, 3), dtype=np.int64)
+    for k in range(3):
+        q[:, k] = np.bincount(col[chunk_of_entry == k], minlength=n)
+    assert q[:, 1].sum() > 0  # the second chunk is populated
+    want = np.lexsort((np.arange(n), -q[:, 2], -q[:, 1], -q[:, 0], -clen))
+    assert np.array_equal(a["col_perm"], want)
+    col_inv = a["col_inv"]
+    # internal A: permuted rows, sign-flipped '<' rows, entries in the user's order
+    sign = np.where(lp["sense"][a["row_perm"]] == LE, -1.0, 1.0)
+    order = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in a["row_perm"]])
+    assert np.array_equal(a["A.row_ptr"], np.concatenate([[0], np.cumsum(rlen[a["row_perm"]])]))
+    assert np.array_equal(a["A.col"], col_inv[col[order]])
+    assert np.array_equal(a["A.val"], np.repeat(sign, rlen[a["row_perm"]]) * val[order])
+    # A': the transpose, each row in increasing internal row order
+    A = sp.csr_matrix((a["A.val"], a["A.col"], a["A.row_ptr"]), shape=(m, n))
+    T = A.T.tocsr()
+    T.sort_indices()
+    assert np.array_equal(a["AT.row_ptr"], T.indptr)
+    assert np.array_equal(a["AT.col"], T.indices)
+    assert np.array_equal(a["AT.val"], T.data)
+    _check_csr_segments("A", a)
+    _check_csr_segments("AT", a)
